@@ -1,0 +1,171 @@
+"""CPU oracle for the Sample-Align-D data-parallel core (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline may import this package. It is a plain, slow, obviously correct
+restatement of the method (``oracle.cpp``) and shares no code with the CUDA
+library in ``paper_0901_2742_gb300``; neither imports the other.
+
+Functions follow the paper:
+  kmer_rank           Section 2 (r_ij, D_i, R_i) and the ancestor steps of the
+                      algorithm box (local/global ancestor), in exact integers
+  partition           Section 2.3.2 regular-sampling redistribution
+  gotoh               the per-bucket sequential aligner of Section 2.3.3, as
+                      global affine-gap (Gotoh) scores
+  bucket_pair_scores  all pairs u <= v inside every bucket
+
+Parity status: every function here is pinned by tests that do not reuse this
+code (brute-force alignment enumeration, sorted-list k-mer intersection,
+hand-worked examples under tests/golden, closed forms and invariants).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_SO = os.path.join(_HERE, "_build", "liborc.so")
+_lib = None
+
+
+def build(force: bool = False, defines: tuple[str, ...] = (), out: str | None = None) -> str:
+    """Compile the oracle with g++ (plain -O2; no vector intrinsics)."""
+    so = out or _SO
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    if force or defines or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC]
+        cmd += [f"-D{d}" for d in defines]
+        subprocess.check_call(cmd)
+        os.replace(tmp, so)
+    return so
+
+
+def _bind(lib):
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    lib.orc_kmer_histograms.restype = i64
+    lib.orc_kmer_histograms.argtypes = [P, P, i32, P, i32, i32, P, i64]
+    lib.orc_kmer_rank.restype = ctypes.c_int
+    lib.orc_kmer_rank.argtypes = [P, P, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P, P]
+    lib.orc_partition.restype = ctypes.c_int
+    lib.orc_partition.argtypes = [i32, P, P, i32, P, P, P]
+    lib.orc_gotoh.restype = i64
+    lib.orc_gotoh.argtypes = [P, i32, P, i32, P, i32, i32, i32]
+    lib.orc_bucket_pair_scores.restype = ctypes.c_int
+    lib.orc_bucket_pair_scores.argtypes = [P, P, i32, P, P, i32, P, i32, i32, i32, i32, P, P]
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def load_variant(path: str):
+    """Load a separately compiled oracle build (used to plant mistakes in tests)."""
+    return _bind(ctypes.CDLL(path))
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(np.asarray(a, dtype=dt))
+
+
+def default_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def kmer_histograms(residues, offsets, k, kmer_alphabet, class_map=None, lib=None):
+    """Per-sequence k-mer counts as an int64 (count, 3) array of (seq, code, count)."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    cm = None if class_map is None else _c(class_map, np.uint8)
+    n = len(offs) - 1
+    cap = max(1, int(offs[-1]))
+    out = np.empty((cap, 3), dtype=np.int64)
+    got = lib.orc_kmer_histograms(_ptr(res), _ptr(offs), n, _ptr(cm), kmer_alphabet, k,
+                                  out.ctypes.data, cap)
+    assert got >= 0
+    return out[:got]
+
+
+def kmer_rank(residues, offsets, alphabet, k, p, class_map=None, kmer_alphabet=None,
+              want_A=True, nthreads=None, lib=None):
+    """Returns dict(A, dloc, dcen, la, ga, key_a, key_b); raises ValueError on bad input."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    n = len(offs) - 1
+    cm = None if class_map is None else _c(class_map, np.uint8)
+    ka = kmer_alphabet if kmer_alphabet is not None else alphabet
+    A = np.zeros((n, n), dtype=np.int32) if want_A else None
+    dloc = np.zeros(n, np.uint64)
+    dcen = np.zeros(n, np.uint64)
+    la = np.zeros(p, np.int32)
+    ga = np.zeros(1, np.int32)
+    key_a = np.zeros(n, np.int32)
+    key_b = np.zeros(n, np.int32)
+    rc = lib.orc_kmer_rank(_ptr(res), _ptr(offs), n, alphabet, _ptr(cm), ka, k, p,
+                           nthreads or default_threads(), _ptr(A), _ptr(dloc), _ptr(dcen),
+                           _ptr(la), _ptr(ga), _ptr(key_a), _ptr(key_b))
+    if rc != 0:
+        raise ValueError("oracle kmer_rank: invalid arguments")
+    return dict(A=A, dloc=dloc, dcen=dcen, la=la, ga=int(ga[0]), key_a=key_a, key_b=key_b)
+
+
+def partition(key_a, key_b, p, lib=None):
+    """Returns dict(bucket_offsets[p+1], order[n], pivot_idx[p-1])."""
+    lib = lib or _load()
+    ka, kb = _c(key_a, np.int32), _c(key_b, np.int32)
+    n = len(ka)
+    bo = np.zeros(p + 1, np.int32)
+    order = np.zeros(max(n, 1), np.int32)
+    piv = np.zeros(max(p - 1, 1), np.int32)
+    rc = lib.orc_partition(n, _ptr(ka), _ptr(kb), p, _ptr(bo), _ptr(order), _ptr(piv))
+    if rc != 0:
+        raise ValueError("oracle partition: invalid arguments")
+    return dict(bucket_offsets=bo, order=order[:n], pivot_idx=piv[:max(p - 1, 0)])
+
+
+def gotoh(x, y, subst, gap_open, gap_extend, lib=None) -> int:
+    lib = lib or _load()
+    x, y = _c(x, np.uint8), _c(y, np.uint8)
+    S = _c(subst, np.int8)
+    return int(lib.orc_gotoh(_ptr(x), len(x), _ptr(y), len(y), _ptr(S), S.shape[0], gap_open,
+                             gap_extend))
+
+
+def bucket_pair_scores(residues, offsets, bucket_offsets, order, subst, gap_open, gap_extend,
+                       nthreads=None, lib=None):
+    """Returns (score_offsets int64[p+1], scores int32[total])."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    bo, od = _c(bucket_offsets, np.int32), _c(order, np.int32)
+    S = _c(subst, np.int8)
+    p = len(bo) - 1
+    nb = np.diff(bo).astype(np.int64)
+    total = int((nb * (nb + 1) // 2).sum())
+    so = np.zeros(p + 1, np.int64)
+    scores = np.zeros(max(total, 1), np.int32)
+    rc = lib.orc_bucket_pair_scores(_ptr(res), _ptr(offs), len(offs) - 1, _ptr(bo), _ptr(od), p,
+                                    _ptr(S), S.shape[0], gap_open, gap_extend,
+                                    nthreads or default_threads(), _ptr(so), _ptr(scores))
+    if rc != 0:
+        raise ValueError("oracle bucket_pair_scores: invalid arguments")
+    return so, scores[:total]
+
+
+def tri_index(u: int, v: int, nb: int) -> int:
+    """Position of pair (u, v), u <= v, in a bucket's row-major upper triangle."""
+    return u * nb - u * (u - 1) // 2 + (v - u)

@@ -1,0 +1,333 @@
+/*
+ * CPU oracle for the Sample-Align-D data-parallel core.
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow, obviously correct statement
+ * of what the GPU path computes. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product path never does. It
+ * shares no code, headers or tables with the CUDA library.
+ *
+ * Every result is an exact integer definition:
+ *   - k-mer similarity numerator a_ij = sum over k-mers tau of
+ *     min(n_xi(tau), n_xj(tau)), denominator b_ij = min(|x_i|, |x_j|) - k + 1
+ *     (Section 2, equation for r_ij; the stray factor tau printed inside the
+ *     sum is read as a typesetting error).
+ *   - average k-mer similarity D_i (Section 2, equation for D_i) in fixed point:
+ *     D^_i = sum_j floor(a_ij * 2^32 / b_ij); the 1/N factor is dropped because it
+ *     never changes an order inside one set. A term with b_ij <= 0 is 0.
+ *   - the k-mer rank R_i = log(0.1 + D_i) (Section 2) is monotone in the ratio,
+ *     so ranks are ordered by the exact key (a_i, b_i, i) with a_i/b_i compared
+ *     by 64-bit cross-multiplication and ties broken by the index.
+ *   - local ancestor of block b = argmax of the local D^ over the block
+ *     (medoid, lowest index on ties); global ancestor = medoid of the local
+ *     ancestors (Algorithm Sample-Align-D: local ancestors gathered at the root,
+ *     the global ancestor broadcast back; Section 2.3.3).
+ *   - regular-sampling redistribution (Section 2.3.2): blocks sorted by rank,
+ *     p-1 evenly spaced samples per block, p(p-1) samples sorted, p-1 pivots,
+ *     bucket = number of pivots strictly below the key.
+ *   - per-bucket all-pairs global alignment scores with affine gaps (Gotoh),
+ *     the aligner each processor runs on its bucket (Section 2.3.3; the paper
+ *     allows any sequential aligner), as the textbook three-state recursion.
+ */
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+using KmerCounts = std::unordered_map<uint64_t, int64_t>;
+
+const int64_t NEG_INF = INT64_MIN / 4;
+
+// Count every contiguous length-k window of sequence s (residues mapped
+// through class_map when given). The code of a k-mer is its base-A' number.
+KmerCounts count_kmers(const uint8_t* s, int64_t len, const uint8_t* class_map,
+                       int32_t kmer_alphabet, int32_t k) {
+    KmerCounts c;
+    for (int64_t start = 0; start + k <= len; start++) {
+        uint64_t code = 0;
+        for (int32_t t = 0; t < k; t++) {
+            uint64_t letter = class_map ? class_map[s[start + t]] : s[start + t];
+            code = code * (uint64_t)kmer_alphabet + letter;
+        }
+        c[code] += 1;
+    }
+    return c;
+}
+
+int64_t shared_kmers(const KmerCounts& x, const KmerCounts& y) {
+    const KmerCounts& small = x.size() <= y.size() ? x : y;
+    const KmerCounts& big = x.size() <= y.size() ? y : x;
+    int64_t a = 0;
+    for (const auto& kv : small) {
+        auto it = big.find(kv.first);
+        if (it != big.end()) a += std::min(kv.second, it->second);
+    }
+    return a;
+}
+
+// floor(a * 2^32 / b) for 0 <= a <= b; 0 when b <= 0 (no k-mer fits).
+uint64_t fixed_ratio(int64_t a, int64_t b) {
+    if (b <= 0) return 0;
+    return ((uint64_t)a << 32) / (uint64_t)b;
+}
+
+int64_t denom(int64_t li, int64_t lj, int32_t k) { return std::min(li, lj) - k + 1; }
+
+template <class F>
+void parallel_for(int64_t count, int32_t nthreads, F fn) {
+    if (nthreads <= 1 || count < 2) {
+        for (int64_t t = 0; t < count; t++) fn(t);
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> pool;
+    for (int32_t w = 0; w < nthreads; w++)
+        pool.emplace_back([&]() {
+            for (;;) {
+                int64_t t = next.fetch_add(1);
+                if (t >= count) break;
+                fn(t);
+            }
+        });
+    for (auto& th : pool) th.join();
+}
+
+int64_t block_begin(int64_t b, int64_t n, int64_t p) { return b * n / p; }
+
+// Rank key order: a_i/b_i ascending (cross-multiplied), then index ascending.
+struct KeyLess {
+    const int32_t* ka;
+    const int32_t* kb;
+    bool operator()(int32_t i, int32_t j) const {
+        int64_t lhs = (int64_t)ka[i] * (int64_t)kb[j];
+        int64_t rhs = (int64_t)ka[j] * (int64_t)kb[i];
+        if (lhs != rhs) return lhs < rhs;
+        return i < j;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+/* Per-sequence k-mer histograms flattened as (sequence, code, count) triples,
+ * sorted by sequence then code. Returns the triple count, or -1 if cap_triples
+ * is too small (then nothing is written). */
+int64_t orc_kmer_histograms(const uint8_t* res, const int64_t* offs, int32_t n,
+                            const uint8_t* class_map, int32_t kmer_alphabet, int32_t k,
+                            int64_t* out_triples, int64_t cap_triples) {
+    std::vector<std::vector<std::pair<uint64_t, int64_t>>> all(n);
+    int64_t total = 0;
+    for (int32_t i = 0; i < n; i++) {
+        KmerCounts c = count_kmers(res + offs[i], offs[i + 1] - offs[i], class_map, kmer_alphabet, k);
+        all[i].assign(c.begin(), c.end());
+        std::sort(all[i].begin(), all[i].end());
+        total += (int64_t)all[i].size();
+    }
+    if (total > cap_triples) return -1;
+    int64_t w = 0;
+    for (int32_t i = 0; i < n; i++)
+        for (auto& kv : all[i]) {
+            out_triples[3 * w] = i;
+            out_triples[3 * w + 1] = (int64_t)kv.first;
+            out_triples[3 * w + 2] = kv.second;
+            w++;
+        }
+    return total;
+}
+
+/* k-mer rank stage. Outputs (all host, caller-owned):
+ *   A      nullable, n*n int32 row-major: a_ij
+ *   dloc   n: sum over j in block(i) of floor(a_ij 2^32 / b_ij)
+ *   dcen   n: the same sum over all j
+ *   la     p: local ancestor of each block (-1 for an empty block)
+ *   ga     1: global ancestor (-1 when n == 0)
+ *   key_a, key_b  n: a(i, GA) and b(i, GA) (key (0, 1) when b(i, GA) <= 0)
+ * Returns 0, or -1 on invalid arguments. */
+int orc_kmer_rank(const uint8_t* res, const int64_t* offs, int32_t n, int32_t alphabet,
+                  const uint8_t* class_map, int32_t kmer_alphabet, int32_t k, int32_t p,
+                  int32_t nthreads, int32_t* A, uint64_t* dloc, uint64_t* dcen, int32_t* la,
+                  int32_t* ga, int32_t* key_a, int32_t* key_b) {
+    if (n < 0 || k < 1 || p < 1 || alphabet < 1 || kmer_alphabet < 1) return -1;
+    for (int32_t i = 0; i < n; i++)
+        for (int64_t t = offs[i]; t < offs[i + 1]; t++) {
+            if (res[t] >= alphabet) return -1;
+            if (class_map && class_map[res[t]] >= kmer_alphabet) return -1;
+            if (!class_map && res[t] >= kmer_alphabet) return -1;
+        }
+    std::vector<KmerCounts> cnt(n);
+    std::vector<int64_t> len(n);
+    parallel_for(n, nthreads, [&](int64_t i) {
+        len[i] = offs[i + 1] - offs[i];
+        cnt[i] = count_kmers(res + offs[i], len[i], class_map, kmer_alphabet, k);
+    });
+    auto block_of = [&](int64_t i) {
+        // largest b with floor(b n / p) <= i
+        int64_t b = (i * p) / n;
+        while (b + 1 < p && block_begin(b + 1, n, p) <= i) b++;
+        while (b > 0 && block_begin(b, n, p) > i) b--;
+        return b;
+    };
+    parallel_for(n, nthreads, [&](int64_t i) {
+        uint64_t sl = 0, sc = 0;
+        int64_t bi = block_of(i);
+        for (int32_t j = 0; j < n; j++) {
+            int64_t a = shared_kmers(cnt[i], cnt[j]);
+            if (A) A[(int64_t)i * n + j] = (int32_t)a;
+            uint64_t term = fixed_ratio(a, denom(len[i], len[j], k));
+            sc += term;
+            if (block_of(j) == bi) sl += term;
+        }
+        dloc[i] = sl;
+        dcen[i] = sc;
+    });
+    for (int32_t b = 0; b < p; b++) {
+        int64_t lo = block_begin(b, n, p), hi = block_begin(b + 1, n, p);
+        int32_t best = -1;
+        for (int64_t i = lo; i < hi; i++)
+            if (best < 0 || dloc[i] > dloc[best]) best = (int32_t)i;
+        la[b] = best;
+    }
+    int32_t g = -1;
+    uint64_t gbest = 0;
+    for (int32_t b = 0; b < p; b++) {
+        if (la[b] < 0) continue;
+        uint64_t s = 0;
+        for (int32_t b2 = 0; b2 < p; b2++) {
+            if (la[b2] < 0) continue;
+            int64_t a = shared_kmers(cnt[la[b]], cnt[la[b2]]);
+            s += fixed_ratio(a, denom(len[la[b]], len[la[b2]], k));
+        }
+        if (g < 0 || s > gbest) { g = la[b]; gbest = s; }
+    }
+    *ga = g;
+    for (int32_t i = 0; i < n; i++) {
+        int64_t b = denom(len[i], len[g], k);
+        if (b <= 0) { key_a[i] = 0; key_b[i] = 1; continue; }
+        key_a[i] = (int32_t)shared_kmers(cnt[i], cnt[g]);
+        key_b[i] = (int32_t)b;
+    }
+    return 0;
+}
+
+/* Regular-sampling redistribution by rank key (Section 2.3.2).
+ * bucket_offsets: p+1; order: n (members of a bucket ascending by index);
+ * pivot_idx: p-1 sequence indices of the pivots (-1 when there is none).
+ * Returns 0, or -1 on invalid arguments. */
+int orc_partition(int32_t n, const int32_t* key_a, const int32_t* key_b, int32_t p,
+                  int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx) {
+    if (n < 0 || p < 1) return -1;
+    for (int32_t i = 0; i < n; i++)
+        if (key_a[i] < 0 || key_b[i] < 1 || key_a[i] > key_b[i]) return -1;
+    KeyLess less{key_a, key_b};
+    std::vector<int32_t> samples;
+    int32_t q = 0;  // blocks that hold at least one sequence
+    for (int32_t b = 0; b < p; b++) {
+        int64_t lo = block_begin(b, n, p), hi = block_begin(b + 1, n, p);
+        int64_t w = hi - lo;
+        if (w == 0) continue;
+        q++;
+        std::vector<int32_t> blk;
+        for (int64_t i = lo; i < hi; i++) blk.push_back((int32_t)i);
+        std::sort(blk.begin(), blk.end(), less);
+        for (int64_t j = 1; j <= p - 1; j++) samples.push_back(blk[(j * w) / p]);
+    }
+    std::sort(samples.begin(), samples.end(), less);
+    std::vector<int32_t> piv;
+    for (int32_t m = 1; m <= p - 1; m++) {
+        if (q == 0) { pivot_idx[m - 1] = -1; continue; }
+        int64_t pos1 = (int64_t)(m - 1) * q + std::max(1, q / 2);  // 1-based
+        int32_t s = samples[pos1 - 1];
+        pivot_idx[m - 1] = s;
+        piv.push_back(s);
+    }
+    std::vector<int32_t> bucket(n);
+    std::vector<int32_t> count(p, 0);
+    for (int32_t i = 0; i < n; i++) {
+        int32_t c = 0;
+        for (int32_t s : piv) if (less(s, i)) c++;
+        bucket[i] = c;
+        count[c]++;
+    }
+    bucket_offsets[0] = 0;
+    for (int32_t b = 0; b < p; b++) bucket_offsets[b + 1] = bucket_offsets[b] + count[b];
+    std::vector<int32_t> fill(bucket_offsets, bucket_offsets + p);
+    for (int32_t i = 0; i < n; i++) order[fill[bucket[i]]++] = i;
+    return 0;
+}
+
+/* Global alignment score with affine gaps: a gap run of length g costs
+ * go + g*ge (go, ge <= 0); end gaps cost the same as internal ones.
+ * Three-state recursion over alignments ending in a match column (M), in x
+ * against a gap (X) or in a gap against y (Y); 64-bit arithmetic. */
+int64_t orc_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const int8_t* S,
+                  int32_t alphabet, int32_t go, int32_t ge) {
+    const int64_t W = (int64_t)n + 1;
+    std::vector<int64_t> M((size_t)(m + 1) * W, NEG_INF), X((size_t)(m + 1) * W, NEG_INF),
+        Y((size_t)(m + 1) * W, NEG_INF);
+    auto at = [&](int64_t i, int64_t j) { return i * W + j; };
+    M[at(0, 0)] = 0;  // the empty alignment
+    for (int32_t i = 0; i <= m; i++)
+        for (int32_t j = 0; j <= n; j++) {
+            if (i == 0 && j == 0) continue;
+            if (i > 0 && j > 0) {
+                int64_t prev = std::max({M[at(i - 1, j - 1)], X[at(i - 1, j - 1)], Y[at(i - 1, j - 1)]});
+                if (prev > NEG_INF) M[at(i, j)] = prev + S[x[i - 1] * alphabet + y[j - 1]];
+            }
+            if (i > 0) {
+                int64_t open = std::max(M[at(i - 1, j)], Y[at(i - 1, j)]);
+                int64_t v = NEG_INF;
+                if (open > NEG_INF) v = open + go + ge;
+                if (X[at(i - 1, j)] > NEG_INF) v = std::max(v, X[at(i - 1, j)] + ge);
+                X[at(i, j)] = v;
+            }
+            if (j > 0) {
+                int64_t open = std::max(M[at(i, j - 1)], X[at(i, j - 1)]);
+                int64_t v = NEG_INF;
+                if (open > NEG_INF) v = open + go + ge;
+                if (Y[at(i, j - 1)] > NEG_INF) v = std::max(v, Y[at(i, j - 1)] + ge);
+                Y[at(i, j)] = v;
+            }
+        }
+    return std::max({M[at(m, n)], X[at(m, n)], Y[at(m, n)]});
+}
+
+/* All pairs u <= v inside every bucket. score_offsets: p+1 (filled);
+ * scores[score_offsets[b] + u*nb - u*(u-1)/2 + (v-u)] = S(x_order[..u], x_order[..v]).
+ * Returns 0, or -1 on invalid arguments. */
+int orc_bucket_pair_scores(const uint8_t* res, const int64_t* offs, int32_t n,
+                           const int32_t* bucket_offsets, const int32_t* order, int32_t p,
+                           const int8_t* S, int32_t alphabet, int32_t go, int32_t ge,
+                           int32_t nthreads, int64_t* score_offsets, int32_t* scores) {
+    if (p < 1 || go > 0 || ge > 0) return -1;
+    for (int32_t a = 0; a < alphabet; a++)
+        for (int32_t b = 0; b < alphabet; b++)
+            if (S[a * alphabet + b] != S[b * alphabet + a]) return -1;
+    score_offsets[0] = 0;
+    for (int32_t b = 0; b < p; b++) {
+        int64_t nb = bucket_offsets[b + 1] - bucket_offsets[b];
+        score_offsets[b + 1] = score_offsets[b] + nb * (nb + 1) / 2;
+    }
+    std::vector<std::pair<int32_t, int64_t>> rows;  // (bucket, u)
+    for (int32_t b = 0; b < p; b++)
+        for (int64_t u = 0; u < bucket_offsets[b + 1] - bucket_offsets[b]; u++) rows.push_back({b, u});
+    parallel_for((int64_t)rows.size(), nthreads, [&](int64_t r) {
+        int32_t b = rows[r].first;
+        int64_t u = rows[r].second;
+        int64_t nb = bucket_offsets[b + 1] - bucket_offsets[b];
+        int32_t xi = order[bucket_offsets[b] + u];
+        for (int64_t v = u; v < nb; v++) {
+            int32_t yi = order[bucket_offsets[b] + v];
+            int64_t s = orc_gotoh(res + offs[xi], (int32_t)(offs[xi + 1] - offs[xi]), res + offs[yi],
+                                  (int32_t)(offs[yi + 1] - offs[yi]), S, alphabet, go, ge);
+            scores[score_offsets[b] + u * nb - u * (u - 1) / 2 + (v - u)] = (int32_t)s;
+        }
+    });
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+"""Planted mistakes: each mutant copy of the oracle must fail at least one pin.
+
+A plausible slip anywhere in the oracle (a dropped term, an off-by-one, a
+wrong state, a flipped comparison) is written into a copy of oracle.cpp,
+compiled on the CPU, and run through a compact battery of the same kinds of
+pins the other oracle tests use (brute-force alignments, brute-force k-mer
+intersections, hand-worked golden examples, literal pivot positions). The
+real oracle passes the battery; every mutant must fail it.
+"""
+import json
+import os
+import random
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0901_2742_gb300 import synth
+from test_oracle_gotoh import brute_force, random_symmetric
+from test_oracle_kmer_partition import kmer_tuples, multiset_intersection_size, check_partition
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+MUTANTS = {
+    "gap open dropped in X": ("if (open > NEG_INF) v = open + go + ge;\n                if (X[", "if (open > NEG_INF) v = open + ge;\n                if (X["),
+    "gap open dropped in Y": ("if (open > NEG_INF) v = open + go + ge;\n                if (Y[", "if (open > NEG_INF) v = open + ge;\n                if (Y["),
+    "match uses wrong residue": ("S[x[i - 1] * alphabet + y[j - 1]]", "S[y[j - 1] * alphabet + y[j - 1]]"),
+    "extend from match state": ("X[at(i - 1, j)] + ge)", "M[at(i - 1, j)] + ge)"),
+    "max instead of min count": ("a += std::min(kv.second, it->second)", "a += std::max(kv.second, it->second)"),
+    "denominator off by one": ("return std::min(li, lj) - k + 1;", "return std::min(li, lj) - k;"),
+    "fixed point 2^31": ("return ((uint64_t)a << 32) / (uint64_t)b;", "return ((uint64_t)a << 31) / (uint64_t)b;"),
+    "local ancestor tie to last": ("dloc[i] > dloc[best]", "dloc[i] >= dloc[best]"),
+    "sample position shifted": ("samples.push_back(blk[(j * w) / p]);", "samples.push_back(blk[((j - 1) * w) / p]);"),
+    "pivot rounding up": ("std::max(1, q / 2)", "std::max(1, (q + 1) / 2)"),
+    "bucket by pivots <= key": ("if (less(s, i)) c++;", "if (!less(i, s)) c++;"),
+    "key denominator ignores GA": ("int64_t b = denom(len[i], len[g], k);", "int64_t b = denom(len[i], len[i], k);"),
+    "self term dropped": ("for (int32_t j = 0; j < n; j++) {\n            int64_t a", "for (int32_t j = 0; j < n; j++) {\n            if (j == i) continue;\n            int64_t a"),
+}
+
+
+def battery(lib):
+    """Return the list of pin names that fail for this oracle build."""
+    failed = []
+    # 1. Gotoh vs brute force, including an odd alphabet and both gap regimes
+    rng = random.Random(1)
+    for _ in range(40):
+        A = rng.choice([2, 3, 20])
+        S = random_symmetric(rng, A, -6, 9)
+        go, ge = rng.choice([0, -3, -11]), rng.choice([-1, -2])
+        x = [rng.randrange(A) for _ in range(rng.randint(0, 5))]
+        y = [rng.randrange(A) for _ in range(rng.randint(0, 5))]
+        if oracle.gotoh(x, y, S, go, ge, lib=lib) != brute_force(x, y, S, go, ge):
+            failed.append("gotoh brute force")
+            break
+    # 2. k-mer matrix vs sorted-tuple intersection
+    seqs = [list(synth.uniform_residues(50 + t, rng.randint(2, 40), 3)) for t in range(8)]
+    res, offs = synth.pack(seqs)
+    r = oracle.kmer_rank(res, offs, 20, 2, 2, lib=lib)
+    tup = [kmer_tuples(s, 2) for s in seqs]
+    if any(r["A"][i, j] != multiset_intersection_size(tup[i], tup[j])
+           for i in range(8) for j in range(8)):
+        failed.append("kmer brute force")
+    # 3. golden examples (rank, partition, scores)
+    with open(os.path.join(GOLD, "kmer_rank_tiny.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        res, offs = synth.pack(c["seqs"])
+        r = oracle.kmer_rank(res, offs, c["alphabet"], c["k"], c["p"], class_map=c["class_map"],
+                             kmer_alphabet=c["kmer_alphabet"], lib=lib)
+        pt = oracle.partition(r["key_a"], r["key_b"], c["p"], lib=lib)
+        got = [r["dcen"].tolist(), r["dloc"].tolist(), r["la"].tolist(), r["ga"],
+               r["key_a"].tolist(), r["key_b"].tolist(), pt["order"].tolist(),
+               pt["pivot_idx"].tolist()]
+        want = [c["dcen"], c["dloc"], c["la"], c["ga"], c["key_a"], c["key_b"], c["order"],
+                c["pivot_idx"]]
+        if got != want:
+            failed.append("golden " + c["name"])
+    with open(os.path.join(GOLD, "psrs_tiny.json")) as f:
+        for c in json.load(f)["cases"]:
+            pt = oracle.partition(c["key_a"], c["key_b"], c["p"], lib=lib)
+            if pt["order"].tolist() != c["order"] or pt["pivot_idx"].tolist() != c["pivot_idx"]:
+                failed.append("golden psrs")
+    # 4. partition properties on random keys
+    g = np.random.default_rng(3)
+    kb = g.integers(1, 300, size=500).astype(np.int32)
+    ka = (g.random(500) * (kb + 1)).astype(np.int32).clip(0, kb)
+    try:
+        check_partition(ka, kb, 7, oracle.partition(ka, kb, 7, lib=lib))
+    except AssertionError:
+        failed.append("partition properties")
+    return failed
+
+
+def test_real_oracle_passes_battery():
+    assert battery(oracle._load()) == []
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name):
+    old, new = MUTANTS[name]
+    with open(oracle._SRC) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation anchor not found exactly once: {old!r}"
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "mut.cpp")
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+        so = os.path.join(d, "libmut.so")
+        os.system(f"g++ -O1 -std=c++17 -fPIC -shared -pthread -o {so} {path}")
+        assert os.path.exists(so)
+        lib = oracle.load_variant(so)
+        try:
+            caught = battery(lib)
+        except (ValueError, AssertionError, IndexError) as e:   # a pin raised: caught
+            caught = [f"raised {type(e).__name__}"]
+        assert caught, f"mutant '{name}' passed every pin"
