@@ -1,0 +1,210 @@
+/*
+ * sad.h -- C ABI of the GB300-native Sample-Align-D data-parallel core.
+ *
+ * Two stages of the method (Saeed & Khokhar, "Sample-Align-D"):
+ *   1. k-mer-rank partitioning (Section 2 "k-mer Rank", the algorithm box,
+ *      Section 2.3.2 "Redistribution Based on k-mer Rank"):
+ *        sad_kmer_rank   counts, all-pairs k-mer similarity, local and global
+ *                        ancestors, rank keys against the global ancestor
+ *        sad_partition   regular-sampling splitters and p buckets
+ *   2. per-bucket alignment (algorithm box "align sequences in each processor
+ *      using any sequential multiple alignment system", Section 2.3.3):
+ *        sad_bucket_pair_scores  all-pairs global affine-gap (Gotoh) scores
+ *                                inside every bucket
+ * plus sad_pipeline (both stages in one call) and a continuous-batching
+ * serving loop (sad_server_*).
+ *
+ * Conventions shared by every call
+ *   - Status: 0 (SAD_OK) or a negative SAD_E* code; sad_last_error() gives a
+ *     message for the calling thread's last failure.
+ *   - Memory: each call takes `mem`. With SAD_MEM_DEVICE every data array
+ *     argument (sequences, offsets, keys, buckets, outputs) is a device
+ *     pointer on the current device; with SAD_MEM_HOST every one is a host
+ *     pointer, the library stages it through device memory and the call
+ *     returns after the results are back in host memory. Parameter tables
+ *     (substitution matrix, class map) are always host pointers.
+ *   - The caller owns every argument buffer. The library allocates only its
+ *     own workspaces, which a sad_ctx caches (grow-only) between calls.
+ *   - `ctx` may be NULL: a default context per device is used. One context
+ *     must not be used by two calls at the same time.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Device-mode
+ *     calls enqueue their kernels on it; calls that must plan on the host
+ *     (sad_bucket_pair_scores, sad_pipeline) synchronise it once to read the
+ *     bucket layout.
+ *   - Nothing here falls back to the CPU: without a usable sm_103 GPU every
+ *     compute call fails with SAD_ECUDA.
+ */
+#ifndef SAD_H
+#define SAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAD_OK 0
+#define SAD_EINVAL (-1)    /* invalid argument (message in sad_last_error) */
+#define SAD_ENOMEM (-2)    /* device or host allocation failed */
+#define SAD_ECUDA (-3)     /* a CUDA runtime call or kernel failed */
+#define SAD_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define SAD_EBUSY (-5)     /* serving: no slot or memory for the job now */
+#define SAD_ERANGE (-6)    /* an output buffer is too small; the size is reported */
+#define SAD_ENOTFOUND (-7) /* serving: unknown job id */
+#define SAD_ECANCELED (-8) /* serving: the job was cancelled */
+
+#define SAD_MEM_HOST 0
+#define SAD_MEM_DEVICE 1
+
+/* Limits of this build (checked; violating one gives SAD_EINVAL). */
+#define SAD_MAX_ALPHABET 32     /* residue codes 0..alphabet-1 */
+#define SAD_MAX_KMER_SPACE 49152 /* kmer_alphabet^k */
+
+typedef struct sad_ctx sad_ctx;
+
+/* A set of n sequences: residues[offsets[i] .. offsets[i+1]) is sequence i.
+ * offsets has n+1 nondecreasing entries with offsets[0] = 0; every residue
+ * is a code < alphabet ("N sequences of amino acids x1..xN", algorithm box
+ * input). Both arrays live where the call's `mem` says. */
+typedef struct sad_seqset {
+    const uint8_t* residues;
+    const int64_t* offsets;
+    int32_t n;
+    int32_t alphabet; /* 1..SAD_MAX_ALPHABET */
+} sad_seqset;
+
+/* k-mer parameters (Section 2: "a k-mer is a contiguous subsequence of length
+ * k"). Residue r is counted as letter class_map[r] of a kmer_alphabet-letter
+ * alphabet (class_map NULL: identity, kmer_alphabet = alphabet).
+ *   cap = 0: all-pairs similarity on saturating uint8 count vectors (the
+ *            plain CUDA-core path; exact for any count via a residual pass).
+ *   cap > 0: the same similarity as threshold planes,
+ *            min(c, c') = sum_{t=1..cap} [c >= t][c' >= t] + residual above
+ *            cap, contracted on the tensor cores; exact for any count. */
+typedef struct sad_kmer_params {
+    int32_t k;               /* >= 1 */
+    int32_t kmer_alphabet;   /* >= 1; kmer_alphabet^k <= SAD_MAX_KMER_SPACE */
+    const uint8_t* class_map; /* host, `alphabet` entries, or NULL */
+    int32_t cap;             /* 0, or 1..8 */
+    int32_t p;               /* number of blocks / buckets, >= 1 */
+} sad_kmer_params;
+
+/* Outputs of sad_kmer_rank (caller-owned, in `mem` space).
+ * With b_ij = min(|x_i|,|x_j|) - k + 1 and a_ij = sum_tau min(n_xi(tau), n_xj(tau))
+ * (Section 2, r_ij = a_ij / b_ij; a term with b_ij <= 0 counts as 0):
+ *   dloc[n]  sum over j in block(i) of floor(a_ij * 2^32 / b_ij), blocks
+ *            [floor(bN/p), floor((b+1)N/p)) ("N/p sequences on each of the
+ *            p processors"); the fixed-point form of the local D_i (the 1/N
+ *            factor of D_i is dropped, it never changes an order)
+ *   dcen[n]  the same sum over all j (the centralised D_i)
+ *   la[p]    local ancestor of each block: argmax dloc in the block, lowest
+ *            index on ties; -1 for an empty block
+ *   ga[1]    global ancestor: the local ancestor with the largest fixed-point
+ *            similarity sum to all local ancestors (lowest index on ties)
+ *   key_a[n], key_b[n]  rank key of sequence i: a(i, GA) and b(i, GA);
+ *            (0, 1) when b(i, GA) <= 0. The k-mer rank R_i = log(0.1 + D)
+ *            of Section 2 is monotone, so sequences are ordered by
+ *            key_a/key_b (compared by 64-bit cross-multiplication), then by
+ *            index.
+ *   A        NULL, or n*n int32 row-major receiving a_ij. */
+typedef struct sad_rank_out {
+    uint64_t* dloc;
+    uint64_t* dcen;
+    int32_t* la;
+    int32_t* ga;
+    int32_t* key_a;
+    int32_t* key_b;
+    int32_t* A;
+} sad_rank_out;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `device`; it owns cached device
+ * workspaces. Returns SAD_OK and *out, or an error. */
+int sad_ctx_create(int32_t device, sad_ctx** out);
+/* Free a context and its workspaces (synchronises its device). */
+int sad_ctx_destroy(sad_ctx* ctx);
+
+/* Thread-local message for the last failure of this thread ("" if none). */
+const char* sad_last_error(void);
+/* Library version string. */
+const char* sad_version(void);
+
+/* ---- stage 1: k-mer rank ----------------------------------------------- */
+
+/* All-pairs k-mer similarity and the rank keys (Section 2 equations r_ij,
+ * D_i, R_i; algorithm box steps "locally compute k-mer rank", local and
+ * global ancestor). Errors: SAD_EINVAL for n < 0, alphabet out of range,
+ * k < 1, p < 1, cap out of range, kmer space too large, a class_map entry
+ * >= kmer_alphabet, bad offsets, or (detected on the device) a residue >=
+ * alphabet; SAD_ENOMEM; SAD_ECUDA. On error the outputs are unspecified. */
+int sad_kmer_rank(sad_ctx* ctx, const sad_seqset* seqs, const sad_kmer_params* params,
+                  const sad_rank_out* out, int32_t mem, void* stream);
+
+/* ---- stage 1: partition ------------------------------------------------- */
+
+/* Regular-sampling redistribution by rank key (Section 2.3.2):
+ * block b = [floor(bN/p), floor((b+1)N/p)) is sorted by key; p-1 samples are
+ * taken at 0-based positions floor(j*w_b/p), j = 1..p-1 of every non-empty
+ * block; the q(p-1) samples (q = non-empty blocks) are sorted into Y; pivot m
+ * (m = 1..p-1) is Y at 1-based position (m-1)q + max(1, floor(q/2)), which is
+ * (m-1)p + floor(p/2) whenever N >= p; sequence i goes to bucket
+ * #{pivots strictly below key_i}.
+ * Inputs key_a[n], key_b[n] (0 <= key_a <= key_b, key_b >= 1).
+ * Outputs: bucket_offsets[p+1] (CSR), order[n] (members of each bucket in
+ * ascending index), pivot_idx[p-1] (sequence index of each pivot; may be
+ * NULL). Errors: SAD_EINVAL (n < 0, p < 1, p > 4096, a bad key), SAD_ECUDA. */
+int sad_partition(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_t* key_b,
+                  int32_t p, int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                  int32_t mem, void* stream);
+
+/* ---- stage 2: per-bucket all-pairs alignment scores -------------------- */
+
+/* Number of scores for a bucket layout: sum_b n_b (n_b + 1) / 2, where
+ * n_b = bucket_offsets[b+1] - bucket_offsets[b]; bucket_offsets is in `mem`
+ * space. Returns SAD_OK and *total. */
+int sad_scores_size(const int32_t* bucket_offsets, int32_t p, int32_t mem, int64_t* total);
+
+#define SAD_SCORES_PER_BUCKET 0  /* one kernel launch per bucket, 32-bit DP */
+#define SAD_SCORES_PERSISTENT 1  /* one persistent launch over a length-binned
+                                    queue of every bucket, CUDA-graph replayed */
+
+/* Global alignment score with affine gaps for every pair u <= v inside every
+ * bucket (the diagonal is the self-score). A gap run of length g scores
+ * gap_open + g * gap_extend (gap_open, gap_extend <= 0, written as negative
+ * numbers, e.g. -11 and -1); end gaps score like internal ones; a gap in x
+ * may directly follow a gap in y, each run with its own opening.
+ * subst: host, alphabet x alphabet int8, row-major, symmetric.
+ * Layout: bucket b's members are order[bucket_offsets[b] .. bucket_offsets[b+1]);
+ * score_offsets[p+1] (written) holds each bucket's start in `scores`; the pair
+ * of local positions (u, v), u <= v, of bucket b with n_b members is at
+ * scores[score_offsets[b] + u*n_b - u*(u-1)/2 + (v-u)].
+ * scores_capacity is the length of `scores`; if it is smaller than the total,
+ * nothing is computed, score_offsets is still written and SAD_ERANGE returned.
+ * Errors: SAD_EINVAL (bad layout or order, asymmetric subst, positive gap
+ * costs, unknown mode), SAD_ERANGE, SAD_ENOMEM, SAD_ECUDA. */
+int sad_bucket_pair_scores(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                           const int32_t* order, int32_t p, const int8_t* subst,
+                           int32_t gap_open, int32_t gap_extend, int32_t mode,
+                           int64_t* score_offsets, int32_t* scores, int64_t scores_capacity,
+                           int32_t mem, void* stream);
+
+/* ---- both stages ------------------------------------------------------- */
+
+/* sad_kmer_rank, sad_partition and sad_bucket_pair_scores in one call, with
+ * every intermediate kept on the device. rank (may have NULL members: those
+ * outputs are skipped), bucket_offsets[p+1], order[n], score_offsets[p+1],
+ * scores[scores_capacity] are in `mem` space. SAD_ERANGE when the scores do
+ * not fit (score_offsets then holds the layout). */
+int sad_pipeline(sad_ctx* ctx, const sad_seqset* seqs, const sad_kmer_params* params,
+                 const int8_t* subst, int32_t gap_open, int32_t gap_extend, int32_t mode,
+                 const sad_rank_out* rank, int32_t* bucket_offsets, int32_t* order,
+                 int64_t* score_offsets, int32_t* scores, int64_t scores_capacity,
+                 int32_t mem, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAD_H */

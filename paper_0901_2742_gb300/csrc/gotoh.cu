@@ -1,0 +1,545 @@
+// Stage 2 of Sample-Align-D: all-pairs global alignment scores with affine
+// gaps inside every bucket (the "align sequences in each processor" step of
+// the algorithm box; Section 2.3.3 lets each processor run any sequential
+// aligner, and a progressive aligner starts from exactly these pair scores).
+//
+// Recurrences (Gotoh), gap run of length g = go + g*ge, go, ge <= 0:
+//   E(i,j) = max(E(i,j-1) + ge, H(i,j-1) + go + ge)      gap in x (consumes y_j)
+//   F(i,j) = max(F(i-1,j) + ge, H(i-1,j) + go + ge)      gap in y (consumes x_i)
+//   H(i,j) = max(H(i-1,j-1) + s(x_i, y_j), E(i,j), F(i,j))
+//   H(0,0) = 0, H(i,0) = go + i ge, H(0,j) = go + j ge, E(i,0) = F(0,j) = -inf.
+// With go <= 0 this equals the best score over alignments where every maximal
+// gap run pays one opening (a run in x may directly follow a run in y).
+//
+// GPU mapping. A CTA owns one query x_q of a bucket and keeps its profile
+// prof[a][i] = s(a, x_i) in shared memory; groups of G lanes each take one
+// subject y_v at a time. Lane t of a group holds R consecutive query rows in
+// registers (H, H+go+ge and E per row) and sweeps the subject's columns; the
+// bottom row's H and F and the column letter move to lane t+1 by a warp
+// shuffle each step, so the group is a diagonal wavefront of G x R rows.
+// Queries longer than G*R rows are processed in strips; a strip's bottom row
+// is handed to the next strip through a per-group boundary buffer in global
+// memory. Per cell: two add-max (DPX), one add, one 3-way max (DPX), one add.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "gotoh_stage.cuh"
+#include "sad_internal.cuh"
+
+namespace sad {
+
+namespace {
+
+constexpr int32_t NEG = -(1 << 30);
+
+// everything a Gotoh kernel needs besides its work items
+struct GotohArgs {
+    const uint8_t* res;        // padded residues
+    const int64_t* pad_off;    // padded starts
+    const int32_t* len;        // lengths
+    const int32_t* order;      // CSR members (sequence ids)
+    const int32_t* bucket_off; // p+1
+    const int32_t* srt;        // per bucket: sorted position -> local CSR position
+    const int64_t* score_off;  // p+1
+    int32_t* scores;
+    int32_t* scratch;          // strip boundaries: per group 2*(max_n+1) ints
+    int64_t scratch_stride;    // ints per group
+    const int8_t* subst;       // alphabet x alphabet (device)
+    int32_t alphabet;
+    int32_t go, ge;
+    int32_t prof_stride;       // bytes per profile row (>= padded query length)
+    int32_t G;                 // lanes per group
+};
+
+__device__ __forceinline__ int64_t tri_pos(int64_t u, int64_t v, int64_t nb) {
+    return u * nb - u * (u - 1) / 2 + (v - u);
+}
+
+// Load R profile bytes and widen them to int32.
+template <int R>
+__device__ __forceinline__ void load_profile(const int8_t* p, int32_t (&s)[R]) {
+    static_assert(R % 4 == 0, "R must be a multiple of 4");
+    uint32_t ww[R / 4];
+    if constexpr (R % 16 == 0) {
+#pragma unroll
+        for (int q = 0; q < R / 16; q++) {
+            const uint4 w = *(const uint4*)(p + 16 * q);
+            ww[4 * q] = w.x; ww[4 * q + 1] = w.y; ww[4 * q + 2] = w.z; ww[4 * q + 3] = w.w;
+        }
+    } else if constexpr (R % 8 == 0) {
+#pragma unroll
+        for (int q = 0; q < R / 8; q++) {
+            const uint2 w = *(const uint2*)(p + 8 * q);
+            ww[2 * q] = w.x; ww[2 * q + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < R / 4; q++) ww[q] = *(const uint32_t*)(p + 4 * q);
+    }
+#pragma unroll
+    for (int t = 0; t < R; t++) s[t] = (int32_t)(int8_t)(ww[t >> 2] >> (8 * (t & 3)));
+}
+
+// One group aligns query (profile in smem, length m) against subject y (length n,
+// n may be 0 for an idle group whose lanes still join the warp's shuffles).
+// Returns the score in every lane of the group (valid when active).
+template <int R>
+__device__ int32_t align_group(const int8_t* __restrict__ prof, int32_t m, const uint8_t* __restrict__ y,
+                               int32_t n, int32_t nsteps_warp, const GotohArgs& a,
+                               int32_t* __restrict__ bnd, int lane, unsigned gmask) {
+    const int G = a.G;
+    const int32_t goe = a.go + a.ge, ge = a.ge, go = a.go;
+    const int32_t strip_h = G * R;
+    const int32_t strips = (m + strip_h - 1) / strip_h;
+    int32_t result = 0;
+    for (int32_t s = 0; s < strips; s++) {
+        const int32_t row0 = s * strip_h + lane * R;   // 0-based residue of my first row
+        int32_t H[R], Hg[R], E[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            H[r] = go + (row0 + r + 1) * ge;
+            Hg[r] = H[r] + goe;
+            E[r] = NEG;
+        }
+        int32_t hdiag = (row0 == 0) ? 0 : go + row0 * ge;   // H(row0, 0)
+        const int32_t top = s * strip_h;                      // DP row above the strip
+        int32_t hin = 0, fin = NEG;                           // values from lane-1
+        uint32_t yin = 0;
+        uint32_t yword = 0;
+        const bool last_strip = s == strips - 1;
+        for (int32_t tau = 0; tau < nsteps_warp; tau++) {
+            const int32_t j = tau - lane + 1;   // my 1-based column this step
+            // lane 0 feeds the strip's top boundary and the subject letter
+            // (reads stay inside the subject and its 16 zero bytes of padding)
+            if (lane == 0 && tau < n) {
+                if ((tau & 3) == 0) yword = *(const uint32_t*)(y + tau);
+                yin = (yword >> (8 * (tau & 3))) & 0xffu;
+                if (s == 0) {
+                    hin = go + (tau + 1) * ge;
+                    fin = NEG;
+                } else {
+                    hin = bnd[2 * (tau + 1)];
+                    fin = bnd[2 * (tau + 1) + 1];
+                }
+            }
+            int32_t hout = hin, fout = fin;
+            if (j >= 1 && j <= n) {
+                int32_t sc[R];
+                load_profile<R>(prof + (int64_t)yin * a.prof_stride + row0, sc);
+                int32_t hu = hin, fu = fin;
+                int32_t hgu = hu + goe;
+                int32_t hd = hdiag;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int32_t e = __viaddmax_s32(E[r], ge, Hg[r]);
+                    const int32_t f = __viaddmax_s32(fu, ge, hgu);
+                    const int32_t h = __vimax3_s32(hd + sc[r], e, f);
+                    hd = H[r];
+                    H[r] = h;
+                    Hg[r] = h + goe;
+                    E[r] = e;
+                    fu = f;
+                    hgu = Hg[r];
+                }
+                hdiag = hin;
+                hout = H[R - 1];
+                fout = fu;
+                if (!last_strip && lane == G - 1) {
+                    bnd[2 * j] = hout;
+                    bnd[2 * j + 1] = fout;
+                }
+            }
+            // pass bottom row and letter one lane down the group
+            hin = __shfl_up_sync(gmask, hout, 1, G);
+            fin = __shfl_up_sync(gmask, fout, 1, G);
+            yin = __shfl_up_sync(gmask, yin, 1, G);
+        }
+        __syncwarp(gmask);
+        if (last_strip) {
+            const int32_t rr = (m - 1) - s * strip_h;   // strip-local row of x_m
+            const int owner = rr / R, rsel = rr % R;
+            int32_t v = 0;
+#pragma unroll
+            for (int r = 0; r < R; r++) v = (r == rsel) ? H[r] : v;
+            result = __shfl_sync(gmask, v, owner, G);
+        }
+        (void)top;
+    }
+    return result;
+}
+
+template <int R>
+__global__ void __launch_bounds__(128)
+k_gotoh_items(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __restrict__ head,
+              GotohArgs a) {
+    extern __shared__ __align__(16) int8_t prof[];
+    __shared__ int32_t item_sh;
+    const int G = a.G;
+    const int NG = blockDim.x / G;
+    const int g = threadIdx.x / G;
+    const int lane = threadIdx.x % G;
+    const int warp_lane0 = (threadIdx.x & 31) - lane;   // first lane of my group in the warp
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << warp_lane0);
+    int32_t it_idx = head ? -1 : (int32_t)blockIdx.x;
+    for (;;) {
+        if (head) {
+            __syncthreads();
+            if (threadIdx.x == 0) item_sh = atomicAdd(head, 1);
+            __syncthreads();
+            it_idx = item_sh;
+        }
+        if (it_idx >= n_items) break;
+        const GotohItem it = items[it_idx];
+        const int32_t b = it.bucket;
+        const int32_t boff = a.bucket_off[b];
+        const int32_t nb = a.bucket_off[b + 1] - boff;
+        const int32_t uq = a.srt[boff + it.q];
+        const int32_t xq = a.order[boff + uq];
+        const int32_t m = a.len[xq];
+        const uint8_t* x = a.res + a.pad_off[xq];
+        // profile rows prof[c][i] = s(c, x_i); rows past m are zero
+        const int32_t mp = a.prof_stride;
+        for (int32_t t = threadIdx.x; t < a.alphabet * mp; t += blockDim.x) {
+            const int32_t c = t / mp, i = t - c * mp;
+            prof[t] = i < m ? a.subst[c * a.alphabet + x[i]] : (int8_t)0;
+        }
+        __syncthreads();
+        int32_t* bnd = a.scratch + ((int64_t)blockIdx.x * NG + g) * a.scratch_stride;
+        const int32_t nsub = it.v1 - it.v0;
+        const int32_t rounds = (nsub + NG - 1) / NG;
+        for (int32_t rd = 0; rd < rounds; rd++) {
+            const int32_t v = it.v0 + rd * NG + g;
+            const bool have = v < it.v1;
+            int32_t uv = 0, ys = 0, n = 0;
+            if (have) {
+                uv = a.srt[boff + v];
+                ys = a.order[boff + uv];
+                n = a.len[ys];
+            }
+            // warp-uniform step count (every group of the warp joins each shuffle)
+            const int32_t need = (have && m > 0 && n > 0) ? n + G - 1 : 0;
+            const int32_t steps = (__reduce_max_sync(0xffffffffu, need) + 3) & ~3;
+            int32_t score = 0;
+            if (steps > 0) {
+                score = align_group<R>(prof, m, a.res + a.pad_off[have ? ys : xq],
+                                       (have && m > 0) ? n : 0, steps, a, bnd, lane, gmask);
+            }
+            if (have && lane == 0) {
+                if (m == 0 && n == 0) score = 0;
+                else if (m == 0) score = a.go + n * a.ge;
+                else if (n == 0) score = a.go + m * a.ge;
+                const int32_t lo = min(uq, uv), hi = max(uq, uv);
+                a.scores[a.score_off[b] + tri_pos(lo, hi, nb)] = score;
+            }
+        }
+        if (!head) break;
+    }
+}
+
+using KernelFn = void (*)(const GotohItem*, int32_t, int32_t*, GotohArgs);
+
+KernelFn kernel_for(int R) {
+    switch (R) {
+        case 4: return k_gotoh_items<4>;
+        case 8: return k_gotoh_items<8>;
+        case 12: return k_gotoh_items<12>;
+        case 16: return k_gotoh_items<16>;
+        case 20: return k_gotoh_items<20>;
+        case 24: return k_gotoh_items<24>;
+        case 32: return k_gotoh_items<32>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+// Host-side plan: per bucket, members sorted by length (ascending, ties by
+// local position); a work item is one query row with a range of subjects
+// that are at least as long.
+void plan_buckets(const std::vector<int32_t>& h_bo, const std::vector<int32_t>& h_order,
+                  const std::vector<int32_t>& h_len, int32_t p, std::vector<int32_t>* srt,
+                  std::vector<int64_t>* score_off) {
+    srt->assign(h_order.size(), 0);
+    score_off->assign((size_t)p + 1, 0);
+    for (int32_t b = 0; b < p; b++) {
+        const int32_t lo = h_bo[b], nb = h_bo[b + 1] - h_bo[b];
+        int32_t* s = srt->data() + lo;
+        std::iota(s, s + nb, 0);
+        std::stable_sort(s, s + nb, [&](int32_t u, int32_t v) {
+            return h_len[h_order[lo + u]] < h_len[h_order[lo + v]];
+        });
+        (*score_off)[b + 1] = (*score_off)[b] + (int64_t)nb * (nb + 1) / 2;
+    }
+}
+
+int gotoh_launch(sad_ctx* ctx, const DevSeqs& S, const GotohLaunch& L, cudaStream_t stream) {
+    KernelFn fn = kernel_for(L.R);
+    SAD_CHECK(fn != nullptr, SAD_EINVAL, "no Gotoh kernel for R = %d", L.R);
+    SAD_CHECK(L.G == 4 || L.G == 8 || L.G == 16 || L.G == 32, SAD_EINVAL, "G = %d", L.G);
+    const int threads = 128;
+    const int NG = threads / L.G;
+    GotohArgs a;
+    a.res = S.res;
+    a.pad_off = S.pad_off;
+    a.len = S.len;
+    a.order = L.order;
+    a.bucket_off = L.bucket_off;
+    a.srt = L.srt;
+    a.score_off = L.score_off;
+    a.scores = L.scores;
+    a.subst = L.subst;
+    a.alphabet = S.alphabet;
+    a.go = L.go;
+    a.ge = L.ge;
+    a.G = L.G;
+    const int32_t strip_h = L.G * L.R;
+    a.prof_stride = (int32_t)round_up(std::max<int32_t>(L.max_m, 1), strip_h);
+    const int grid = L.persistent ? L.persistent_grid : L.n_items;
+    if (grid == 0) return SAD_OK;
+    // strip boundaries are needed only for queries longer than one strip
+    a.scratch_stride = 2 * ((int64_t)S.max_len + 1 + 4);
+    int32_t* scratch = nullptr;
+    if (L.max_m > strip_h) {
+        void* sp = nullptr;
+        SAD_RET(workspace(ctx, WS_SCORE_SCRATCH, sizeof(int32_t) * (size_t)grid * NG * a.scratch_stride,
+                          stream, &sp));
+        scratch = (int32_t*)sp;
+    }
+    a.scratch = scratch;
+    const size_t smem = (size_t)S.alphabet * a.prof_stride;
+    SAD_CHECK(smem <= ctx->smem_optin, SAD_EINVAL, "query profile of %zu bytes exceeds shared memory",
+              smem);
+    SAD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fn<<<grid, threads, smem, stream>>>(L.items, L.n_items, L.head, a);
+    SAD_CUDA(cudaGetLastError());
+    return SAD_OK;
+}
+
+// Choose R for a query length so that one strip covers it with little padding
+// at G = 32 lanes; longer queries strip-mine at R = 32.
+int pick_R(int32_t m) {
+    static const int Rs[] = {4, 8, 12, 16, 20, 24, 32};
+    for (int R : Rs)
+        if (m <= 32 * R) return R;
+    return 32;
+}
+
+int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, const int32_t* d_order,
+                         int32_t p, const int8_t* h_subst, int32_t go, int32_t ge, int32_t mode,
+                         int64_t* d_score_off_out, int32_t* d_scores, int64_t capacity,
+                         int64_t* total_out, cudaStream_t stream) {
+    const int32_t n = S.n;
+    std::vector<int32_t> h_bo((size_t)p + 1), h_order((size_t)n);
+    SAD_CUDA(cudaMemcpyAsync(h_bo.data(), d_bo, 4ull * (p + 1), cudaMemcpyDeviceToHost, stream));
+    if (n > 0)
+        SAD_CUDA(cudaMemcpyAsync(h_order.data(), d_order, 4ull * n, cudaMemcpyDeviceToHost, stream));
+    SAD_CUDA(cudaStreamSynchronize(stream));
+    SAD_CHECK(h_bo[0] == 0 && h_bo[p] == n, SAD_EINVAL,
+              "bucket_offsets must start at 0 and end at n = %d", n);
+    std::vector<char> seen((size_t)n, 0);
+    for (int32_t b = 0; b < p; b++)
+        SAD_CHECK(h_bo[b + 1] >= h_bo[b], SAD_EINVAL, "bucket_offsets decreases at %d", b);
+    for (int32_t t = 0; t < n; t++) {
+        const int32_t i = h_order[t];
+        SAD_CHECK(i >= 0 && i < n && !seen[i], SAD_EINVAL,
+                  "order is not a permutation of 0..n-1 (entry %d = %d)", t, i);
+        seen[i] = 1;
+    }
+    std::vector<int32_t> srt;
+    std::vector<int64_t> score_off;
+    plan_buckets(h_bo, h_order, S.h_len, p, &srt, &score_off);
+    *total_out = score_off[p];
+    // device plan: srt, score_off, subst, items
+    std::vector<GotohItem> items;
+    int32_t max_m = 0;
+    for (int32_t b = 0; b < p; b++) {
+        const int32_t lo = h_bo[b], nb = h_bo[b + 1] - lo;
+        for (int32_t q = 0; q < nb; q++) {
+            items.push_back(GotohItem{b, q, q, nb});
+            max_m = std::max(max_m, S.h_len[h_order[lo + srt[lo + q]]]);
+        }
+    }
+    SAD_CHECK(mode == SAD_SCORES_PER_BUCKET || mode == SAD_SCORES_PERSISTENT, SAD_EINVAL,
+              "unknown scores mode %d", mode);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return o;
+    };
+    const size_t o_srt = carve(4ull * (n + 1)), o_so = carve(8ull * (p + 1)),
+                 o_sub = carve((size_t)S.alphabet * S.alphabet), o_items = carve(sizeof(GotohItem) * (items.size() + 1)),
+                 o_head = carve(16);
+    void* plan = nullptr;
+    SAD_RET(workspace(ctx, WS_SCORE_PLAN, off, stream, &plan));
+    void* pin = nullptr;
+    SAD_RET(pinned(ctx, off, stream, &pin));
+    char* hp = (char*)pin;
+    memcpy(hp + o_srt, srt.data(), 4ull * n);
+    memcpy(hp + o_so, score_off.data(), 8ull * (p + 1));
+    memcpy(hp + o_sub, h_subst, (size_t)S.alphabet * S.alphabet);
+    memcpy(hp + o_items, items.data(), sizeof(GotohItem) * items.size());
+    memset(hp + o_head, 0, 16);
+    char* dp = (char*)plan;
+    SAD_CUDA(cudaMemcpyAsync(dp, hp, off, cudaMemcpyHostToDevice, stream));
+    if (d_score_off_out)
+        SAD_CUDA(cudaMemcpyAsync(d_score_off_out, dp + o_so, 8ull * (p + 1), cudaMemcpyDeviceToDevice,
+                                 stream));
+    if (score_off[p] > capacity) {
+        set_error("scores need %lld entries, capacity is %lld", (long long)score_off[p],
+                  (long long)capacity);
+        return SAD_ERANGE;
+    }
+    GotohLaunch L;
+    L.order = d_order;
+    L.bucket_off = d_bo;
+    L.srt = (const int32_t*)(dp + o_srt);
+    L.score_off = (const int64_t*)(dp + o_so);
+    L.scores = d_scores;
+    L.subst = (const int8_t*)(dp + o_sub);
+    L.go = go;
+    L.ge = ge;
+    const GotohItem* d_items = (const GotohItem*)(dp + o_items);
+    if (mode == SAD_SCORES_PER_BUCKET) {
+        // one launch per bucket, R from the bucket's median member length
+        int64_t first = 0;
+        for (int32_t b = 0; b < p; b++) {
+            const int32_t lo = h_bo[b], nb = h_bo[b + 1] - lo;
+            if (nb == 0) continue;
+            int32_t bm = 0;
+            for (int32_t q = 0; q < nb; q++) bm = std::max(bm, S.h_len[h_order[lo + q]]);
+            const int32_t med = S.h_len[h_order[lo + srt[lo + nb / 2]]];
+            L.R = pick_R(med);
+            L.G = 32;
+            L.max_m = bm;
+            L.items = d_items + first;
+            L.n_items = nb;
+            L.head = nullptr;
+            L.persistent = false;
+            SAD_RET(gotoh_launch(ctx, S, L, stream));
+            first += nb;
+        }
+    } else {
+        // persistent: one launch over every bucket's rows, longest first
+        std::vector<int64_t> cost(items.size());
+        std::vector<int32_t> idx(items.size());
+        for (size_t t = 0; t < items.size(); t++) {
+            const GotohItem& it = items[t];
+            const int32_t lo = h_bo[it.bucket];
+            const int64_t mq = S.h_len[h_order[lo + srt[lo + it.q]]];
+            int64_t c = 0;
+            for (int32_t v = it.v0; v < it.v1; v++) c += mq * S.h_len[h_order[lo + srt[lo + v]]];
+            cost[t] = c;
+            idx[t] = (int32_t)t;
+        }
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+        std::vector<GotohItem> sorted(items.size());
+        for (size_t t = 0; t < items.size(); t++) sorted[t] = items[idx[t]];
+        memcpy(hp + o_items, sorted.data(), sizeof(GotohItem) * sorted.size());
+        SAD_CUDA(cudaMemcpyAsync(dp + o_items, hp + o_items, sizeof(GotohItem) * sorted.size(),
+                                 cudaMemcpyHostToDevice, stream));
+        std::vector<int32_t> all_len;
+        for (int32_t i = 0; i < n; i++) all_len.push_back(S.h_len[i]);
+        std::sort(all_len.begin(), all_len.end());
+        const int32_t med = n ? all_len[n / 2] : 1;
+        L.R = pick_R(med);
+        L.G = 32;
+        L.max_m = max_m;
+        L.items = d_items;
+        L.n_items = (int32_t)items.size();
+        L.head = (int32_t*)(dp + o_head);
+        L.persistent = true;
+        L.persistent_grid = ctx->num_sms * 4;
+        SAD_RET(gotoh_launch(ctx, S, L, stream));
+    }
+    return SAD_OK;
+}
+
+}  // namespace sad
+
+extern "C" int sad_scores_size(const int32_t* bucket_offsets, int32_t p, int32_t mem, int64_t* total) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(bucket_offsets && total && p >= 1, SAD_EINVAL, "invalid arguments");
+    std::vector<int32_t> bo((size_t)p + 1);
+    SAD_RET(arg_to_host(bucket_offsets, 4ull * (p + 1), mem, 0, bo.data()));
+    int64_t t = 0;
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bo[b + 1] - bo[b];
+        SAD_CHECK(nb >= 0, SAD_EINVAL, "bucket_offsets decreases at %d", b);
+        t += nb * (nb + 1) / 2;
+    }
+    *total = t;
+    return SAD_OK;
+}
+
+extern "C" int sad_bucket_pair_scores(sad_ctx* ctx_in, const sad_seqset* seqs,
+                                      const int32_t* bucket_offsets, const int32_t* order, int32_t p,
+                                      const int8_t* subst, int32_t gap_open, int32_t gap_extend,
+                                      int32_t mode, int64_t* score_offsets, int32_t* scores,
+                                      int64_t scores_capacity, int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(seqs && bucket_offsets && score_offsets && subst, SAD_EINVAL, "a required pointer is NULL");
+    SAD_CHECK(p >= 1, SAD_EINVAL, "p = %d < 1", p);
+    SAD_CHECK(gap_open <= 0 && gap_extend <= 0, SAD_EINVAL,
+              "gap costs must be <= 0 (got open %d, extend %d)", gap_open, gap_extend);
+    SAD_CHECK(gap_open >= -(1 << 20) && gap_extend >= -(1 << 20), SAD_EINVAL, "gap costs too large");
+    const int32_t A = seqs->alphabet;
+    SAD_CHECK(A >= 1 && A <= SAD_MAX_ALPHABET, SAD_EINVAL, "alphabet %d", A);
+    for (int32_t x = 0; x < A; x++)
+        for (int32_t y = 0; y < A; y++)
+            SAD_CHECK(subst[x * A + y] == subst[y * A + x], SAD_EINVAL,
+                      "substitution matrix is not symmetric at (%d, %d)", x, y);
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    SAD_RET(status_clear(ctx, stream));
+    DevSeqs S;
+    SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
+    const int32_t n = S.n;
+    SAD_CHECK(n == 0 || order != nullptr, SAD_EINVAL, "order is NULL");
+    // scores must fit int32: |score| <= (max|s| + |go| + |ge|) * (m + n)
+    int32_t smax = 0;
+    for (int32_t t = 0; t < A * A; t++) smax = std::max(smax, (int32_t)std::abs((int)subst[t]));
+    const int64_t bound = ((int64_t)smax + (int64_t)-gap_open + (int64_t)-gap_extend) * 2 *
+                          ((int64_t)S.max_len + 1);
+    SAD_CHECK(bound < (1ll << 29), SAD_EINVAL, "scores could exceed the 32-bit DP range");
+    const int32_t* dbo = bucket_offsets;
+    const int32_t* dord = order;
+    int64_t* dso = score_offsets;
+    int32_t* dsc = scores;
+    int64_t total = 0;
+    if (mem == SAD_MEM_HOST) {
+        void* st = nullptr;
+        SAD_RET(workspace(ctx, WS_PART_OUT, 4ull * (p + 1 + n) + 8ull * (p + 1) + 1024, stream, &st));
+        int32_t* s32 = (int32_t*)st;
+        SAD_CUDA(cudaMemcpyAsync(s32, bucket_offsets, 4ull * (p + 1), cudaMemcpyHostToDevice, stream));
+        if (n) SAD_CUDA(cudaMemcpyAsync(s32 + p + 1, order, 4ull * n, cudaMemcpyHostToDevice, stream));
+        dbo = s32;
+        dord = s32 + p + 1;
+        dso = (int64_t*)(((uintptr_t)(s32 + p + 1 + n) + 15) & ~(uintptr_t)15);
+        SAD_RET(sad_scores_size(bucket_offsets, p, SAD_MEM_HOST, &total));
+        if (total <= scores_capacity) {
+            void* so = nullptr;
+            SAD_RET(workspace(ctx, WS_SCORE_OUT, 4ull * (total + 1), stream, &so));
+            dsc = (int32_t*)so;
+        }
+    }
+    int rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend, mode, dso, dsc,
+                                  scores_capacity, &total, stream);
+    if (mem == SAD_MEM_HOST) {
+        SAD_CUDA(cudaMemcpyAsync(score_offsets, dso, 8ull * (p + 1), cudaMemcpyDeviceToHost, stream));
+        if (rc == SAD_OK && total > 0)
+            SAD_CUDA(cudaMemcpyAsync(scores, dsc, 4ull * total, cudaMemcpyDeviceToHost, stream));
+    }
+    if (rc != SAD_OK) {
+        cudaStreamSynchronize(stream);
+        return rc;
+    }
+    SAD_RET(status_check(ctx, stream));
+    return SAD_OK;
+}

@@ -1,0 +1,259 @@
+// Regular-sampling redistribution by k-mer rank (Section 2.3.2, the sample-sort
+// steps of the algorithm box): sort each block by rank, take p-1 evenly spaced
+// samples per block, sort the samples, pick p-1 pivots, bucket every sequence.
+//
+// A rank key (a_i, b_i, i) is packed into one 64-bit integer
+//   K_i = floor(a_i 2^32 / b_i) << 31 | i.
+// For b <= 2^16 two different fractions differ by at least 2^-32, so the
+// fixed-point part orders them exactly and equal fractions tie; the index
+// breaks ties. Every comparison below is then a plain 64-bit comparison.
+#include <cstring>
+
+#include "partition_stage.cuh"
+#include "sad_internal.cuh"
+
+namespace sad {
+
+namespace {
+
+constexpr uint32_t STATUS_BAD_KEY = 1u << 3;
+
+__global__ void k_part_keys(int32_t n, const int32_t* __restrict__ ka, const int32_t* __restrict__ kb,
+                            uint64_t* __restrict__ K, uint32_t* __restrict__ status) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t a = ka[i], b = kb[i];
+    if (a < 0 || b < 1 || a > b || b > 65536) {
+        atomicOr(status, STATUS_BAD_KEY);
+        a = 0;
+        b = 1;
+    }
+    const uint64_t fx = ((uint64_t)a << 32) / (uint64_t)b;
+    K[i] = (fx << 31) | (uint64_t)i;
+}
+
+// rank of every key inside its block: grid (p, chunks of 256 elements)
+__global__ void k_part_block_rank(int32_t n, int32_t p, const uint64_t* __restrict__ K,
+                                  int32_t* __restrict__ rank) {
+    __shared__ uint64_t tile[1024];
+    const int32_t b = blockIdx.x;
+    const int64_t lo = (int64_t)b * n / p, hi = (int64_t)(b + 1) * n / p;
+    const int64_t i = lo + (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (lo + (int64_t)blockIdx.y * blockDim.x >= hi) return;  // whole CTA idle (uniform)
+    const uint64_t key = i < hi ? K[i] : 0;
+    int32_t r = 0;
+    for (int64_t t0 = lo; t0 < hi; t0 += 1024) {
+        const int64_t m = min((int64_t)1024, hi - t0);
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < m; t += blockDim.x) tile[t] = K[t0 + t];
+        __syncthreads();
+        for (int64_t t = 0; t < m; t++) r += tile[t] < key;
+    }
+    if (i < hi) rank[i] = r;
+}
+
+// samples: element of rank r in block b is sample j for every j in 1..p-1 with
+// floor(j w / p) = r, i.e. j in [ceil(r p / w), ceil((r+1) p / w) - 1]
+__global__ void k_part_samples(int32_t n, int32_t p, const uint64_t* __restrict__ K,
+                               const int32_t* __restrict__ rank, uint64_t* __restrict__ Y) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // block of i: largest b with floor(b n / p) <= i
+    int64_t b = ((int64_t)i * p) / n;
+    while (b + 1 < p && (b + 1) * n / p <= i) b++;
+    while (b > 0 && b * n / p > i) b--;
+    const int64_t lo = b * n / p, hi = (b + 1) * n / p, w = hi - lo;
+    const int64_t r = rank[i];
+    int64_t jlo = (r * p + w - 1) / w, jhi = ((r + 1) * p + w - 1) / w - 1;
+    if (jlo < 1) jlo = 1;
+    if (jhi > p - 1) jhi = p - 1;
+    for (int64_t j = jlo; j <= jhi; j++) Y[b * (p - 1) + j - 1] = K[i];
+}
+
+// position of every sample in sorted order (equal samples keep their slot order)
+__global__ void k_part_sample_rank(int32_t M, const uint64_t* __restrict__ Y,
+                                   uint64_t* __restrict__ Ysorted) {
+    __shared__ uint64_t tile[1024];
+    const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t key = s < M ? Y[s] : 0;
+    int32_t r = 0;
+    for (int32_t t0 = 0; t0 < M; t0 += 1024) {
+        const int32_t m = min(1024, M - t0);
+        __syncthreads();
+        for (int32_t t = threadIdx.x; t < m; t += blockDim.x) tile[t] = Y[t0 + t];
+        __syncthreads();
+        for (int32_t t = 0; t < m; t++) {
+            const uint64_t v = tile[t];
+            r += (v < key) | ((v == key) & (t0 + t < s));
+        }
+    }
+    if (s < M) Ysorted[r] = key;
+}
+
+// pivot m = sorted sample at 1-based (m-1) q + max(1, floor(q/2)), q = non-empty blocks
+__global__ void k_part_pivots(int32_t n, int32_t p, const uint64_t* __restrict__ Ysorted,
+                              uint64_t* __restrict__ piv, int32_t* __restrict__ pivot_idx) {
+    const int32_t m = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (m > p - 1) return;
+    const int64_t q = n < p ? n : p;
+    if (q == 0) {
+        piv[m - 1] = ~0ull;
+        if (pivot_idx) pivot_idx[m - 1] = -1;
+        return;
+    }
+    const int64_t pos1 = (int64_t)(m - 1) * q + (q / 2 > 1 ? q / 2 : 1);
+    const uint64_t v = Ysorted[pos1 - 1];
+    piv[m - 1] = v;
+    if (pivot_idx) pivot_idx[m - 1] = (int32_t)(v & 0x7fffffffull);
+}
+
+// bucket = number of pivots strictly below the key (pivots are sorted)
+__global__ void k_part_bucket(int32_t n, int32_t p, const uint64_t* __restrict__ K,
+                              const uint64_t* __restrict__ piv, int32_t* __restrict__ bucket,
+                              int32_t* __restrict__ count) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t key = K[i];
+    int32_t lo = 0, hi = p - 1;  // first pivot >= key
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (piv[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    bucket[i] = lo;
+    atomicAdd(&count[lo], 1);
+}
+
+__global__ void k_part_offsets(int32_t p, const int32_t* __restrict__ count,
+                               int32_t* __restrict__ offsets) {
+    if (threadIdx.x != 0) return;
+    int32_t s = 0;
+    offsets[0] = 0;
+    for (int32_t b = 0; b < p; b++) {
+        s += count[b];
+        offsets[b + 1] = s;
+    }
+}
+
+// one warp per bucket: its members in ascending index (ballot compaction)
+__global__ void k_part_scatter(int32_t n, int32_t p, const int32_t* __restrict__ bucket,
+                               const int32_t* __restrict__ offsets, int32_t* __restrict__ order) {
+    const int32_t b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= p) return;
+    const int lane = threadIdx.x & 31;
+    int32_t pos = offsets[b];
+    for (int32_t t0 = 0; t0 < n; t0 += 32) {
+        const int32_t i = t0 + lane;
+        const bool f = i < n && bucket[i] == b;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (f) order[pos + __popc(bal & ((1u << lane) - 1u))] = i;
+        pos += __popc(bal);
+    }
+}
+
+}  // namespace
+
+int partition_device(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_t* key_b,
+                     int32_t p, int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                     cudaStream_t stream) {
+    const int64_t M = (int64_t)p * (p - 1);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return o;
+    };
+    const size_t oK = carve(8ull * (n + 1)), oRank = carve(4ull * (n + 1)), oY = carve(8ull * (M + 1)),
+                 oYs = carve(8ull * (M + 1)), oPiv = carve(8ull * p), oBucket = carve(4ull * (n + 1)),
+                 oCount = carve(4ull * p);
+    void* ws = nullptr;
+    SAD_RET(workspace(ctx, WS_PART, off, stream, &ws));
+    char* w = (char*)ws;
+    uint64_t* K = (uint64_t*)(w + oK);
+    int32_t* rank = (int32_t*)(w + oRank);
+    uint64_t* Y = (uint64_t*)(w + oY);
+    uint64_t* Ys = (uint64_t*)(w + oYs);
+    uint64_t* piv = (uint64_t*)(w + oPiv);
+    int32_t* bucket = (int32_t*)(w + oBucket);
+    int32_t* count = (int32_t*)(w + oCount);
+    SAD_CUDA(cudaMemsetAsync(count, 0, 4ull * p, stream));
+    if (n == 0) {
+        SAD_CUDA(cudaMemsetAsync(bucket_offsets, 0, 4ull * (p + 1), stream));
+        if (pivot_idx && p > 1) SAD_CUDA(cudaMemsetAsync(pivot_idx, 0xff, 4ull * (p - 1), stream));
+        return SAD_OK;
+    }
+    const int nb = (n + 255) / 256;
+    k_part_keys<<<nb, 256, 0, stream>>>(n, key_a, key_b, K, ctx->d_status);
+    SAD_CUDA(cudaGetLastError());
+    if (p > 1) {
+        const int64_t wmax = (n + p - 1) / p + 1;
+        dim3 g((unsigned)p, (unsigned)((wmax + 255) / 256));
+        k_part_block_rank<<<g, 256, 0, stream>>>(n, p, K, rank);
+        SAD_CUDA(cudaGetLastError());
+        SAD_CUDA(cudaMemsetAsync(Y, 0xff, 8ull * M, stream));
+        k_part_samples<<<nb, 256, 0, stream>>>(n, p, K, rank, Y);
+        SAD_CUDA(cudaGetLastError());
+        k_part_sample_rank<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>((int32_t)M, Y, Ys);
+        SAD_CUDA(cudaGetLastError());
+        k_part_pivots<<<(p - 1 + 255) / 256, 256, 0, stream>>>(n, p, Ys, piv, pivot_idx);
+        SAD_CUDA(cudaGetLastError());
+    }
+    k_part_bucket<<<nb, 256, 0, stream>>>(n, p, K, piv, bucket, count);
+    SAD_CUDA(cudaGetLastError());
+    k_part_offsets<<<1, 32, 0, stream>>>(p, count, bucket_offsets);
+    SAD_CUDA(cudaGetLastError());
+    k_part_scatter<<<(p + 7) / 8, 256, 0, stream>>>(n, p, bucket, bucket_offsets, order);
+    SAD_CUDA(cudaGetLastError());
+    return SAD_OK;
+}
+
+}  // namespace sad
+
+extern "C" int sad_partition(sad_ctx* ctx_in, int32_t n, const int32_t* key_a,
+                             const int32_t* key_b, int32_t p, int32_t* bucket_offsets,
+                             int32_t* order, int32_t* pivot_idx, int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(n >= 0, SAD_EINVAL, "n = %d < 0", n);
+    SAD_CHECK(p >= 1 && p <= kMaxPartitionP, SAD_EINVAL, "p = %d outside 1..%d", p, kMaxPartitionP);
+    SAD_CHECK(bucket_offsets && (n == 0 || (order && key_a && key_b)), SAD_EINVAL,
+              "a required pointer is NULL");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    SAD_RET(status_clear(ctx, stream));
+    const int32_t* dka = key_a;
+    const int32_t* dkb = key_b;
+    int32_t *dbo = bucket_offsets, *dord = order, *dpiv = pivot_idx;
+    if (mem == SAD_MEM_HOST) {
+        void* st = nullptr;
+        const size_t nn = (size_t)n + 1;
+        SAD_RET(workspace(ctx, WS_PART_OUT, 4 * (nn * 3 + (size_t)p * 2 + 8) + 1024, stream, &st));
+        int32_t* s = (int32_t*)st;
+        int32_t* ska = s;
+        int32_t* skb = ska + nn;
+        dord = skb + nn;
+        dbo = dord + nn;
+        dpiv = pivot_idx ? dbo + p + 1 : nullptr;
+        if (n > 0) {
+            SAD_CUDA(cudaMemcpyAsync(ska, key_a, 4ull * n, cudaMemcpyHostToDevice, stream));
+            SAD_CUDA(cudaMemcpyAsync(skb, key_b, 4ull * n, cudaMemcpyHostToDevice, stream));
+        }
+        dka = ska;
+        dkb = skb;
+    }
+    SAD_RET(partition_device(ctx, n, dka, dkb, p, dbo, dord, dpiv, stream));
+    if (mem == SAD_MEM_HOST) {
+        SAD_CUDA(cudaMemcpyAsync(bucket_offsets, dbo, 4ull * (p + 1), cudaMemcpyDeviceToHost, stream));
+        if (n > 0) SAD_CUDA(cudaMemcpyAsync(order, dord, 4ull * n, cudaMemcpyDeviceToHost, stream));
+        if (pivot_idx && p > 1)
+            SAD_CUDA(cudaMemcpyAsync(pivot_idx, dpiv, 4ull * (p - 1), cudaMemcpyDeviceToHost, stream));
+    }
+    SAD_RET(status_check(ctx, stream));
+    uint32_t s = *ctx->h_status;
+    SAD_CHECK(!(s & STATUS_BAD_KEY), SAD_EINVAL,
+              "a rank key violates 0 <= key_a <= key_b, 1 <= key_b <= 65536");
+    return SAD_OK;
+}

@@ -1,0 +1,138 @@
+// Internal runtime shared by the CUDA translation units of libsad: error
+// reporting, the per-device context with its cached workspaces, host/device
+// staging and the device-resident copy of a sequence set.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "sad.h"
+
+namespace sad {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define SAD_CUDA(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            ::sad::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, \
+                             __LINE__);                                                     \
+            return SAD_ECUDA;                                                               \
+        }                                                                                   \
+    } while (0)
+
+#define SAD_CHECK(cond, code, ...)            \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::sad::set_error(__VA_ARGS__);    \
+            return (code);                    \
+        }                                     \
+    } while (0)
+
+#define SAD_RET(expr)              \
+    do {                           \
+        int _rc = (expr);          \
+        if (_rc != SAD_OK) return _rc; \
+    } while (0)
+
+// Bits of the device status word (set by kernels with atomicOr).
+enum : uint32_t {
+    STATUS_BAD_RESIDUE = 1u << 0,   // a residue code >= alphabet
+    STATUS_TIMEOUT = 1u << 1,       // a bounded wait gave up
+    STATUS_CAPACITY = 1u << 2,      // an internal capacity was exceeded
+};
+
+// Workspace slots; each slot is a grow-only device buffer owned by a context.
+enum Slot : int {
+    WS_RES_STAGE = 0,  // host-mode residue staging
+    WS_OFFS,           // int64 offsets copy
+    WS_RES_PAD,        // 16-byte aligned residues
+    WS_SEQ_META,       // padded offsets, lengths
+    WS_COUNTS,         // uint8 counts
+    WS_PLANES,         // threshold planes
+    WS_EXCESS,         // excess lists
+    WS_HEAVY,          // heavy index/list, residual matrix
+    WS_KMER_MISC,      // per-sequence aux arrays
+    WS_RANK_OUT,       // staging of rank outputs (host mode)
+    WS_PART,           // partition scratch
+    WS_PART_OUT,       // staging of partition outputs
+    WS_SCORE_PLAN,     // Gotoh work items and per-bucket tables
+    WS_SCORE_SCRATCH,  // strip-boundary scratch of the Gotoh kernels
+    WS_SCORE_OUT,      // staging of scores (host mode)
+    WS_PIPE,           // pipeline intermediates
+    WS_NUM_SLOTS
+};
+
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace sad
+
+struct sad_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+    sad::Buffer ws[sad::WS_NUM_SLOTS];
+    uint32_t* d_status = nullptr;     // device status word
+    uint32_t* h_status = nullptr;     // pinned mirror
+    void* h_pinned = nullptr;         // small pinned staging area
+    size_t h_pinned_bytes = 0;
+    std::mutex mu;
+};
+
+namespace sad {
+
+// Resolve ctx (NULL -> default context of the current device) and make its
+// device current.
+int resolve_ctx(sad_ctx* in, sad_ctx** out);
+
+// Grow-only workspace of a slot; synchronises `stream` before freeing an old
+// buffer. Returns SAD_OK and the pointer, or SAD_ENOMEM.
+int workspace(sad_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, void** out);
+
+// Pinned host scratch of at least `bytes` (grow-only).
+int pinned(sad_ctx* ctx, size_t bytes, cudaStream_t stream, void** out);
+
+// Device status word helpers: clear before a stage, read (synchronising
+// `stream`) after it and turn set bits into an error code.
+int status_clear(sad_ctx* ctx, cudaStream_t stream);
+int status_check(sad_ctx* ctx, cudaStream_t stream);
+
+// Copy `bytes` from an argument buffer in `mem` space into device memory of a
+// workspace slot (host mode), or return the device pointer itself.
+int arg_to_device(sad_ctx* ctx, Slot slot, const void* arg, size_t bytes, int32_t mem,
+                  cudaStream_t stream, const void** dev);
+
+// Read a small argument array in `mem` space into host memory.
+int arg_to_host(const void* arg, size_t bytes, int32_t mem, cudaStream_t stream, void* host);
+
+// Device-resident sequence set: every sequence starts on a 16-byte boundary
+// and is followed by at least 16 bytes of zero padding.
+struct DevSeqs {
+    int32_t n = 0;
+    int32_t alphabet = 0;
+    const uint8_t* res = nullptr;   // padded residues
+    const int64_t* pad_off = nullptr;  // n+1 padded starts
+    const int32_t* len = nullptr;   // n lengths
+    std::vector<int64_t> h_off;     // host copy of the caller's offsets
+    std::vector<int32_t> h_len;     // host lengths
+    int32_t max_len = 0;
+};
+
+// Validate a sequence set and build its device-resident copy (residue codes
+// are checked on the device; a bad code sets STATUS_BAD_RESIDUE).
+int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t stream,
+                 DevSeqs* out);
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace sad

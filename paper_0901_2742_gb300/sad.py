@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libsad (include/sad.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library. Arrays may be numpy arrays (host memory; the call is synchronous and
+returns numpy arrays) or CUDA torch tensors (device memory; results are CUDA
+tensors, enqueued on the current torch stream unless ``stream`` is given).
+There is no CPU fallback: if the library is missing or the GPU unusable, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SAD_OK, SAD_EINVAL, SAD_ENOMEM, SAD_ECUDA, SAD_ETIMEOUT = 0, -1, -2, -3, -4
+SAD_EBUSY, SAD_ERANGE, SAD_ENOTFOUND, SAD_ECANCELED = -5, -6, -7, -8
+MEM_HOST, MEM_DEVICE = 0, 1
+PER_BUCKET, PERSISTENT = 0, 1
+
+_NAMES = {SAD_EINVAL: "EINVAL", SAD_ENOMEM: "ENOMEM", SAD_ECUDA: "ECUDA", SAD_ETIMEOUT: "ETIMEOUT",
+          SAD_EBUSY: "EBUSY", SAD_ERANGE: "ERANGE", SAD_ENOTFOUND: "ENOTFOUND",
+          SAD_ECANCELED: "ECANCELED"}
+
+
+class SadError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sad error {code} ({_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class SeqSet(ctypes.Structure):
+    _fields_ = [("residues", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("alphabet", ctypes.c_int32)]
+
+
+class KmerParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("kmer_alphabet", ctypes.c_int32),
+                ("class_map", ctypes.c_void_p), ("cap", ctypes.c_int32), ("p", ctypes.c_int32)]
+
+
+class RankOut(ctypes.Structure):
+    _fields_ = [("dloc", ctypes.c_void_p), ("dcen", ctypes.c_void_p), ("la", ctypes.c_void_p),
+                ("ga", ctypes.c_void_p), ("key_a", ctypes.c_void_p), ("key_b", ctypes.c_void_p),
+                ("A", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libsad.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsad.so is not built ({path}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "sad_ctx_create": (ctypes.c_int, [i32, ctypes.POINTER(ctypes.c_void_p)]),
+        "sad_ctx_destroy": (ctypes.c_int, [P]),
+        "sad_last_error": (ctypes.c_char_p, []),
+        "sad_version": (ctypes.c_char_p, []),
+        "sad_kmer_rank": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), ctypes.POINTER(KmerParams),
+                                         ctypes.POINTER(RankOut), i32, P]),
+        "sad_partition": (ctypes.c_int, [P, i32, P, P, i32, P, P, P, i32, P]),
+        "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
+        "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
+                                                  i32, P, P, i64, i32, P]),
+        "sad_pipeline": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), ctypes.POINTER(KmerParams), P, i32,
+                                        i32, i32, ctypes.POINTER(RankOut), P, P, P, P, i64, i32, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != SAD_OK:
+        raise SadError(rc, load().sad_last_error().decode(errors="replace"))
+
+
+def version() -> str:
+    return load().sad_version().decode()
+
+
+# ---- argument helpers -------------------------------------------------------
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return x.data_ptr() if x.numel() else None
+    return x.ctypes.data if x.size else None
+
+
+def _host(x, dtype):
+    return np.ascontiguousarray(np.asarray(x, dtype=dtype))
+
+
+def _mode(*arrays) -> int:
+    dev = [_is_torch(a) and a.is_cuda for a in arrays if a is not None]
+    if any(dev) and not all(dev):
+        raise ValueError("mix of host and device arrays")
+    return MEM_DEVICE if dev and all(dev) else MEM_HOST
+
+
+def _stream(stream, mem):
+    if mem == MEM_HOST:
+        return stream
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _empty(shape, dtype, mem, like=None):
+    if mem == MEM_HOST:
+        return np.zeros(shape, dtype=dtype)
+    torch = _torch()
+    tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint64: torch.uint64,
+           np.uint8: torch.uint8}[dtype]
+    dev = like.device if like is not None else "cuda"
+    return torch.empty(shape, dtype=tdt, device=dev)
+
+
+def _as(x, dtype, mem):
+    if mem == MEM_DEVICE:
+        torch = _torch()
+        tdt = {np.int32: torch.int32, np.int64: torch.int64, np.uint8: torch.uint8}[dtype]
+        return x.to(tdt).contiguous()
+    return _host(x, dtype)
+
+
+def _seqset(residues, offsets, alphabet):
+    n = (offsets.shape[0] if _is_torch(offsets) else len(offsets)) - 1
+    return SeqSet(_ptr(residues), _ptr(offsets), n, alphabet)
+
+
+class Context:
+    """An explicit sad_ctx (owns cached workspaces) bound to one device."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().sad_ctx_create(device, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _check(load().sad_ctx_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ctx(ctx):
+    return None if ctx is None else ctx.handle
+
+
+# ---- the calls --------------------------------------------------------------
+
+def kmer_rank(residues, offsets, alphabet: int, k: int, p: int, cap: int = 0,
+              kmer_alphabet: int | None = None, class_map=None, want_A: bool = False, ctx=None,
+              stream=None) -> dict:
+    """sad_kmer_rank: dict(dloc, dcen, la, ga, key_a, key_b, A)."""
+    mem = _mode(residues, offsets)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    n = offs.shape[0] - 1
+    cm = None if class_map is None else _host(class_map, np.uint8)
+    ka = kmer_alphabet if kmer_alphabet is not None else alphabet
+    params = KmerParams(k, ka, None if cm is None else cm.ctypes.data, cap, p)
+    out = dict(dloc=_empty(max(n, 0), np.uint64, mem, offs), dcen=_empty(max(n, 0), np.uint64, mem, offs),
+               la=_empty(p, np.int32, mem, offs), ga=_empty(1, np.int32, mem, offs),
+               key_a=_empty(max(n, 0), np.int32, mem, offs), key_b=_empty(max(n, 0), np.int32, mem, offs),
+               A=_empty((n, n), np.int32, mem, offs) if want_A else None)
+    ro = RankOut(*[_ptr(out[x]) if out[x] is not None and (n > 0 or x in ("la", "ga")) else None
+                   for x in ("dloc", "dcen", "la", "ga", "key_a", "key_b", "A")])
+    # the C side requires non-NULL output pointers even for n == 0
+    dummy = _empty(8, np.int64, mem, offs)
+    for f in ("dloc", "dcen", "key_a", "key_b"):
+        if getattr(ro, f) is None:
+            setattr(ro, f, _ptr(dummy))
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_kmer_rank(_ctx(ctx), ctypes.byref(ss), ctypes.byref(params), ctypes.byref(ro), mem,
+                                _stream(stream, mem)))
+    out["ga"] = int(out["ga"][0]) if mem == MEM_HOST else out["ga"]
+    return out
+
+
+def partition(key_a, key_b, p: int, ctx=None, stream=None) -> dict:
+    """sad_partition: dict(bucket_offsets, order, pivot_idx)."""
+    mem = _mode(key_a, key_b)
+    ka, kb = _as(key_a, np.int32, mem), _as(key_b, np.int32, mem)
+    n = ka.shape[0]
+    bo = _empty(p + 1, np.int32, mem, ka)
+    order = _empty(n, np.int32, mem, ka)
+    piv = _empty(max(p - 1, 0), np.int32, mem, ka)
+    _check(load().sad_partition(_ctx(ctx), n, _ptr(ka), _ptr(kb), p, _ptr(bo), _ptr(order),
+                                _ptr(piv) if p > 1 else None, mem, _stream(stream, mem)))
+    return dict(bucket_offsets=bo, order=order, pivot_idx=piv)
+
+
+def scores_size(bucket_offsets) -> int:
+    mem = _mode(bucket_offsets)
+    bo = _as(bucket_offsets, np.int32, mem)
+    t = ctypes.c_int64()
+    _check(load().sad_scores_size(_ptr(bo), bo.shape[0] - 1, mem, ctypes.byref(t)))
+    return t.value
+
+
+def bucket_pair_scores(residues, offsets, alphabet: int, bucket_offsets, order, subst,
+                       gap_open: int, gap_extend: int, mode: int = PERSISTENT, capacity=None, ctx=None,
+                       stream=None):
+    """sad_bucket_pair_scores: (score_offsets int64[p+1], scores int32[total])."""
+    mem = _mode(residues, offsets, bucket_offsets, order)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    bo, od = _as(bucket_offsets, np.int32, mem), _as(order, np.int32, mem)
+    p = bo.shape[0] - 1
+    S = _host(subst, np.int8)
+    total = scores_size(bo)
+    cap = total if capacity is None else capacity
+    so = _empty(p + 1, np.int64, mem, bo)
+    sc = _empty(max(cap, 1), np.int32, mem, bo)
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_bucket_pair_scores(_ctx(ctx), ctypes.byref(ss), _ptr(bo), _ptr(od), p, S.ctypes.data,
+                                         gap_open, gap_extend, mode, _ptr(so), _ptr(sc), cap, mem,
+                                         _stream(stream, mem)))
+    return so, sc[:total]
+
+
+def pipeline(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: int, gap_extend: int,
+             cap: int = 0, kmer_alphabet: int | None = None, class_map=None, mode: int = PERSISTENT,
+             capacity: int | None = None, want_rank: bool = True, ctx=None, stream=None, out=None) -> dict:
+    """sad_pipeline: rank outputs, bucket layout and scores in one call.
+
+    ``out`` may carry preallocated buffers (keys as in the returned dict) so
+    that repeated calls reuse them.
+    """
+    mem = _mode(residues, offsets)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    n = offs.shape[0] - 1
+    cm = None if class_map is None else _host(class_map, np.uint8)
+    ka = kmer_alphabet if kmer_alphabet is not None else alphabet
+    params = KmerParams(k, ka, None if cm is None else cm.ctypes.data, cap, p)
+    S = _host(subst, np.int8)
+    if capacity is None:
+        capacity = n * (n + 1) // 2  # any layout fits
+    o = dict(out or {})
+    o.setdefault("bucket_offsets", _empty(p + 1, np.int32, mem, offs))
+    o.setdefault("order", _empty(max(n, 1), np.int32, mem, offs))
+    o.setdefault("score_offsets", _empty(p + 1, np.int64, mem, offs))
+    o.setdefault("scores", _empty(max(capacity, 1), np.int32, mem, offs))
+    ro = None
+    if want_rank:
+        for key, shape, dt in (("dloc", n, np.uint64), ("dcen", n, np.uint64), ("la", p, np.int32),
+                               ("ga", 1, np.int32), ("key_a", n, np.int32), ("key_b", n, np.int32)):
+            o.setdefault(key, _empty(max(shape, 1), dt, mem, offs))
+        ro = RankOut(_ptr(o["dloc"]), _ptr(o["dcen"]), _ptr(o["la"]), _ptr(o["ga"]), _ptr(o["key_a"]),
+                     _ptr(o["key_b"]), None)
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_pipeline(_ctx(ctx), ctypes.byref(ss), ctypes.byref(params), S.ctypes.data, gap_open,
+                               gap_extend, mode, ctypes.byref(ro) if ro is not None else None,
+                               _ptr(o["bucket_offsets"]), _ptr(o["order"]), _ptr(o["score_offsets"]),
+                               _ptr(o["scores"]), capacity, mem, _stream(stream, mem)))
+    return o

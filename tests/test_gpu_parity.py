@@ -1,0 +1,235 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Every output is an integer, so the bar is bit-exact: similarity numerators,
+fixed-point D sums, ancestors, rank keys, pivots, the bucket layout and every
+alignment score. Inputs are the seeded synthetic families (tree-evolved
+protein-like sequences) plus adversarial cases.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0901_2742_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+@pytest.fixture(scope="module")
+def sad():
+    from paper_0901_2742_gb300 import build, sad as s
+    build.build()
+    s.load()
+    return s
+
+
+def oracle_all(w, key=None):
+    if key is None or key not in _cache:
+        r = oracle.kmer_rank(w.residues, w.offsets, w.alphabet, w.k, w.p, class_map=w.class_map,
+                             kmer_alphabet=w.kmer_alphabet, want_A=w.n <= 2000)
+        pt = oracle.partition(r["key_a"], r["key_b"], w.p)
+        so, sc = oracle.bucket_pair_scores(w.residues, w.offsets, pt["bucket_offsets"], pt["order"],
+                                           w.subst, w.gap_open, w.gap_extend)
+        if key is None:
+            return (r, pt, so, sc)
+        _cache[key] = (r, pt, so, sc)
+    return _cache[key]
+
+
+def to_np(x):
+    if hasattr(x, "cpu"):
+        return x.cpu().numpy()
+    return np.asarray(x)
+
+
+def assert_rank_equal(got, want, check_A=True):
+    for f in ("dloc", "dcen", "la", "key_a", "key_b"):
+        np.testing.assert_array_equal(to_np(got[f]), want[f], err_msg=f)
+    assert int(np.asarray(to_np(got["ga"])).reshape(-1)[0]) == want["ga"]
+    if check_A and got.get("A") is not None and want["A"] is not None:
+        np.testing.assert_array_equal(to_np(got["A"]), want["A"])
+
+
+def run_gpu(sad, w, mode, device=False):
+    res, offs = w.residues, w.offsets
+    if device:
+        import torch
+        res = torch.from_numpy(res).cuda()
+        offs = torch.from_numpy(offs).cuda()
+    r = sad.kmer_rank(res, offs, w.alphabet, w.k, w.p, cap=w.cap, kmer_alphabet=w.kmer_alphabet,
+                      class_map=w.class_map, want_A=w.n <= 2000)
+    pt = sad.partition(r["key_a"], r["key_b"], w.p)
+    so, sc = sad.bucket_pair_scores(res, offs, w.alphabet, pt["bucket_offsets"], pt["order"], w.subst,
+                                    w.gap_open, w.gap_extend, mode=mode)
+    if device:
+        import torch
+        torch.cuda.synchronize()
+    return r, pt, so, sc
+
+
+@pytest.mark.parametrize("device", [False, True], ids=["host", "device"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["per_bucket", "persistent"])
+def test_small_family_full_parity(sad, device, mode):
+    w = synth.workload(1)
+    want = oracle_all(w, "cfg1")
+    r, pt, so, sc = run_gpu(sad, w, mode, device)
+    assert_rank_equal(r, want[0])
+    np.testing.assert_array_equal(to_np(pt["bucket_offsets"]), want[1]["bucket_offsets"])
+    np.testing.assert_array_equal(to_np(pt["order"]), want[1]["order"])
+    np.testing.assert_array_equal(to_np(pt["pivot_idx"]), want[1]["pivot_idx"])
+    np.testing.assert_array_equal(to_np(so), want[2])
+    np.testing.assert_array_equal(to_np(sc), want[3])
+
+
+@pytest.mark.parametrize("seed", range(1, 9))
+def test_small_family_seed_sweep(sad, seed):
+    w = synth.workload(1, seed=seed)
+    want = oracle_all(w, f"cfg1s{seed}")
+    r, pt, so, sc = run_gpu(sad, w, 1)
+    assert_rank_equal(r, want[0])
+    np.testing.assert_array_equal(pt["order"], want[1]["order"])
+    np.testing.assert_array_equal(sc, want[3])
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["per_bucket", "persistent"])
+def test_paper_scale_plain_full_parity(sad, mode):
+    """N = 2000, L ~ N(316, 60), k = 3, p = 16: every output of every stage."""
+    w = synth.workload(2)
+    want = oracle_all(w, "cfg2")
+    r, pt, so, sc = run_gpu(sad, w, mode)
+    assert_rank_equal(r, want[0])
+    np.testing.assert_array_equal(pt["bucket_offsets"], want[1]["bucket_offsets"])
+    np.testing.assert_array_equal(pt["order"], want[1]["order"])
+    np.testing.assert_array_equal(so, want[2])
+    np.testing.assert_array_equal(sc, want[3])
+
+
+def test_pipeline_matches_oracle(sad):
+    w = synth.workload(2)
+    want = oracle_all(w, "cfg2")
+    for mem in ("host", "device"):
+        res, offs = w.residues, w.offsets
+        if mem == "device":
+            import torch
+            res, offs = torch.from_numpy(res).cuda(), torch.from_numpy(offs).cuda()
+        o = sad.pipeline(res, offs, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend,
+                         cap=w.cap, mode=1)
+        total = int(want[2][-1])
+        np.testing.assert_array_equal(to_np(o["bucket_offsets"]), want[1]["bucket_offsets"])
+        np.testing.assert_array_equal(to_np(o["order"]), want[1]["order"])
+        np.testing.assert_array_equal(to_np(o["score_offsets"]), want[2])
+        np.testing.assert_array_equal(to_np(o["scores"])[:total], want[3])
+        np.testing.assert_array_equal(to_np(o["dcen"]), want[0]["dcen"])
+        np.testing.assert_array_equal(to_np(o["key_a"]), want[0]["key_a"])
+
+
+def make_workload(seqs, p, k=3, alphabet=20, subst=None, go=-11, ge=-1, class_map=None, ka=None):
+    res, offs = synth.pack(seqs)
+    S = synth.subst_matrix(99, alphabet) if subst is None else subst
+    return synth.Workload("adhoc", res, offs, alphabet, S, go, ge, k, p, 0, ka or alphabet, class_map)
+
+
+def compare_all(sad, w, modes=(0, 1)):
+    want = oracle_all(w)
+    for mode in modes:
+        r, pt, so, sc = run_gpu(sad, w, mode)
+        assert_rank_equal(r, want[0])
+        np.testing.assert_array_equal(pt["order"], want[1]["order"])
+        np.testing.assert_array_equal(pt["bucket_offsets"], want[1]["bucket_offsets"])
+        np.testing.assert_array_equal(sc, want[3])
+
+
+def test_edge_short_and_empty_sequences(sad):
+    rng = np.random.default_rng(1)
+    seqs = [[], [3], [1, 2], [1, 2, 3], list(rng.integers(0, 20, 40)), [], list(rng.integers(0, 20, 5)),
+            [7, 7, 7]]
+    compare_all(sad, make_workload(seqs, p=3))
+
+
+def test_edge_fewer_sequences_than_buckets(sad):
+    rng = np.random.default_rng(2)
+    for n in (1, 2, 5):
+        seqs = [list(rng.integers(0, 20, rng.integers(10, 60))) for _ in range(n)]
+        compare_all(sad, make_workload(seqs, p=8))
+
+
+def test_edge_identical_sequences(sad):
+    seqs = [list(synth.uniform_residues(5, 90))] * 37
+    compare_all(sad, make_workload(seqs, p=5))
+
+
+def test_edge_counts_above_255_use_the_residual(sad):
+    # homopolymers and short-period repeats: k-mer counts far above 255
+    rng = np.random.default_rng(3)
+    seqs = [[4] * 700, [4] * 300 + [5] * 300, [4, 5] * 350, [4] * 260, list(rng.integers(0, 20, 300)),
+            [4] * 1000 + list(rng.integers(0, 20, 50)), [5] * 600]
+    compare_all(sad, make_workload(seqs, p=2))
+
+
+def test_edge_long_sequences_strip_mining(sad):
+    # queries longer than one strip of the widest kernel variant
+    rng = np.random.default_rng(4)
+    seqs = [list(rng.integers(0, 20, L)) for L in (1100, 1500, 2000, 2000, 1700, 900, 50, 1)]
+    compare_all(sad, make_workload(seqs, p=1))
+
+
+def test_edge_odd_p_and_p_one(sad):
+    w = synth.workload(1, seed=77)
+    for p in (1, 3, 7):
+        w.p = p
+        compare_all(sad, w)
+
+
+def test_compressed_alphabet_k4(sad):
+    """Six-letter compressed alphabet, k = 4 (the large-batch k-mer setting) on a small set."""
+    w = synth.workload(4, n_override=300)
+    w.cap = 0
+    compare_all(sad, w, modes=(1,))
+
+
+@pytest.mark.parametrize("params", [(-11, -1), (0, -1), (-3, 0), (0, 0), (-40, -7)])
+def test_gotoh_random_buckets_and_gap_costs(sad, params):
+    go, ge = params
+    rng = np.random.default_rng(abs(go) * 10 + abs(ge))
+    lens = list(rng.integers(0, 6, 10)) + list(rng.integers(1, 400, 40)) + [777, 1025, 1300]
+    seqs = [list(rng.integers(0, 20, L)) for L in lens]
+    res, offs = synth.pack(seqs)
+    n = len(seqs)
+    order = rng.permutation(n).astype(np.int32)
+    bo = np.array([0, 1, 1, 12, 30, n], np.int32)   # includes an empty and a singleton bucket
+    S = synth.subst_matrix(5)
+    want_so, want_sc = oracle.bucket_pair_scores(res, offs, bo, order, S, go, ge)
+    for mode in (0, 1):
+        so, sc = sad.bucket_pair_scores(res, offs, 20, bo, order, S, go, ge, mode=mode)
+        np.testing.assert_array_equal(so, want_so)
+        np.testing.assert_array_equal(sc, want_sc)
+
+
+def test_partition_random_keys_with_ties(sad):
+    rng = np.random.default_rng(8)
+    for n, p in ((500, 7), (64, 4), (3, 5), (2000, 16), (1000, 1), (4096, 64)):
+        kb = rng.integers(1, 40, n).astype(np.int32)
+        ka = (rng.random(n) * (kb + 1)).astype(np.int32).clip(0, kb)
+        want = oracle.partition(ka, kb, p)
+        got = sad.partition(ka, kb, p)
+        np.testing.assert_array_equal(got["bucket_offsets"], want["bucket_offsets"])
+        np.testing.assert_array_equal(got["order"], want["order"])
+        np.testing.assert_array_equal(got["pivot_idx"], want["pivot_idx"])
+
+
+def test_bad_residue_is_reported(sad):
+    res = np.array([1, 2, 30, 4], np.uint8)
+    offs = np.array([0, 4], np.int64)
+    with pytest.raises(sad.SadError) as e:
+        sad.kmer_rank(res, offs, 20, 2, 1)
+    assert e.value.code == sad.SAD_EINVAL
+
+
+def test_scores_capacity_too_small(sad):
+    w = synth.workload(1)
+    want = oracle_all(w, "cfg1")
+    bo, order = want[1]["bucket_offsets"], want[1]["order"]
+    with pytest.raises(sad.SadError) as e:
+        sad.bucket_pair_scores(w.residues, w.offsets, 20, bo, order, w.subst, -11, -1, capacity=10)
+    assert e.value.code == sad.SAD_ERANGE
