@@ -131,6 +131,28 @@ const char* sad_last_error(void);
 /* Library version string. */
 const char* sad_version(void);
 
+/* ---- tracing ------------------------------------------------------------ */
+
+/* Stages whose device time the tracer records (CUDA events on the call's
+ * stream around the stage's kernels). */
+#define SAD_STAGE_PREPARE 0    /* staging and padding of the sequences */
+#define SAD_STAGE_COUNT 1      /* k-mer counts, planes, excess lists, residual matrix */
+#define SAD_STAGE_ALLPAIRS 2   /* all-pairs similarity with the fused D sums */
+#define SAD_STAGE_RANK 3       /* ancestors and rank keys */
+#define SAD_STAGE_PARTITION 4  /* regular-sampling partition */
+#define SAD_STAGE_SCORES 5     /* alignment-score kernels */
+#define SAD_NUM_STAGES 6
+
+/* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
+ * accumulated times. */
+int sad_trace_enable(sad_ctx* ctx, int32_t on);
+/* Wait for the recorded events, then write per stage the accumulated device
+ * milliseconds (ms[s]) and the number of traced intervals (counts[s]) for
+ * s < nstages, and clear them. */
+int sad_trace_read(sad_ctx* ctx, double* ms, int32_t* counts, int32_t nstages);
+/* Number of kernels this library has launched in this process. */
+uint64_t sad_launch_count(void);
+
 /* ---- stage 1: k-mer rank ----------------------------------------------- */
 
 /* All-pairs k-mer similarity and the rank keys (Section 2 equations r_ij,

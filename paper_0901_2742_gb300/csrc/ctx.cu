@@ -1,5 +1,6 @@
 // Context, workspaces, error reporting and sequence staging for libsad.
 #include <cstdarg>
+#include <atomic>
 #include <cstring>
 
 #include "sad_internal.cuh"
@@ -8,6 +9,7 @@ namespace sad {
 
 namespace {
 thread_local char g_err[1024] = "";
+std::atomic<uint64_t> g_launches{0};
 std::mutex g_default_mu;
 sad_ctx* g_default[64] = {nullptr};
 }  // namespace
@@ -20,6 +22,36 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_err[0] = 0; }
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t take_event(sad_ctx* ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+TraceScope::TraceScope(sad_ctx* ctx, int stage, cudaStream_t stream)
+    : ctx_(ctx), stage_(stage), stream_(stream) {
+    if (!ctx_ || !ctx_->trace_on) return;
+    cudaEvent_t b = take_event(ctx_);
+    end_ = take_event(ctx_);
+    if (!b || !end_) return;
+    cudaEventRecord(b, stream_);
+    ctx_->trace[stage_].pending.push_back({b, end_});
+}
+
+TraceScope::~TraceScope() {
+    if (end_) cudaEventRecord(end_, stream_);
+}
 
 static int ctx_init(int32_t device, sad_ctx* c) {
     int ndev = 0;
@@ -227,9 +259,10 @@ int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t st
         const void* doff = nullptr;
         SAD_RET(arg_to_device(ctx, WS_OFFS, s->offsets, sizeof(int64_t) * (n + 1), mem, stream,
                               &doff));
+        TraceScope ts(ctx, SAD_STAGE_PREPARE, stream);
         k_gather_pad<<<n, 128, 0, stream>>>((const uint8_t*)src, (const int64_t*)doff, d_pad,
                                             s->alphabet, (uint8_t*)dres, ctx->d_status);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
     }
     out->res = (const uint8_t*)dres;
     out->pad_off = d_pad;
@@ -269,6 +302,59 @@ int sad_ctx_destroy(sad_ctx* ctx) {
 }
 
 const char* sad_last_error(void) { return sad::g_err; }
+
+uint64_t sad_launch_count(void) { return sad::g_launches.load(); }
+
+int sad_trace_enable(sad_ctx* ctx_in, int32_t on) {
+    sad::clear_error();
+    sad_ctx* ctx = nullptr;
+    SAD_RET(sad::resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (auto& st : ctx->trace) {
+        for (auto& pr : st.pending) {
+            cudaEventSynchronize(pr.second);
+            ctx->event_pool.push_back(pr.first);
+            ctx->event_pool.push_back(pr.second);
+        }
+        st.pending.clear();
+        st.ms = 0;
+        st.count = 0;
+    }
+    ctx->trace_on = on != 0;
+    return SAD_OK;
+}
+
+int sad_trace_read(sad_ctx* ctx_in, double* ms, int32_t* counts, int32_t nstages) {
+    sad::clear_error();
+    SAD_CHECK(ms && counts && nstages >= 0, SAD_EINVAL, "invalid arguments");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(sad::resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (int s = 0; s < SAD_NUM_STAGES; s++) {
+        auto& st = ctx->trace[s];
+        for (auto& pr : st.pending) {
+            SAD_CUDA(cudaEventSynchronize(pr.second));
+            float t = 0;
+            SAD_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+            st.ms += t;
+            st.count++;
+            ctx->event_pool.push_back(pr.first);
+            ctx->event_pool.push_back(pr.second);
+        }
+        st.pending.clear();
+        if (s < nstages) {
+            ms[s] = st.ms;
+            counts[s] = st.count;
+        }
+        st.ms = 0;
+        st.count = 0;
+    }
+    for (int s = SAD_NUM_STAGES; s < nstages; s++) {
+        ms[s] = 0;
+        counts[s] = 0;
+    }
+    return SAD_OK;
+}
 
 const char* sad_version(void) { return "sad-gb300 0.1 (sm_103a)"; }
 

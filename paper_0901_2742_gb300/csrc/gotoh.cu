@@ -311,8 +311,9 @@ int gotoh_launch(sad_ctx* ctx, const DevSeqs& S, const GotohLaunch& L, cudaStrea
     SAD_CHECK(smem <= ctx->smem_optin, SAD_EINVAL, "query profile of %zu bytes exceeds shared memory",
               smem);
     SAD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TraceScope ts(ctx, SAD_STAGE_SCORES, stream);
     fn<<<grid, threads, smem, stream>>>(L.items, L.n_items, L.head, a);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     return SAD_OK;
 }
 

@@ -565,18 +565,22 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     int32_t* ex_tau = (int32_t*)exb;
     int32_t* ex_val = ex_tau + excap;
     const size_t smem = sizeof(uint32_t) * Vs;
+    int32_t H = 0;
+    {
+    TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
     if (smem > 48 * 1024)
         SAD_CUDA(cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_count<<<n, kCountThreads, smem, stream>>>(S.res, S.pad_off, S.len, k, A2, Vs, cm, T, cap,
                                                (uint8_t*)c8, planes, (const int64_t*)(dm + o_exoff),
                                                ex_tau, ex_val, d_nex, d_sT);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     k_heavy_index<<<1, 1024, 0, stream>>>(n, d_nex, d_hidx, d_hlist, d_H);
-    SAD_CUDA(cudaGetLastError());
-    int32_t H = 0;
+    SAD_LAUNCHED();
+    }
     SAD_CUDA(cudaMemcpyAsync(&H, d_H, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     SAD_CUDA(cudaStreamSynchronize(stream));
     if (H > 0) {
+        TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
         SAD_CHECK((int64_t)H * H <= (1ll << 29), SAD_ENOMEM,
                   "%d sequences have k-mer counts above %d; the residual matrix would need %lld "
                   "entries",
@@ -589,9 +593,11 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         const int grid = (int)std::min<int64_t>((npairs + 255) / 256, (int64_t)ctx->num_sms * 16);
         k_residual<<<grid, 256, 0, stream>>>(H, d_hlist, (const int64_t*)(dm + o_exoff), ex_tau,
                                              ex_val, d_nex, (int32_t*)rb);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
     }
     // all pairs
+    {
+    TraceScope ts(ctx, SAD_STAGE_ALLPAIRS, stream);
     if (cap > 0) {
         SAD_RET(allpairs_planes(ctx, n, cap * Vs, planes, tab, out.dloc, out.dcen, out.A, stream));
     } else {
@@ -599,18 +605,20 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         const int64_t ntri = (int64_t)ntiles * (ntiles + 1) / 2;
         k_allpairs_u8<<<(unsigned)ntri, 256, 0, stream>>>(n, Vs, ntiles, (const uint8_t*)c8, d_sT,
                                                           tab, out.dloc, out.dcen, out.A);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
+    }
     }
     // ancestors and keys
+    TraceScope ts(ctx, SAD_STAGE_RANK, stream);
     k_local_ancestors<<<p, 256, 0, stream>>>(n, p, out.dloc, out.la);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     k_ga_sums<<<p, 256, 0, stream>>>(p, out.la, (const uint8_t*)c8, Vs, (uint32_t)T, tab, d_gsum);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     k_ga_select<<<1, 32, 0, stream>>>(p, out.la, d_gsum, out.ga);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     k_key_column<<<(n + 7) / 8, 256, 0, stream>>>(n, out.ga, (const uint8_t*)c8, Vs, (uint32_t)T,
                                                   tab, out.key_a, out.key_b);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     return SAD_OK;
 }
 

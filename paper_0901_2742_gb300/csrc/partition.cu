@@ -183,27 +183,28 @@ int partition_device(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_
         return SAD_OK;
     }
     const int nb = (n + 255) / 256;
+    TraceScope ts(ctx, SAD_STAGE_PARTITION, stream);
     k_part_keys<<<nb, 256, 0, stream>>>(n, key_a, key_b, K, ctx->d_status);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     if (p > 1) {
         const int64_t wmax = (n + p - 1) / p + 1;
         dim3 g((unsigned)p, (unsigned)((wmax + 255) / 256));
         k_part_block_rank<<<g, 256, 0, stream>>>(n, p, K, rank);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
         SAD_CUDA(cudaMemsetAsync(Y, 0xff, 8ull * M, stream));
         k_part_samples<<<nb, 256, 0, stream>>>(n, p, K, rank, Y);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
         k_part_sample_rank<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>((int32_t)M, Y, Ys);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
         k_part_pivots<<<(p - 1 + 255) / 256, 256, 0, stream>>>(n, p, Ys, piv, pivot_idx);
-        SAD_CUDA(cudaGetLastError());
+        SAD_LAUNCHED();
     }
     k_part_bucket<<<nb, 256, 0, stream>>>(n, p, K, piv, bucket, count);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     k_part_offsets<<<1, 32, 0, stream>>>(p, count, bucket_offsets);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     k_part_scatter<<<(p + 7) / 8, 256, 0, stream>>>(n, p, bucket, bucket_offsets, order);
-    SAD_CUDA(cudaGetLastError());
+    SAD_LAUNCHED();
     return SAD_OK;
 }
 

@@ -27,6 +27,14 @@ void clear_error();
         }                                                                                   \
     } while (0)
 
+// After a kernel launch: count it and surface launch errors.
+void note_launch();
+#define SAD_LAUNCHED()                      \
+    do {                                    \
+        ::sad::note_launch();               \
+        SAD_CUDA(cudaGetLastError());       \
+    } while (0)
+
 #define SAD_CHECK(cond, code, ...)            \
     do {                                      \
         if (!(cond)) {                        \
@@ -74,6 +82,12 @@ struct Buffer {
     size_t bytes = 0;
 };
 
+struct TraceStage {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    double ms = 0;
+    int32_t count = 0;
+};
+
 }  // namespace sad
 
 struct sad_ctx {
@@ -87,6 +101,9 @@ struct sad_ctx {
     void* h_pinned = nullptr;         // small pinned staging area
     size_t h_pinned_bytes = 0;
     std::mutex mu;
+    bool trace_on = false;
+    sad::TraceStage trace[SAD_NUM_STAGES];
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace sad {
@@ -134,5 +151,18 @@ int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t st
                  DevSeqs* out);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Records CUDA events around a stage on `stream` when the context traces.
+class TraceScope {
+  public:
+    TraceScope(sad_ctx* ctx, int stage, cudaStream_t stream);
+    ~TraceScope();
+
+  private:
+    sad_ctx* ctx_;
+    int stage_;
+    cudaStream_t stream_;
+    cudaEvent_t end_ = nullptr;
+};
 
 }  // namespace sad

@@ -76,6 +76,9 @@ def load():
         "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
                                                   i32, P, P, i64, i32, P]),
+        "sad_trace_enable": (ctypes.c_int, [P, i32]),
+        "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
+        "sad_launch_count": (ctypes.c_uint64, []),
         "sad_pipeline": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), ctypes.POINTER(KmerParams), P, i32,
                                         i32, i32, ctypes.POINTER(RankOut), P, P, P, P, i64, i32, P]),
     }
@@ -179,6 +182,27 @@ class Context:
 
 def _ctx(ctx):
     return None if ctx is None else ctx.handle
+
+
+STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores")
+
+
+def trace_enable(on: bool = True, ctx=None):
+    """Record CUDA events around every stage of the context's calls."""
+    _check(load().sad_trace_enable(_ctx(ctx), 1 if on else 0))
+
+
+def trace_read(ctx=None) -> dict:
+    """{stage: (device ms, intervals)} accumulated since the last read."""
+    ms = (ctypes.c_double * len(STAGES))()
+    cnt = (ctypes.c_int32 * len(STAGES))()
+    _check(load().sad_trace_read(_ctx(ctx), ms, cnt, len(STAGES)))
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+
+def launch_count() -> int:
+    """Kernels launched by libsad in this process."""
+    return int(load().sad_launch_count())
 
 
 # ---- the calls --------------------------------------------------------------
