@@ -181,6 +181,33 @@ int sad_partition(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_t* 
                   int32_t p, int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
                   int32_t mem, void* stream);
 
+/* ---- stage 1: partition without any allocation ------------------------- */
+
+#define SAD_NOALLOC_MAX_N 262144 /* keys per call of sad_partition_noalloc */
+#define SAD_NOALLOC_MAX_P 256    /* buckets per call of sad_partition_noalloc */
+
+/* The same partition as sad_partition, for callers that cannot call
+ * cudaMalloc: code that runs where a device allocation is forbidden or would
+ * stall other work (a real-time or latency-critical loop, a host callback,
+ * an embedding whose device memory is owned and capped by another framework).
+ * The paper has no counterpart; this is an interface for those callers.
+ * It allocates nothing: no device memory, no pinned or heap host memory, no
+ * context. Its scratch is one fixed array in device memory of about 5 MiB,
+ * which every GPU that loads the library holds until the process exits.
+ *   key_a, key_b [n], bucket_offsets [p+1], order [n], pivot_idx [p-1]
+ *   (nullable): device pointers on the current device, same meaning as in
+ *   sad_partition; n <= SAD_NOALLOC_MAX_N and 1 <= p <= SAD_NOALLOC_MAX_P,
+ *   otherwise SAD_EINVAL before any device work.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture. Every call reuses the same array, and
+ * each call clears the parts that must start at zero; two calls that overlap
+ * on the GPU (other threads or streams at the same time) race and give wrong
+ * results, so serialise them. The call synchronises `stream` to report bad
+ * keys (SAD_EINVAL), like sad_partition. */
+int sad_partition_noalloc(int32_t n, const int32_t* key_a, const int32_t* key_b, int32_t p,
+                          int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                          void* stream);
+
 /* ---- stage 2: per-bucket all-pairs alignment scores -------------------- */
 
 /* Number of scores for a bucket layout: sum_b n_b (n_b + 1) / 2, where

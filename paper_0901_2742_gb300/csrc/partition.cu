@@ -258,3 +258,122 @@ extern "C" int sad_partition(sad_ctx* ctx_in, int32_t n, const int32_t* key_a,
               "a rank key violates 0 <= key_a <= key_b, 1 <= key_b <= 65536");
     return SAD_OK;
 }
+
+namespace sad {
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the partition for callers that cannot allocate
+// device memory. Its scratch is one file-scope device array of fixed size,
+// laid out like the workspace of partition_device; the same kernels run on it.
+namespace {
+
+constexpr size_t kNaK = 0;
+constexpr size_t kNaRank = kNaK + 8ull * SAD_NOALLOC_MAX_N;
+constexpr size_t kNaBucket = kNaRank + 4ull * SAD_NOALLOC_MAX_N;
+constexpr size_t kNaY = kNaBucket + 4ull * SAD_NOALLOC_MAX_N;
+constexpr size_t kNaYs = kNaY + 8ull * SAD_NOALLOC_MAX_P * (SAD_NOALLOC_MAX_P - 1);
+constexpr size_t kNaPiv = kNaYs + 8ull * SAD_NOALLOC_MAX_P * (SAD_NOALLOC_MAX_P - 1);
+constexpr size_t kNaCount = kNaPiv + 8ull * SAD_NOALLOC_MAX_P;
+constexpr size_t kNaStatus = kNaCount + 4ull * SAD_NOALLOC_MAX_P;
+constexpr size_t kNaBytes = kNaStatus + 256;
+
+std::mutex g_na_mu;
+void* g_na_ptr[64] = {nullptr};
+
+}  // namespace
+
+// Every GPU that loads the library holds this array (about 5 MiB) until exit.
+static __device__ __align__(256) unsigned char g_partition_scratch[kNaBytes];
+
+namespace {
+
+// Device address of the scratch array on the current device. The host-side
+// name of a __device__ array is only a stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    SAD_CUDA(cudaGetDevice(&dev));
+    SAD_CHECK(dev >= 0 && dev < 64, SAD_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_partition_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            set_error("cudaGetSymbolAddress of the partition scratch failed: %s", cudaGetErrorString(e));
+            return SAD_ECUDA;
+        }
+        g_na_ptr[dev] = p;
+    }
+    *out = g_na_ptr[dev];
+    return SAD_OK;
+}
+
+}  // namespace
+
+}  // namespace sad
+
+extern "C" int sad_partition_noalloc(int32_t n, const int32_t* key_a, const int32_t* key_b, int32_t p,
+                                     int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                                     void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(n >= 0 && n <= SAD_NOALLOC_MAX_N, SAD_EINVAL,
+              "n = %d outside 0..%d: the static scratch of sad_partition_noalloc holds at most %d keys",
+              n, SAD_NOALLOC_MAX_N, SAD_NOALLOC_MAX_N);
+    SAD_CHECK(p >= 1 && p <= SAD_NOALLOC_MAX_P, SAD_EINVAL,
+              "p = %d outside 1..%d: the static scratch of sad_partition_noalloc holds at most %d buckets",
+              p, SAD_NOALLOC_MAX_P, SAD_NOALLOC_MAX_P);
+    SAD_CHECK(bucket_offsets && (n == 0 || (order && key_a && key_b)), SAD_EINVAL,
+              "a required pointer is NULL");
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    void* base = nullptr;
+    SAD_RET(noalloc_scratch(&base));
+    char* w = (char*)base;
+    uint64_t* K = (uint64_t*)(w + kNaK);
+    int32_t* rank = (int32_t*)(w + kNaRank);
+    int32_t* bucket = (int32_t*)(w + kNaBucket);
+    uint64_t* Y = (uint64_t*)(w + kNaY);
+    uint64_t* Ys = (uint64_t*)(w + kNaYs);
+    uint64_t* piv = (uint64_t*)(w + kNaPiv);
+    int32_t* count = (int32_t*)(w + kNaCount);
+    uint32_t* status = (uint32_t*)(w + kNaStatus);
+    const int64_t M = (int64_t)p * (p - 1);
+    // the array keeps the previous call's contents: clear what must start at zero
+    SAD_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream));
+    SAD_CUDA(cudaMemsetAsync(count, 0, 4ull * p, stream));
+    if (n == 0) {
+        SAD_CUDA(cudaMemsetAsync(bucket_offsets, 0, 4ull * (p + 1), stream));
+        if (pivot_idx && p > 1) SAD_CUDA(cudaMemsetAsync(pivot_idx, 0xff, 4ull * (p - 1), stream));
+        return SAD_OK;
+    }
+    const int nb = (n + 255) / 256;
+    k_part_keys<<<nb, 256, 0, stream>>>(n, key_a, key_b, K, status);
+    SAD_LAUNCHED();
+    if (p > 1) {
+        const int64_t wmax = (n + p - 1) / p + 1;
+        dim3 g((unsigned)p, (unsigned)((wmax + 255) / 256));
+        k_part_block_rank<<<g, 256, 0, stream>>>(n, p, K, rank);
+        SAD_LAUNCHED();
+        SAD_CUDA(cudaMemsetAsync(Y, 0xff, 8ull * M, stream));
+        k_part_samples<<<nb, 256, 0, stream>>>(n, p, K, rank, Y);
+        SAD_LAUNCHED();
+        k_part_sample_rank<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>((int32_t)M, Y, Ys);
+        SAD_LAUNCHED();
+        k_part_pivots<<<(p - 1 + 255) / 256, 256, 0, stream>>>(n, p, Ys, piv, pivot_idx);
+        SAD_LAUNCHED();
+    }
+    k_part_bucket<<<nb, 256, 0, stream>>>(n, p, K, piv, bucket, count);
+    SAD_LAUNCHED();
+    k_part_offsets<<<1, 32, 0, stream>>>(p, count, bucket_offsets);
+    SAD_LAUNCHED();
+    k_part_scatter<<<(p + 7) / 8, 256, 0, stream>>>(n, p, bucket, bucket_offsets, order);
+    SAD_LAUNCHED();
+    // report bad keys: read the status word into thread-local host memory
+    static thread_local uint32_t h_status = 0;
+    SAD_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+    SAD_CUDA(cudaStreamSynchronize(stream));
+    SAD_CHECK(!(h_status & STATUS_BAD_KEY), SAD_EINVAL,
+              "a rank key violates 0 <= key_a <= key_b, 1 <= key_b <= 65536");
+    return SAD_OK;
+}

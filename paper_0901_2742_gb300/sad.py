@@ -73,6 +73,7 @@ def load():
         "sad_kmer_rank": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), ctypes.POINTER(KmerParams),
                                          ctypes.POINTER(RankOut), i32, P]),
         "sad_partition": (ctypes.c_int, [P, i32, P, P, i32, P, P, P, i32, P]),
+        "sad_partition_noalloc": (ctypes.c_int, [i32, P, P, i32, P, P, P, P]),
         "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
                                                   i32, P, P, i64, i32, P]),
