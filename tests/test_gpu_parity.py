@@ -233,3 +233,45 @@ def test_scores_capacity_too_small(sad):
     with pytest.raises(sad.SadError) as e:
         sad.bucket_pair_scores(w.residues, w.offsets, 20, bo, order, w.subst, -11, -1, capacity=10)
     assert e.value.code == sad.SAD_ERANGE
+
+
+# ---- threshold planes on the tensor cores (cap > 0) ---------------------------
+
+def run_rank_only(sad, w, cap):
+    return sad.kmer_rank(w.residues, w.offsets, w.alphabet, w.k, w.p, cap=cap,
+                         kmer_alphabet=w.kmer_alphabet, class_map=w.class_map, want_A=True)
+
+
+def test_planes_single_tile(sad):
+    """One 128 x 128 tile (N = 64): every numerator from the tcgen05 GEMM."""
+    w = synth.workload(1)
+    want = oracle_all(w, "cfg1")
+    assert_rank_equal(run_rank_only(sad, w, 4), want[0])
+
+
+@pytest.mark.parametrize("cap", [1, 2, 3, 4, 8])
+def test_planes_caps_and_residuals(sad, cap):
+    # caps below typical counts force the residual path for many pairs
+    rng = np.random.default_rng(cap)
+    seqs = [list(rng.integers(0, 4, L)) for L in rng.integers(3, 300, 150)]
+    seqs += [[4] * 400, [4, 5] * 200, [1] * 3, []]
+    w = make_workload(seqs, p=5, k=2)
+    want = oracle_all(w)
+    assert_rank_equal(run_rank_only(sad, w, cap), want[0])
+
+
+def test_planes_paper_scale(sad):
+    """N = 2000, cap 4, K = 4 x 8000: ragged last tile row, 136 tiles."""
+    w = synth.workload(3)
+    want = oracle_all(w, "cfg2")
+    r, pt, so, sc = run_gpu(sad, w, 1)
+    assert_rank_equal(r, want[0])
+    np.testing.assert_array_equal(pt["order"], want[1]["order"])
+    np.testing.assert_array_equal(sc, want[3])
+
+
+def test_planes_compressed_alphabet(sad):
+    """Six-letter alphabet, k = 4, cap 4 (K = 4 x 1344, a partial last k-block)."""
+    w = synth.workload(4, n_override=700)
+    want = oracle_all(w)
+    assert_rank_equal(run_rank_only(sad, w, 4), want[0])
