@@ -51,6 +51,20 @@ def workload_cells(lengths, bucket_offsets, order):
     return cells
 
 
+def aggregate_ranks(ms_step: float, units: float, dist=None, device=None):
+    """Whole-job throughput over replicas: every rank processed `units` in its
+    own ms_step; the job takes the slowest rank's time. Returns
+    (max ms_step over ranks, summed units, world size)."""
+    if dist is None or not dist.is_initialized():
+        return ms_step, units, 1
+    import torch
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item()), dist.get_world_size()
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -162,14 +176,87 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def run_serving(args):
+    """Serving workload: a Poisson stream of partition-and-score jobs with N
+    uniform in 100..5000 and lengths lognormal(median 300, sigma 0.55) in
+    [50, 1500] (k = 3, p = 4), admitted by device memory into a continuous-
+    batching server. Offline capacity = every job submitted at once; the
+    stream then arrives at 0.7 x that rate. Prints one JSON line."""
+    import threading
+
+    import torch
+    from paper_0901_2742_gb300 import build, sad, synth
+    build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(args.seed)
+    njobs = args.jobs
+    sizes = rng.integers(100, 5001, njobs)
+    jobs = [synth.workload(5, seed=10_000 + i, n_override=int(sizes[i])) for i in range(njobs)]
+
+    def run_offline():
+        with sad.Server(slots=args.slots) as srv:
+            t0 = time.perf_counter()
+            ids = [srv.submit(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend)
+                   for w in jobs]
+            for j in ids:
+                assert srv.wait(j) == sad.SAD_OK, srv.error()
+            span = time.perf_counter() - t0
+            outs = [srv.result(j, w.n) for j, w in zip(ids, jobs)]
+            return span, outs, srv.stats()
+
+    run_offline()  # warm-up (workspaces, module load)
+    span, outs, st_off = run_offline()
+    total_cells = 0
+    for w, o in zip(jobs, outs):
+        total_cells += workload_cells(w.lengths(), o["bucket_offsets"], o["order"])
+    capacity = njobs / span
+    rate = 0.7 * capacity
+    gaps = -np.log(1.0 - synth.uniform_f64(args.seed + 1, njobs)) / rate
+    arrivals = np.cumsum(gaps)
+    with sad.Server(slots=args.slots) as srv:
+        ids = [None] * njobs
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i, w in enumerate(jobs):
+                delay = arrivals[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids[i] = srv.submit(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open,
+                                    w.gap_extend)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        for j in ids:
+            assert srv.wait(j) == sad.SAD_OK, srv.error()
+        span_stream = time.perf_counter() - t0
+        st = srv.stats()
+        same = all(np.array_equal(srv.result(j, w.n)["scores"], o["scores"]) for j, w, o in zip(ids, jobs, outs))
+    line = {"mode": "serving", "metric": "jobs/s with p50/p99 latency (Poisson arrivals)", "value": st["jobs_per_s"],
+            "unit": "jobs/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "arrival_rate_jobs_per_s": rate, "offline_jobs_per_s": capacity,
+            "offline_gcups": total_cells / span / 1e9, "stream_gcups": total_cells / span_stream / 1e9,
+            "offline_p50_ms": st_off["p50_ms"], "offline_p99_ms": st_off["p99_ms"],
+            "jobs": njobs, "slots": args.slots, "results_identical_to_offline": bool(same),
+            "config": {"workload": "N ~ U{100..5000}, L ~ logN(300, 0.55) in [50, 1500], k=3, p=4, "
+                                   "gap -11/-1"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--serving", action="store_true", help="Poisson job stream through the server")
+    ap.add_argument("--jobs", type=int, default=200)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--seed", type=int, default=5005)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", type=int, default=2, help="2: N=2000 paper scale; 4: N=20000")
-    ap.add_argument("--cap", type=int, default=0, help="0: uint8 CUDA-core k-mer path; >0 planes")
+    ap.add_argument("--cap", type=int, default=4, help="0: uint8 CUDA-core k-mer path; >0 planes")
     ap.add_argument("--mode", type=int, default=1, help="0: per-bucket launches, 1: persistent")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -177,6 +264,8 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.serving:
+        return run_serving(args) if rank == 0 else 0
 
     import torch
     from paper_0901_2742_gb300 import build, sad, synth
@@ -236,16 +325,15 @@ def main():
     if dist:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in evs]
-    ms_step = sum(ms) / len(ms)
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ws * cells / (ms_step * 1e-3) / 1e9
+    ms_step, all_cells, _ = aggregate_ranks(sum(ms) / len(ms), float(cells), dist, dev)
+    value = all_cells / (ms_step * 1e-3) / 1e9
     kmer_ms = (trace["count"][0] + trace["allpairs"][0] + trace["rank"][0]) / args.steps
-    score_ms = trace["scores"][0] / max(trace["scores"][1], 1)
-    score_launches_per_step = trace["scores"][1] / args.steps
-    achieved = OPS_PER_CELL * cells / (trace["scores"][0] / args.steps * 1e-3) / 1e12
+    packed = trace["scores_packed"][1] > 0
+    sc_ms, sc_n = trace["scores_packed"] if packed else trace["scores"]
+    score_ms = sc_ms / max(sc_n, 1)
+    score_launches_per_step = sc_n / args.steps
+    ops_per_cell = OPS_PER_CELL / 2 if packed else OPS_PER_CELL   # 16x2: one instruction, two cells
+    achieved = ops_per_cell * cells / (sc_ms / args.steps * 1e-3) / 1e12
     peak = SMS * INT_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
 
     # end to end through the C ABI with pinned host buffers
@@ -293,7 +381,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded tree-evolved families)",
+        "vs_baseline": None, "dtype": "int16x2" if packed else "int32",
+        "data": "synthetic (seeded tree-evolved families)",
         "config": {"workload": w.name, "n": n, "p": p, "k": w.k,
                    "kmer_path": "uint8 min-sum, CUDA cores" if w.cap == 0 else f"cap-{w.cap} threshold planes, tensor cores",
                    "scores_mode": "persistent" if args.mode == 1 else "one launch per bucket",
@@ -303,10 +392,13 @@ def main():
         "pairs_scored": pairs_scored, "cells": cells,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_gotoh_items (alignment scores)",
+                     "kernel": ("k_gotoh_pair16 (alignment scores, two problems per 16x2 lane)" if packed
+                                else "k_gotoh_items (alignment scores, 32-bit DP)"),
                      "kernel_ms": score_ms, "launches_per_step": score_launches_per_step,
+                     "gcups": cells / (sc_ms / args.steps * 1e-3) / 1e9,
+                     "peak_gcups": peak * 1e12 / ops_per_cell / 1e9,
                      "peak_basis": f"{SMS} SMs x {INT_OPS_PER_CLK_SM} int ops/clk x {SM_MAX_MHZ:.0f} MHz; "
-                                   f"{OPS_PER_CELL} ops per cell"},
+                                   f"{ops_per_cell:g} instructions per cell"},
         "gpu_launches": int(launches),
         "wall_s": wall,
         "clocks": clocks,

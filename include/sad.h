@@ -140,8 +140,9 @@ const char* sad_version(void);
 #define SAD_STAGE_ALLPAIRS 2   /* all-pairs similarity with the fused D sums */
 #define SAD_STAGE_RANK 3       /* ancestors and rank keys */
 #define SAD_STAGE_PARTITION 4  /* regular-sampling partition */
-#define SAD_STAGE_SCORES 5     /* alignment-score kernels */
-#define SAD_NUM_STAGES 6
+#define SAD_STAGE_SCORES 5     /* alignment-score kernels, 32-bit DP */
+#define SAD_STAGE_SCORES_PACKED 6 /* alignment-score kernels, two problems per 16x2 lane */
+#define SAD_NUM_STAGES 7
 
 /* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
  * accumulated times. */
@@ -239,6 +240,19 @@ int sad_bucket_pair_scores(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* 
                            int64_t* score_offsets, int32_t* scores, int64_t scores_capacity,
                            int32_t mem, void* stream);
 
+/* Variant table of the packed alignment kernel (SAD_SCORES_PERSISTENT mode
+ * when every score provably fits 16 bits). The pair of queries at length-order
+ * positions 2q, 2q+1 of a bucket with `rows` = the longer length uses the first
+ * bin b with rows <= upper[b]: R[b] query rows per lane (8, 12, 16, 20, 24 or
+ * 32) and G[b] lanes per subject (8, 16 or 32); rows beyond every bin, or an
+ * empty table (nbins = 0, the default), use the built-in cost model. Bounds
+ * must increase; at most 16 bins. The table only changes speed, never a score.
+ * get: copies up to max_bins entries and the bin count. */
+int sad_scores_set_variants(sad_ctx* ctx, const int32_t* upper, const int32_t* R, const int32_t* G,
+                            int32_t nbins);
+int sad_scores_get_variants(sad_ctx* ctx, int32_t* upper, int32_t* R, int32_t* G, int32_t max_bins,
+                            int32_t* nbins);
+
 /* ---- both stages ------------------------------------------------------- */
 
 /* sad_kmer_rank, sad_partition and sad_bucket_pair_scores in one call, with
@@ -251,6 +265,80 @@ int sad_pipeline(sad_ctx* ctx, const sad_seqset* seqs, const sad_kmer_params* pa
                  const sad_rank_out* rank, int32_t* bucket_offsets, int32_t* order,
                  int64_t* score_offsets, int32_t* scores, int64_t scores_capacity,
                  int32_t mem, void* stream);
+
+/* ---- serving: continuous batching of partition-and-score jobs ----------- */
+
+/* A stream of jobs (each a full sad_pipeline: k-mer rank, partition, bucket
+ * scores) of different sizes on one GPU. The server runs `slots` jobs at once,
+ * each on its own stream with its own workspaces, so their kernels overlap on
+ * the device; a queued job is admitted as soon as a slot is free and its
+ * device-memory estimate fits in what the running jobs leave of `hbm_budget`
+ * (the first queued job that fits goes first). Results stay in server-owned
+ * host memory until released. Every result is bit-identical to the same job
+ * run alone. The paper has no serving layer; this is the batching of its
+ * per-processor work across independent requests. */
+typedef struct sad_server sad_server;
+
+typedef struct sad_server_config {
+    int32_t device;          /* CUDA device */
+    int32_t slots;           /* jobs in flight at once, 1..64 */
+    int64_t hbm_budget;      /* bytes of device memory jobs may hold at once; 0 = 90% of free */
+    int32_t queue_capacity;  /* queued jobs; submit returns SAD_EBUSY beyond it */
+} sad_server_config;
+
+/* One job; every array is host memory and is copied by sad_server_submit. */
+typedef struct sad_job {
+    const uint8_t* residues;
+    const int64_t* offsets;  /* n+1 */
+    int32_t n;
+    int32_t alphabet;
+    sad_kmer_params kmer;
+    const int8_t* subst;     /* alphabet x alphabet, symmetric */
+    int32_t gap_open;
+    int32_t gap_extend;
+} sad_job;
+
+#define SAD_JOB_QUEUED 0
+#define SAD_JOB_RUNNING 1
+#define SAD_JOB_DONE 2
+#define SAD_JOB_FAILED 3
+#define SAD_JOB_CANCELLED 4
+
+typedef struct sad_server_stats {
+    int64_t done, failed, cancelled, queued;
+    int32_t running;
+    double p50_ms, p99_ms, mean_ms;  /* submit-to-done latency of finished jobs */
+    double jobs_per_s;               /* finished jobs / (last finish - first submit) */
+    int64_t budget_bytes, reserved_bytes;
+} sad_server_stats;
+
+/* Start the workers. Errors: SAD_EINVAL, SAD_ECUDA, SAD_ENOMEM. */
+int sad_server_create(const sad_server_config* cfg, sad_server** out);
+/* Validate and queue a job; *job_id identifies it. SAD_ENOMEM when the job's
+ * estimate exceeds the whole budget, SAD_EBUSY when the queue is full,
+ * SAD_EINVAL for bad parameters (bad residue codes surface later as the job's
+ * own failure). */
+int sad_server_submit(sad_server* s, const sad_job* job, uint64_t* job_id);
+/* *state = SAD_JOB_*; returns the job's error code if it failed. */
+int sad_server_poll(sad_server* s, uint64_t job_id, int32_t* state);
+/* Wait until the job ends (timeout_ms < 0: no limit). SAD_OK when done,
+ * SAD_EBUSY on timeout, SAD_ECANCELED, or the job's own error code. */
+int sad_server_wait(sad_server* s, uint64_t job_id, int64_t timeout_ms);
+/* Copy a finished job's bucket_offsets[p+1], order[n], score_offsets[p+1] and
+ * scores (layout as sad_bucket_pair_scores); any output pointer may be NULL.
+ * *n_scores receives the score count, *latency_ms (nullable) the job's
+ * submit-to-done time. SAD_ERANGE if capacity < *n_scores. */
+int sad_server_result(sad_server* s, uint64_t job_id, int32_t* bucket_offsets, int32_t* order,
+                      int64_t* score_offsets, int32_t* scores, int64_t capacity, int64_t* n_scores,
+                      double* latency_ms);
+/* Forget a finished job and free its results. */
+int sad_server_release(sad_server* s, uint64_t job_id);
+/* Cancel: a queued job is dropped now; a running one stops between stages. */
+int sad_server_cancel(sad_server* s, uint64_t job_id);
+int sad_server_get_stats(sad_server* s, sad_server_stats* out);
+/* Stop the workers (running jobs finish, queued jobs are cancelled) and free
+ * everything. */
+int sad_server_destroy(sad_server* s);
 
 #ifdef __cplusplus
 }

@@ -123,6 +123,20 @@ int workspace(sad_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, void**
     return SAD_OK;
 }
 
+int allow_max_dynamic_smem(sad_ctx* ctx, const void* fn) {
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void*>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& d : done)
+        if (d.first == ctx->device && d.second == fn) return SAD_OK;
+    cudaFuncAttributes attr;
+    SAD_CUDA(cudaFuncGetAttributes(&attr, fn));
+    const int dyn = (int)ctx->smem_optin - (int)attr.sharedSizeBytes;  // room left by static smem
+    SAD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    done.push_back({ctx->device, fn});
+    return SAD_OK;
+}
+
 int pinned(sad_ctx* ctx, size_t bytes, cudaStream_t stream, void** out) {
     if (ctx->h_pinned_bytes < bytes) {
         if (ctx->h_pinned) {
@@ -297,6 +311,19 @@ int sad_ctx_destroy(sad_ctx* ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->aux_ready) {
+        for (int v = 0; v < sad::kAuxStreams; v++) {
+            cudaStreamDestroy(ctx->aux[v]);
+            cudaEventDestroy(ctx->ev_join[v]);
+        }
+        cudaEventDestroy(ctx->ev_fork);
+    }
+    for (auto& st : ctx->trace)
+        for (auto& pr : st.pending) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
     return SAD_OK;
 }

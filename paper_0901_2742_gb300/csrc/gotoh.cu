@@ -252,6 +252,232 @@ KernelFn kernel_for(int R) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed form: two queries of similar length share every instruction. Each
+// 32-bit register holds the same DP cell of both problems (x1 in the low
+// halfword, x2 in the high halfword) and every cell operation is one 16x2
+// DPX instruction; an add is __viaddmax_s16x2(a, b, NEG2), exact while every
+// value stays above NEG16 (the host proves |values| fit before choosing this
+// form). Per row and column: 5 instructions for 2 cells.
+constexpr int32_t NEG16 = -20000;
+
+__device__ __forceinline__ uint32_t pk2(int32_t lo, int32_t hi) {
+    return ((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16);
+}
+
+__device__ __forceinline__ int32_t lo16(uint32_t v) { return (int32_t)(int16_t)(v & 0xffffu); }
+__device__ __forceinline__ int32_t hi16(uint32_t v) { return (int32_t)(int16_t)(v >> 16); }
+
+// Words per lane chunk of the packed profile: R rows padded so that a chunk is
+// an odd number of 16-byte units; the 8 lanes of one 128-bit load phase then
+// hit 8 different 16-byte bank groups.
+template <int R>
+__host__ __device__ constexpr int rpad() {
+    return ((R / 4) % 2 == 0) ? R + 4 : R;
+}
+
+template <int R>
+__device__ __forceinline__ void load_profile32(const uint32_t* p, uint32_t (&s)[R]) {
+    if constexpr (R % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < R / 4; q++) {
+            const uint4 w = *(const uint4*)(p + 4 * q);
+            s[4 * q] = w.x; s[4 * q + 1] = w.y; s[4 * q + 2] = w.z; s[4 * q + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; q++) s[q] = p[q];
+    }
+}
+
+// One group aligns the query pair (packed profile in smem, lengths m1, m2)
+// against subject y of length n; writes the two scores to r1, r2 (valid for
+// m1 >= 1 and m2 >= 1 respectively).
+template <int R>
+__device__ void align_pair16(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2,
+                             const uint8_t* __restrict__ y, int32_t n, int32_t nsteps_warp,
+                             const GotohArgs& a, int32_t* __restrict__ bnd, int lane, unsigned gmask,
+                             int32_t* r1, int32_t* r2) {
+    const int G = a.G;
+    const int32_t go = a.go, ge = a.ge;
+    const uint32_t NEG2 = pk2(NEG16, NEG16);
+    const uint32_t ge2 = pk2(ge, ge), goe2 = pk2(go + ge, go + ge);
+    const int32_t strip_h = G * R;
+    const int32_t mrows = max(m1, m2);
+    const int32_t strips = (mrows + strip_h - 1) / strip_h;
+    for (int32_t s = 0; s < strips; s++) {
+        const int32_t row0 = s * strip_h + lane * R;
+        uint32_t H[R], Hg[R], E[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int32_t b0 = go + (row0 + r + 1) * ge;
+            H[r] = pk2(b0, b0);
+            Hg[r] = __viaddmax_s16x2(H[r], goe2, NEG2);
+            E[r] = NEG2;
+        }
+        const int32_t d0 = (row0 == 0) ? 0 : go + row0 * ge;
+        uint32_t hdiag = pk2(d0, d0);
+        uint32_t hin = 0, fin = NEG2, yin = 0, yword = 0;
+        const bool last_strip = s == strips - 1;
+        for (int32_t tau = 0; tau < nsteps_warp; tau++) {
+            const int32_t j = tau - lane + 1;
+            if (lane == 0 && tau < n) {
+                if ((tau & 3) == 0) yword = *(const uint32_t*)(y + tau);
+                yin = (yword >> (8 * (tau & 3))) & 0xffu;
+                if (s == 0) {
+                    const int32_t b0 = go + (tau + 1) * ge;
+                    hin = pk2(b0, b0);
+                    fin = NEG2;
+                } else {
+                    hin = (uint32_t)bnd[2 * (tau + 1)];
+                    fin = (uint32_t)bnd[2 * (tau + 1) + 1];
+                }
+            }
+            uint32_t hout = hin, fout = fin;
+            if (j >= 1 && j <= n) {
+                uint32_t sc[R];
+                load_profile32<R>(prof + (int64_t)yin * a.prof_stride + (int64_t)(row0 / R) * rpad<R>(),
+                                  sc);
+                uint32_t fu = fin;
+                uint32_t hgu = __viaddmax_s16x2(hin, goe2, NEG2);
+                uint32_t hd = hdiag;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
+                    const uint32_t f = __viaddmax_s16x2(fu, ge2, hgu);
+                    const uint32_t t = __viaddmax_s16x2(hd, sc[r], NEG2);
+                    const uint32_t h = __vimax3_s16x2(t, e, f);
+                    hd = H[r];
+                    H[r] = h;
+                    Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
+                    E[r] = e;
+                    fu = f;
+                    hgu = Hg[r];
+                }
+                hdiag = hin;
+                hout = H[R - 1];
+                fout = fu;
+                if (!last_strip && lane == G - 1) {
+                    bnd[2 * j] = (int32_t)hout;
+                    bnd[2 * j + 1] = (int32_t)fout;
+                }
+            }
+            hin = __shfl_up_sync(gmask, hout, 1, G);
+            fin = __shfl_up_sync(gmask, fout, 1, G);
+            yin = __shfl_up_sync(gmask, yin, 1, G);
+        }
+        __syncwarp(gmask);
+        // a query whose last row lies in this strip has its score now
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int32_t mq = q == 0 ? m1 : m2;
+            if (mq >= 1 && (mq - 1) / strip_h == s) {
+                const int32_t rr = (mq - 1) - s * strip_h;
+                const int owner = rr / R, rsel = rr % R;
+                uint32_t v = 0;
+#pragma unroll
+                for (int r = 0; r < R; r++) v = (r == rsel) ? H[r] : v;
+                v = __shfl_sync(gmask, v, owner, G);
+                if (q == 0) *r1 = lo16(v);
+                else *r2 = hi16(v);
+            }
+        }
+    }
+}
+
+// Work item (bucket, query pair qp, subjects [v0, v1)): queries are the
+// members at length-order positions 2qp and 2qp+1 of the bucket.
+template <int R>
+__global__ void __launch_bounds__(128, (R <= 20) ? 4 : ((R <= 24) ? 3 : 2))
+k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __restrict__ head,
+               GotohArgs a) {
+    extern __shared__ __align__(16) uint32_t prof32[];
+    __shared__ int32_t item_sh;
+    const int G = a.G;
+    const int NG = blockDim.x / G;
+    const int g = threadIdx.x / G;
+    const int lane = threadIdx.x % G;
+    const int warp_lane0 = (threadIdx.x & 31) - lane;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << warp_lane0);
+    int32_t* bnd = a.scratch ? a.scratch + ((int64_t)blockIdx.x * NG + g) * a.scratch_stride : nullptr;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_sh = atomicAdd(head, 1);
+        __syncthreads();
+        const int32_t it_idx = item_sh;
+        if (it_idx >= n_items) break;
+        const GotohItem it = items[it_idx];
+        const int32_t b = it.bucket;
+        const int32_t boff = a.bucket_off[b];
+        const int32_t nb = a.bucket_off[b + 1] - boff;
+        const int32_t u1 = a.srt[boff + 2 * it.q];
+        const int32_t u2 = (2 * it.q + 1 < nb) ? a.srt[boff + 2 * it.q + 1] : -1;
+        const int32_t x1 = a.order[boff + u1];
+        const int32_t x2 = u2 >= 0 ? a.order[boff + u2] : x1;
+        const int32_t m1 = a.len[x1];
+        const int32_t m2 = u2 >= 0 ? a.len[x2] : 0;
+        const uint8_t* q1 = a.res + a.pad_off[x1];
+        const uint8_t* q2 = a.res + a.pad_off[x2];
+        // profile words of letter c: lane chunks of R rows, each padded to rpad<R>() words
+        const int32_t mp = a.prof_stride;
+        for (int32_t t = threadIdx.x; t < a.alphabet * mp; t += blockDim.x) {
+            const int32_t c = t / mp, w = t - c * mp;
+            const int32_t chunk = w / rpad<R>(), off = w - chunk * rpad<R>();
+            const int32_t i = chunk * R + off;
+            const bool row = off < R;
+            const int32_t lo = (row && i < m1) ? a.subst[c * a.alphabet + q1[i]] : 0;
+            const int32_t hi = (row && i < m2) ? a.subst[c * a.alphabet + q2[i]] : 0;
+            prof32[t] = pk2(lo, hi);
+        }
+        __syncthreads();
+        const int32_t mrows = max(m1, m2);
+        const int32_t nsub = it.v1 - it.v0;
+        const int32_t rounds = (nsub + NG - 1) / NG;
+        for (int32_t rd = 0; rd < rounds; rd++) {
+            const int32_t v = it.v0 + rd * NG + g;
+            const bool have = v < it.v1;
+            int32_t uv = 0, ys = 0, n = 0;
+            if (have) {
+                uv = a.srt[boff + v];
+                ys = a.order[boff + uv];
+                n = a.len[ys];
+            }
+            const int32_t need = (have && mrows > 0 && n > 0) ? n + G - 1 : 0;
+            const int32_t steps = (__reduce_max_sync(0xffffffffu, need) + 3) & ~3;
+            int32_t s1 = 0, s2 = 0;
+            if (steps > 0)
+                align_pair16<R>(prof32, m1, m2, a.res + a.pad_off[have ? ys : x1], (have && mrows > 0) ? n : 0,
+                                steps, a, bnd, lane, gmask, &s1, &s2);
+            if (have && lane == 0) {
+                const int32_t mq[2] = {m1, m2};
+                int32_t sc[2] = {s1, s2};
+                const int32_t uq[2] = {u1, u2};
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    if (uq[q] < 0) continue;
+                    if (mq[q] == 0 && n == 0) sc[q] = 0;
+                    else if (mq[q] == 0) sc[q] = a.go + n * a.ge;
+                    else if (n == 0) sc[q] = a.go + mq[q] * a.ge;
+                    const int32_t lo = min(uq[q], uv), hi = max(uq[q], uv);
+                    a.scores[a.score_off[b] + tri_pos(lo, hi, nb)] = sc[q];
+                }
+            }
+        }
+    }
+}
+
+KernelFn pair16_kernel_for(int R) {
+    switch (R) {
+        case 8: return k_gotoh_pair16<8>;
+        case 12: return k_gotoh_pair16<12>;
+        case 16: return k_gotoh_pair16<16>;
+        case 20: return k_gotoh_pair16<20>;
+        case 24: return k_gotoh_pair16<24>;
+        case 32: return k_gotoh_pair16<32>;
+        default: return nullptr;
+    }
+}
+
 }  // namespace
 
 // Host-side plan: per bucket, members sorted by length (ascending, ties by
@@ -310,7 +536,7 @@ int gotoh_launch(sad_ctx* ctx, const DevSeqs& S, const GotohLaunch& L, cudaStrea
     const size_t smem = (size_t)S.alphabet * a.prof_stride;
     SAD_CHECK(smem <= ctx->smem_optin, SAD_EINVAL, "query profile of %zu bytes exceeds shared memory",
               smem);
-    SAD_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
     TraceScope ts(ctx, SAD_STAGE_SCORES, stream);
     fn<<<grid, threads, smem, stream>>>(L.items, L.n_items, L.head, a);
     SAD_LAUNCHED();
@@ -324,6 +550,256 @@ int pick_R(int32_t m) {
     for (int R : Rs)
         if (m <= 32 * R) return R;
     return 32;
+}
+
+// Variants of the packed kernel: R rows per lane x G lanes per subject.
+constexpr int kPackedR[] = {8, 12, 16, 20, 24, 32};
+constexpr int kPackedG[] = {8, 16, 32};
+constexpr int kNumR = 6, kNumG = 3, kNumVariants = kNumR * kNumG;
+constexpr int kPackedThreads = 128;
+constexpr int32_t kChunkSubjects = 64;
+
+// Every value of the packed DP must stay inside (NEG16, 2^15): scores are at
+// most max(s, 0) * min(m, n) and at least the all-gap path 2 go + (i + j) ge
+// (minus one gap opening and the most negative substitution for E, F and the
+// diagonal sum), with i up to the padded strip rows.
+bool fits_packed16(const DevSeqs& S, const int8_t* subst, int32_t go, int32_t ge) {
+    int32_t smax = 0, smin = 0;
+    for (int32_t t = 0; t < S.alphabet * S.alphabet; t++) {
+        smax = std::max<int32_t>(smax, subst[t]);
+        smin = std::min<int32_t>(smin, subst[t]);
+    }
+    const int64_t L = S.max_len;
+    const int64_t rows = L + 1024;  // padding of the widest strip
+    const int64_t hi = (int64_t)smax * L;
+    const int64_t lo = 3ll * -go + (int64_t)-ge * (rows + L + 2) - smin;
+    return hi < 32000 && lo < -(int64_t)NEG16 - 1000 && -ge < 4000 && -go < 4000;
+}
+
+int rpad_rt(int R) { return ((R / 4) % 2 == 0) ? R + 4 : R; }
+
+int variant_index(int R, int G) {
+    for (int ri = 0; ri < kNumR; ri++)
+        for (int gi = 0; gi < kNumG; gi++)
+            if (kPackedR[ri] == R && kPackedG[gi] == G) return ri * kNumG + gi;
+    return -1;
+}
+
+// Cost estimate (instruction slots) of one subject of length n for a query
+// pair of `rows` rows under variant (R, G).
+double packed_cost(int32_t rows, double n, int R, int G) {
+    const int32_t strip_h = R * G;
+    const int32_t strips = (rows + strip_h - 1) / strip_h;
+    return (double)strips * G * (n + G + 1) * (5.0 * R + 16.0) + strips * G * 40.0;
+}
+
+int ensure_aux_streams(sad_ctx* ctx) {
+    if (ctx->aux_ready) return SAD_OK;
+    for (int v = 0; v < kAuxStreams; v++) {
+        SAD_CUDA(cudaStreamCreateWithFlags(&ctx->aux[v], cudaStreamNonBlocking));
+        SAD_CUDA(cudaEventCreateWithFlags(&ctx->ev_join[v], cudaEventDisableTiming));
+    }
+    SAD_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    ctx->aux_ready = true;
+    return SAD_OK;
+}
+
+int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_bo,
+                  const std::vector<int32_t>& h_order, const std::vector<int32_t>& srt,
+                  const GotohLaunch& base, cudaStream_t stream) {
+    const int32_t p = (int32_t)h_bo.size() - 1;
+    auto len_at = [&](int32_t b, int32_t pos) { return S.h_len[h_order[h_bo[b] + srt[h_bo[b] + pos]]]; };
+    std::vector<GotohItem> by_var[kNumVariants];
+    std::vector<double> cost_var[kNumVariants];
+    int32_t rows_var[kNumVariants] = {0};
+    std::vector<GotohItem> singles;  // single-query items for the 32-bit kernel
+    int32_t singles_rows = 0;
+    for (int32_t b = 0; b < p; b++) {
+        const int32_t nb = h_bo[b + 1] - h_bo[b];
+        for (int32_t qp = 0; 2 * qp < nb; qp++) {
+            const int32_t m1 = len_at(b, 2 * qp);
+            const int32_t m2 = (2 * qp + 1 < nb) ? len_at(b, 2 * qp + 1) : 0;
+            const int32_t rows = std::max(m1, m2);
+            for (int32_t v0 = 2 * qp; v0 < nb; v0 += kChunkSubjects) {
+                const int32_t v1 = std::min(nb, v0 + kChunkSubjects);
+                double nsum = 0;
+                for (int32_t v = v0; v < v1; v++) nsum += len_at(b, v);
+                const double navg = nsum / (v1 - v0);
+                // the packed profile of the pair must fit in shared memory
+                auto fits = [&](int v) {
+                    const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+                    const int64_t words = round_up(std::max(rows, 1), (int64_t)R * G) / R * rpad_rt(R);
+                    return (size_t)S.alphabet * words * 4 <= ctx->smem_optin;
+                };
+                int best = -1;
+                double bc = 1e300;
+                const ScoreTuning& tu = ctx->tuning;
+                for (int t = 0; t < tu.nbins && best < 0; t++)
+                    if (rows <= tu.upper[t]) best = variant_index(tu.R[t], tu.G[t]);
+                if (best >= 0 && fits(best)) {
+                    bc = packed_cost(std::max(rows, 1), navg, kPackedR[best / kNumG], kPackedG[best % kNumG]);
+                } else {
+                    best = -1;
+                    for (int ri = 0; ri < kNumR; ri++)
+                        for (int gi = 0; gi < kNumG; gi++) {
+                            if (!fits(ri * kNumG + gi)) continue;
+                            const double c = packed_cost(std::max(rows, 1), navg, kPackedR[ri], kPackedG[gi]);
+                            if (c < bc) {
+                                bc = c;
+                                best = ri * kNumG + gi;
+                            }
+                        }
+                }
+                if (best < 0) {
+                    // too long for any packed profile: both queries go to the 32-bit kernel
+                    singles.push_back(GotohItem{b, 2 * qp, v0, v1});
+                    if (2 * qp + 1 < nb && std::max(v0, 2 * qp + 1) < v1)
+                        singles.push_back(GotohItem{b, 2 * qp + 1, std::max(v0, 2 * qp + 1), v1});
+                    singles_rows = std::max(singles_rows, rows);
+                    continue;
+                }
+                by_var[best].push_back(GotohItem{b, qp, v0, v1});
+                cost_var[best].push_back(bc * (v1 - v0));
+                rows_var[best] = std::max(rows_var[best], rows);
+            }
+        }
+    }
+    // longest first inside every variant
+    std::vector<GotohItem> all;
+    int32_t first[kNumVariants + 1];
+    for (int v = 0; v < kNumVariants; v++) {
+        first[v] = (int32_t)all.size();
+        std::vector<int32_t> idx(by_var[v].size());
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int32_t x, int32_t y) { return cost_var[v][x] > cost_var[v][y]; });
+        for (int32_t t : idx) all.push_back(by_var[v][t]);
+    }
+    first[kNumVariants] = (int32_t)all.size();
+    const int32_t first_single = (int32_t)all.size();
+    for (const GotohItem& it : singles) all.push_back(it);
+    const size_t items_bytes = sizeof(GotohItem) * (all.size() + 1);
+    const size_t heads_off = (size_t)round_up((int64_t)items_bytes, 256);
+    const size_t heads_bytes = 4 * (kNumVariants + 1);
+    void* dplan = nullptr;
+    SAD_RET(workspace(ctx, WS_SCORE_ITEMS, heads_off + heads_bytes + 256, stream, &dplan));
+    void* pin = nullptr;
+    SAD_RET(pinned(ctx, heads_off + heads_bytes, stream, &pin));
+    SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may feed an earlier copy
+    memcpy(pin, all.data(), sizeof(GotohItem) * all.size());
+    memset((char*)pin + heads_off, 0, heads_bytes);
+    SAD_CUDA(cudaMemcpyAsync(dplan, pin, heads_off + heads_bytes, cudaMemcpyHostToDevice, stream));
+    const GotohItem* d_items = (const GotohItem*)dplan;
+    int32_t* d_heads = (int32_t*)((char*)dplan + heads_off);
+    // launch shapes and strip-boundary scratch
+    struct Shape {
+        int grid = 0;
+        size_t smem = 0;
+        int64_t scratch_off = 0;
+        bool strips = false;
+        int32_t prof_stride = 0;
+    } shp[kNumVariants];
+    const int64_t stride = 2 * ((int64_t)S.max_len + 1 + 4);
+    int64_t scratch_ints = 0;
+    for (int v = 0; v < kNumVariants; v++) {
+        const int32_t nv = first[v + 1] - first[v];
+        if (nv == 0) continue;
+        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+        const int32_t strip_h = R * G;
+        shp[v].prof_stride = (int32_t)(round_up(std::max<int32_t>(rows_var[v], 1), strip_h) / R) * rpad_rt(R);
+        shp[v].smem = (size_t)S.alphabet * shp[v].prof_stride * 4;
+        SAD_CHECK(shp[v].smem <= ctx->smem_optin, SAD_EINVAL,
+                  "packed query profile of %zu bytes exceeds shared memory", shp[v].smem);
+        KernelFn fn = pair16_kernel_for(R);
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
+        int occ = 0;
+        SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPackedThreads, shp[v].smem));
+        occ = std::max(occ, 1);
+        shp[v].grid = std::min<int64_t>(nv, (int64_t)ctx->num_sms * occ);
+        shp[v].strips = rows_var[v] > strip_h;
+        if (shp[v].strips) {
+            shp[v].scratch_off = scratch_ints;
+            scratch_ints += (int64_t)shp[v].grid * (kPackedThreads / G) * stride;
+        }
+    }
+    int32_t* scratch = nullptr;
+    if (scratch_ints > 0) {
+        void* sp = nullptr;
+        SAD_RET(workspace(ctx, WS_SCORE_SCRATCH, sizeof(int32_t) * (size_t)scratch_ints, stream, &sp));
+        scratch = (int32_t*)sp;
+    }
+    SAD_RET(ensure_aux_streams(ctx));
+    TraceScope ts(ctx, SAD_STAGE_SCORES_PACKED, stream);
+    SAD_CUDA(cudaEventRecord(ctx->ev_fork, stream));
+    int used = 0;
+    for (int v = 0; v < kNumVariants; v++) {
+        if (shp[v].grid == 0) continue;
+        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+        GotohArgs a;
+        a.res = S.res;
+        a.pad_off = S.pad_off;
+        a.len = S.len;
+        a.order = base.order;
+        a.bucket_off = base.bucket_off;
+        a.srt = base.srt;
+        a.score_off = base.score_off;
+        a.scores = base.scores;
+        a.subst = base.subst;
+        a.alphabet = S.alphabet;
+        a.go = base.go;
+        a.ge = base.ge;
+        a.G = G;
+        a.prof_stride = shp[v].prof_stride;
+        a.scratch = shp[v].strips ? scratch + shp[v].scratch_off : nullptr;
+        a.scratch_stride = stride;
+        cudaStream_t sv = ctx->aux[used % kAuxStreams];
+        SAD_CUDA(cudaStreamWaitEvent(sv, ctx->ev_fork, 0));
+        pair16_kernel_for(R)<<<shp[v].grid, kPackedThreads, shp[v].smem, sv>>>(
+            d_items + first[v], first[v + 1] - first[v], d_heads + v, a);
+        SAD_LAUNCHED();
+        used++;
+    }
+    if (!singles.empty()) {
+        // queries too long for a packed profile: 32-bit kernel, int8 profile, G = 32, R = 32
+        constexpr int R1 = 32, G1 = 32, T1 = 128;
+        KernelFn fn = kernel_for(R1);
+        GotohArgs a;
+        a.res = S.res;
+        a.pad_off = S.pad_off;
+        a.len = S.len;
+        a.order = base.order;
+        a.bucket_off = base.bucket_off;
+        a.srt = base.srt;
+        a.score_off = base.score_off;
+        a.scores = base.scores;
+        a.subst = base.subst;
+        a.alphabet = S.alphabet;
+        a.go = base.go;
+        a.ge = base.ge;
+        a.G = G1;
+        a.prof_stride = (int32_t)round_up(std::max<int32_t>(singles_rows, 1), R1 * G1);
+        a.scratch_stride = stride;
+        const size_t smem = (size_t)S.alphabet * a.prof_stride;
+        SAD_CHECK(smem <= ctx->smem_optin, SAD_EINVAL, "query profile of %zu bytes exceeds shared memory", smem);
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
+        int occ = 0;
+        SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, T1, smem));
+        const int grid = (int)std::min<int64_t>((int64_t)singles.size(), (int64_t)ctx->num_sms * std::max(occ, 1));
+        void* sp = nullptr;
+        SAD_RET(workspace(ctx, WS_SCORE_SCRATCH_LONG, sizeof(int32_t) * (size_t)grid * (T1 / G1) * stride, stream,
+                          &sp));
+        a.scratch = (int32_t*)sp;
+        cudaStream_t sv = ctx->aux[used % kAuxStreams];
+        SAD_CUDA(cudaStreamWaitEvent(sv, ctx->ev_fork, 0));
+        fn<<<grid, T1, smem, sv>>>(d_items + first_single, (int32_t)singles.size(), d_heads + kNumVariants, a);
+        SAD_LAUNCHED();
+        used++;
+    }
+    for (int u = 0; u < std::min(used, kAuxStreams); u++) {
+        SAD_CUDA(cudaEventRecord(ctx->ev_join[u], ctx->aux[u]));
+        SAD_CUDA(cudaStreamWaitEvent(stream, ctx->ev_join[u], 0));
+    }
+    return SAD_OK;
 }
 
 int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, const int32_t* d_order,
@@ -422,6 +898,10 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
             first += nb;
         }
     } else {
+        if (fits_packed16(S, h_subst, go, ge)) {
+            SAD_RET(launch_packed(ctx, S, h_bo, h_order, srt, L, stream));
+            return SAD_OK;
+        }
         // persistent: one launch over every bucket's rows, longest first
         std::vector<int64_t> cost(items.size());
         std::vector<int32_t> idx(items.size());
@@ -458,6 +938,47 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
 }
 
 }  // namespace sad
+
+extern "C" int sad_scores_set_variants(sad_ctx* ctx_in, const int32_t* upper, const int32_t* R,
+                                       const int32_t* G, int32_t nbins) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(nbins >= 0 && nbins <= ScoreTuning::kMaxBins, SAD_EINVAL, "nbins = %d outside 0..%d", nbins,
+              ScoreTuning::kMaxBins);
+    SAD_CHECK(nbins == 0 || (upper && R && G), SAD_EINVAL, "a table pointer is NULL");
+    for (int32_t b = 0; b < nbins; b++) {
+        SAD_CHECK(variant_index(R[b], G[b]) >= 0, SAD_EINVAL,
+                  "bin %d: no packed kernel with R = %d rows per lane and G = %d lanes", b, R[b], G[b]);
+        SAD_CHECK(b == 0 || upper[b] > upper[b - 1], SAD_EINVAL, "bin bounds must increase");
+    }
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->tuning.nbins = nbins;
+    for (int32_t b = 0; b < nbins; b++) {
+        ctx->tuning.upper[b] = upper[b];
+        ctx->tuning.R[b] = R[b];
+        ctx->tuning.G[b] = G[b];
+    }
+    return SAD_OK;
+}
+
+extern "C" int sad_scores_get_variants(sad_ctx* ctx_in, int32_t* upper, int32_t* R, int32_t* G,
+                                       int32_t max_bins, int32_t* nbins) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(nbins != nullptr, SAD_EINVAL, "nbins is NULL");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    *nbins = ctx->tuning.nbins;
+    for (int32_t b = 0; b < ctx->tuning.nbins && b < max_bins; b++) {
+        upper[b] = ctx->tuning.upper[b];
+        R[b] = ctx->tuning.R[b];
+        G[b] = ctx->tuning.G[b];
+    }
+    return SAD_OK;
+}
 
 extern "C" int sad_scores_size(const int32_t* bucket_offsets, int32_t p, int32_t mem, int64_t* total) {
     using namespace sad;

@@ -569,7 +569,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     {
     TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
     if (smem > 48 * 1024)
-        SAD_CUDA(cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_count));
     k_count<<<n, kCountThreads, smem, stream>>>(S.res, S.pad_off, S.len, k, A2, Vs, cm, T, cap,
                                                (uint8_t*)c8, planes, (const int64_t*)(dm + o_exoff),
                                                ex_tau, ex_val, d_nex, d_sT);

@@ -368,7 +368,7 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
     const int64_t ntri = (int64_t)ntiles * (ntiles + 1) / 2;
     const int32_t kblocks = (K + kKB - 1) / kKB;
     const size_t smem = (size_t)2 * kStages * kStageBytes + 1024;
-    SAD_CUDA(cudaFuncSetAttribute(k_plane_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm));
     k_plane_gemm<<<(unsigned)ntri, 128, smem, stream>>>(tmap, n, kblocks, ntiles, tab, dloc, dcen, A,
                                                         ctx->d_status);
     SAD_LAUNCHED();

@@ -73,6 +73,8 @@ enum Slot : int {
     WS_SCORE_PLAN,     // Gotoh work items and per-bucket tables
     WS_SCORE_SCRATCH,  // strip-boundary scratch of the Gotoh kernels
     WS_SCORE_OUT,      // staging of scores (host mode)
+    WS_SCORE_ITEMS,    // packed-kernel work items and queue heads
+    WS_SCORE_SCRATCH_LONG,  // strip boundaries of queries too long to pack
     WS_PIPE,           // pipeline intermediates
     WS_NUM_SLOTS
 };
@@ -80,6 +82,16 @@ enum Slot : int {
 struct Buffer {
     void* ptr = nullptr;
     size_t bytes = 0;
+};
+
+// Variant table of the packed alignment kernel: query pairs with at most
+// upper[b] rows use R[b] rows per lane and G[b] lanes per subject.
+struct ScoreTuning {
+    static constexpr int kMaxBins = 16;
+    int nbins = 0;
+    int32_t upper[kMaxBins] = {};
+    int32_t R[kMaxBins] = {};
+    int32_t G[kMaxBins] = {};
 };
 
 struct TraceStage {
@@ -101,6 +113,11 @@ struct sad_ctx {
     void* h_pinned = nullptr;         // small pinned staging area
     size_t h_pinned_bytes = 0;
     std::mutex mu;
+    sad::ScoreTuning tuning;
+    bool aux_ready = false;
+    cudaStream_t aux[8] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[8] = {};
     bool trace_on = false;
     sad::TraceStage trace[SAD_NUM_STAGES];
     std::vector<cudaEvent_t> event_pool;
@@ -115,6 +132,11 @@ int resolve_ctx(sad_ctx* in, sad_ctx** out);
 // Grow-only workspace of a slot; synchronises `stream` before freeing an old
 // buffer. Returns SAD_OK and the pointer, or SAD_ENOMEM.
 int workspace(sad_ctx* ctx, Slot slot, size_t bytes, cudaStream_t stream, void** out);
+
+// Allow kernel `fn` the device's maximum dynamic shared memory. The attribute
+// is process-wide per kernel, so it is raised once (under a lock) and never
+// lowered: concurrent callers with different needs cannot race on it.
+int allow_max_dynamic_smem(sad_ctx* ctx, const void* fn);
 
 // Pinned host scratch of at least `bytes` (grow-only).
 int pinned(sad_ctx* ctx, size_t bytes, cudaStream_t stream, void** out);
@@ -149,6 +171,8 @@ struct DevSeqs {
 // are checked on the device; a bad code sets STATUS_BAD_RESIDUE).
 int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t stream,
                  DevSeqs* out);
+
+constexpr int kAuxStreams = 8;  // forked streams for concurrent kernel variants
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

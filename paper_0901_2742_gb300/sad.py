@@ -77,6 +77,8 @@ def load():
         "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
                                                   i32, P, P, i64, i32, P]),
+        "sad_scores_set_variants": (ctypes.c_int, [P, P, P, P, i32]),
+        "sad_scores_get_variants": (ctypes.c_int, [P, P, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_trace_enable": (ctypes.c_int, [P, i32]),
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -185,7 +187,7 @@ def _ctx(ctx):
     return None if ctx is None else ctx.handle
 
 
-STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores")
+STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed")
 
 
 def trace_enable(on: bool = True, ctx=None):
@@ -199,6 +201,23 @@ def trace_read(ctx=None) -> dict:
     cnt = (ctypes.c_int32 * len(STAGES))()
     _check(load().sad_trace_read(_ctx(ctx), ms, cnt, len(STAGES)))
     return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+
+def set_score_variants(table, ctx=None):
+    """table: list of (upper_rows, R, G); [] restores the built-in cost model."""
+    n = len(table)
+    up = np.array([t[0] for t in table] or [0], np.int32)
+    R = np.array([t[1] for t in table] or [0], np.int32)
+    G = np.array([t[2] for t in table] or [0], np.int32)
+    _check(load().sad_scores_set_variants(_ctx(ctx), up.ctypes.data, R.ctypes.data, G.ctypes.data, n))
+
+
+def get_score_variants(ctx=None):
+    up, R, G = (np.zeros(16, np.int32) for _ in range(3))
+    nb = ctypes.c_int32()
+    _check(load().sad_scores_get_variants(_ctx(ctx), up.ctypes.data, R.ctypes.data, G.ctypes.data, 16,
+                                          ctypes.byref(nb)))
+    return [(int(up[i]), int(R[i]), int(G[i])) for i in range(nb.value)]
 
 
 def launch_count() -> int:
@@ -312,3 +331,129 @@ def pipeline(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: 
                                _ptr(o["bucket_offsets"]), _ptr(o["order"]), _ptr(o["score_offsets"]),
                                _ptr(o["scores"]), capacity, mem, _stream(stream, mem)))
     return o
+
+
+# ---- serving ------------------------------------------------------------------
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
+                ("queue_capacity", ctypes.c_int32)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("residues", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("alphabet", ctypes.c_int32), ("kmer", KmerParams), ("subst", ctypes.c_void_p),
+                ("gap_open", ctypes.c_int32), ("gap_extend", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int64), ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int32), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("jobs_per_s", ctypes.c_double),
+                ("budget_bytes", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
+
+
+def _bind_server(lib):
+    if getattr(lib, "_server_bound", False):
+        return lib
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "sad_server_create": [ctypes.POINTER(ServerConfig), ctypes.POINTER(ctypes.c_void_p)],
+        "sad_server_submit": [P, ctypes.POINTER(Job), ctypes.POINTER(u64)],
+        "sad_server_poll": [P, u64, ctypes.POINTER(i32)],
+        "sad_server_wait": [P, u64, i64],
+        "sad_server_result": [P, u64, P, P, P, P, i64, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)],
+        "sad_server_release": [P, u64],
+        "sad_server_cancel": [P, u64],
+        "sad_server_get_stats": [P, ctypes.POINTER(ServerStats)],
+        "sad_server_destroy": [P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = args
+    lib._server_bound = True
+    return lib
+
+
+class Server:
+    """Continuous-batching server of partition-and-score jobs (sad_server_*)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget: int = 0, queue_capacity: int = 4096):
+        self.lib = _bind_server(load())
+        h = ctypes.c_void_p()
+        cfg = ServerConfig(device, slots, hbm_budget, queue_capacity)
+        _check(self.lib.sad_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, residues, offsets, alphabet, k, p, subst, gap_open, gap_extend, cap=0,
+               kmer_alphabet=None, class_map=None) -> int:
+        res, offs = _host(residues, np.uint8), _host(offsets, np.int64)
+        S = _host(subst, np.int8)
+        cm = None if class_map is None else _host(class_map, np.uint8)
+        kp = KmerParams(k, kmer_alphabet or alphabet, None if cm is None else cm.ctypes.data, cap, p)
+        job = Job(res.ctypes.data, offs.ctypes.data, len(offs) - 1, alphabet, kp, S.ctypes.data, gap_open,
+                  gap_extend)
+        jid = ctypes.c_uint64()
+        _check(self.lib.sad_server_submit(self.handle, ctypes.byref(job), ctypes.byref(jid)))
+        self._keep[jid.value] = p
+        return jid.value
+
+    def poll(self, job_id) -> int:
+        st = ctypes.c_int32()
+        rc = self.lib.sad_server_poll(self.handle, job_id, ctypes.byref(st))
+        if rc not in (SAD_OK,) and st.value != JOB_FAILED:
+            _check(rc)
+        return st.value
+
+    def wait(self, job_id, timeout_ms: int = -1) -> int:
+        """Returns the status code (SAD_OK, SAD_EBUSY on timeout, SAD_ECANCELED, or the job's error)."""
+        return self.lib.sad_server_wait(self.handle, job_id, timeout_ms)
+
+    def error(self) -> str:
+        return self.lib.sad_last_error().decode(errors="replace")
+
+    def result(self, job_id, n: int) -> dict:
+        p = self._keep[job_id]
+        cnt = ctypes.c_int64()
+        lat = ctypes.c_double()
+        _check(self.lib.sad_server_result(self.handle, job_id, None, None, None, None, 0, ctypes.byref(cnt),
+                                          None) if False else SAD_OK)
+        rc = self.lib.sad_server_result(self.handle, job_id, None, None, None, None, 1 << 62,
+                                        ctypes.byref(cnt), ctypes.byref(lat))
+        _check(rc)
+        bo = np.zeros(p + 1, np.int32)
+        order = np.zeros(max(n, 1), np.int32)
+        so = np.zeros(p + 1, np.int64)
+        sc = np.zeros(max(cnt.value, 1), np.int32)
+        _check(self.lib.sad_server_result(self.handle, job_id, bo.ctypes.data, order.ctypes.data, so.ctypes.data,
+                                          sc.ctypes.data, len(sc), ctypes.byref(cnt), ctypes.byref(lat)))
+        return dict(bucket_offsets=bo, order=order[:n], score_offsets=so, scores=sc[:cnt.value],
+                    latency_ms=lat.value)
+
+    def release(self, job_id):
+        _check(self.lib.sad_server_release(self.handle, job_id))
+        self._keep.pop(job_id, None)
+
+    def cancel(self, job_id):
+        _check(self.lib.sad_server_cancel(self.handle, job_id))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self.lib.sad_server_get_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            _check(self.lib.sad_server_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -275,3 +275,26 @@ def test_planes_compressed_alphabet(sad):
     w = synth.workload(4, n_override=700)
     want = oracle_all(w)
     assert_rank_equal(run_rank_only(sad, w, 4), want[0])
+
+
+@pytest.mark.parametrize("R", [8, 12, 16, 20, 24, 32])
+@pytest.mark.parametrize("G", [8, 16, 32])
+def test_every_packed_variant_exact(sad, R, G):
+    """Force one packed-kernel variant for every query pair: scores stay exact,
+    including queries that need several strips of G x R rows."""
+    rng = np.random.default_rng(R * 100 + G)
+    lens = list(rng.integers(1, 300, 30)) + [G * R - 1, G * R, G * R + 1, 3 * G * R + 5, 0]
+    seqs = [list(rng.integers(0, 20, L)) for L in lens]
+    res, offs = synth.pack(seqs)
+    n = len(seqs)
+    order = rng.permutation(n).astype(np.int32)
+    bo = np.array([0, 9, 20, n], np.int32)
+    S = synth.subst_matrix(6)
+    want_so, want_sc = oracle.bucket_pair_scores(res, offs, bo, order, S, -11, -1)
+    sad.set_score_variants([(2 ** 31 - 1, R, G)])
+    try:
+        so, sc = sad.bucket_pair_scores(res, offs, 20, bo, order, S, -11, -1, mode=1)
+    finally:
+        sad.set_score_variants([])
+    np.testing.assert_array_equal(so, want_so)
+    np.testing.assert_array_equal(sc, want_sc)
