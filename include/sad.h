@@ -253,6 +253,20 @@ int sad_scores_set_variants(sad_ctx* ctx, const int32_t* upper, const int32_t* R
 int sad_scores_get_variants(sad_ctx* ctx, int32_t* upper, int32_t* R, int32_t* G, int32_t max_bins,
                             int32_t* nbins);
 
+/* Autotuner: on the caller's own sequences and bucket layout (arguments as
+ * sad_bucket_pair_scores), time every packed-kernel variant on the query
+ * pairs of each length bin (rows in (bin_upper[b-1], bin_upper[b]]), `reps`
+ * times after one warm-up run, with CUDA events on `stream`, and store the
+ * fastest variant of every non-empty bin in ctx's variant table (read it with
+ * sad_scores_get_variants; save and restore it with set). A variant that
+ * cannot hold some pair of a bin in shared memory is not eligible for that
+ * bin. Synchronises `stream`. SAD_EINVAL when the inputs need the 32-bit
+ * kernel (nothing to tune). */
+int sad_scores_autotune(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                        const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
+                        int32_t gap_extend, const int32_t* bin_upper, int32_t nbins, int32_t reps,
+                        int32_t mem, void* stream);
+
 /* ---- both stages ------------------------------------------------------- */
 
 /* sad_kmer_rank, sad_partition and sad_bucket_pair_scores in one call, with

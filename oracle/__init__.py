@@ -51,6 +51,8 @@ def _bind(lib):
     lib.orc_kmer_histograms.argtypes = [P, P, i32, P, i32, i32, P, i64]
     lib.orc_kmer_rank.restype = ctypes.c_int
     lib.orc_kmer_rank.argtypes = [P, P, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P, P]
+    lib.orc_kmer_rows.restype = ctypes.c_int
+    lib.orc_kmer_rows.argtypes = [P, P, i32, i32, P, i32, i32, i32, P, i32, i32, P, P, P]
     lib.orc_partition.restype = ctypes.c_int
     lib.orc_partition.argtypes = [i32, P, P, i32, P, P, P]
     lib.orc_gotoh.restype = i64
@@ -122,6 +124,25 @@ def kmer_rank(residues, offsets, alphabet, k, p, class_map=None, kmer_alphabet=N
     if rc != 0:
         raise ValueError("oracle kmer_rank: invalid arguments")
     return dict(A=A, dloc=dloc, dcen=dcen, la=la, ga=int(ga[0]), key_a=key_a, key_b=key_b)
+
+
+def kmer_rows(residues, offsets, alphabet, k, p, rows, class_map=None, kmer_alphabet=None, nthreads=None,
+              lib=None):
+    """Selected rows of the k-mer stage: dict(A_rows[len(rows), n], dloc, dcen) for those rows."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    n = len(offs) - 1
+    cm = None if class_map is None else _c(class_map, np.uint8)
+    ka = kmer_alphabet if kmer_alphabet is not None else alphabet
+    rw = _c(rows, np.int32)
+    A = np.zeros((len(rw), n), np.int32)
+    dloc = np.zeros(len(rw), np.uint64)
+    dcen = np.zeros(len(rw), np.uint64)
+    rc = lib.orc_kmer_rows(_ptr(res), _ptr(offs), n, alphabet, _ptr(cm), ka, k, p, _ptr(rw), len(rw),
+                           nthreads or default_threads(), _ptr(A), _ptr(dloc), _ptr(dcen))
+    if rc != 0:
+        raise ValueError("oracle kmer_rows: invalid arguments")
+    return dict(A_rows=A, dloc=dloc, dcen=dcen)
 
 
 def partition(key_a, key_b, p, lib=None):

@@ -214,6 +214,46 @@ int orc_kmer_rank(const uint8_t* res, const int64_t* offs, int32_t n, int32_t al
     return 0;
 }
 
+/* Selected rows of the k-mer stage, for inputs too large to redo in full:
+ * for each listed sequence i, a_ij for every j (A_rows, nrows x n) and its
+ * two fixed-point D sums, exactly as orc_kmer_rank defines them.
+ * Returns 0, or -1 on invalid arguments. */
+int orc_kmer_rows(const uint8_t* res, const int64_t* offs, int32_t n, int32_t alphabet,
+                  const uint8_t* class_map, int32_t kmer_alphabet, int32_t k, int32_t p,
+                  const int32_t* rows, int32_t nrows, int32_t nthreads, int32_t* A_rows,
+                  uint64_t* dloc, uint64_t* dcen) {
+    if (n < 1 || k < 1 || p < 1) return -1;
+    std::vector<KmerCounts> cnt(n);
+    std::vector<int64_t> len(n);
+    parallel_for(n, nthreads, [&](int64_t i) {
+        len[i] = offs[i + 1] - offs[i];
+        cnt[i] = count_kmers(res + offs[i], len[i], class_map, kmer_alphabet, k);
+    });
+    auto block_of = [&](int64_t i) {
+        int64_t b = (i * p) / n;
+        while (b + 1 < p && block_begin(b + 1, n, p) <= i) b++;
+        while (b > 0 && block_begin(b, n, p) > i) b--;
+        return b;
+    };
+    for (int32_t r = 0; r < nrows; r++)
+        if (rows[r] < 0 || rows[r] >= n) return -1;
+    parallel_for(nrows, nthreads, [&](int64_t r) {
+        const int32_t i = rows[r];
+        uint64_t sl = 0, sc = 0;
+        const int64_t bi = block_of(i);
+        for (int32_t j = 0; j < n; j++) {
+            const int64_t a = shared_kmers(cnt[i], cnt[j]);
+            A_rows[r * (int64_t)n + j] = (int32_t)a;
+            const uint64_t term = fixed_ratio(a, denom(len[i], len[j], k));
+            sc += term;
+            if (block_of(j) == bi) sl += term;
+        }
+        dloc[r] = sl;
+        dcen[r] = sc;
+    });
+    return 0;
+}
+
 /* Regular-sampling redistribution by rank key (Section 2.3.2).
  * bucket_offsets: p+1; order: n (members of a bucket ascending by index);
  * pivot_idx: p-1 sequence indices of the pivots (-1 when there is none).

@@ -284,6 +284,49 @@ int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t st
     return SAD_OK;
 }
 
+
+int trace_reset(sad_ctx* ctx, bool on) {
+    for (auto& st : ctx->trace) {
+        for (auto& pr : st.pending) {
+            cudaEventSynchronize(pr.second);
+            ctx->event_pool.push_back(pr.first);
+            ctx->event_pool.push_back(pr.second);
+        }
+        st.pending.clear();
+        st.ms = 0;
+        st.count = 0;
+    }
+    ctx->trace_on = on;
+    return SAD_OK;
+}
+
+int trace_collect(sad_ctx* ctx, double* ms, int32_t* counts, int32_t nstages) {
+    for (int s = 0; s < SAD_NUM_STAGES; s++) {
+        auto& st = ctx->trace[s];
+        for (auto& pr : st.pending) {
+            SAD_CUDA(cudaEventSynchronize(pr.second));
+            float t = 0;
+            SAD_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+            st.ms += t;
+            st.count++;
+            ctx->event_pool.push_back(pr.first);
+            ctx->event_pool.push_back(pr.second);
+        }
+        st.pending.clear();
+        if (s < nstages) {
+            ms[s] = st.ms;
+            counts[s] = st.count;
+        }
+        st.ms = 0;
+        st.count = 0;
+    }
+    for (int s = SAD_NUM_STAGES; s < nstages; s++) {
+        ms[s] = 0;
+        counts[s] = 0;
+    }
+    return SAD_OK;
+}
+
 }  // namespace sad
 
 extern "C" {
@@ -337,17 +380,7 @@ int sad_trace_enable(sad_ctx* ctx_in, int32_t on) {
     sad_ctx* ctx = nullptr;
     SAD_RET(sad::resolve_ctx(ctx_in, &ctx));
     std::lock_guard<std::mutex> lock(ctx->mu);
-    for (auto& st : ctx->trace) {
-        for (auto& pr : st.pending) {
-            cudaEventSynchronize(pr.second);
-            ctx->event_pool.push_back(pr.first);
-            ctx->event_pool.push_back(pr.second);
-        }
-        st.pending.clear();
-        st.ms = 0;
-        st.count = 0;
-    }
-    ctx->trace_on = on != 0;
+    sad::trace_reset(ctx, on != 0);
     return SAD_OK;
 }
 
@@ -357,30 +390,7 @@ int sad_trace_read(sad_ctx* ctx_in, double* ms, int32_t* counts, int32_t nstages
     sad_ctx* ctx = nullptr;
     SAD_RET(sad::resolve_ctx(ctx_in, &ctx));
     std::lock_guard<std::mutex> lock(ctx->mu);
-    for (int s = 0; s < SAD_NUM_STAGES; s++) {
-        auto& st = ctx->trace[s];
-        for (auto& pr : st.pending) {
-            SAD_CUDA(cudaEventSynchronize(pr.second));
-            float t = 0;
-            SAD_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
-            st.ms += t;
-            st.count++;
-            ctx->event_pool.push_back(pr.first);
-            ctx->event_pool.push_back(pr.second);
-        }
-        st.pending.clear();
-        if (s < nstages) {
-            ms[s] = st.ms;
-            counts[s] = st.count;
-        }
-        st.ms = 0;
-        st.count = 0;
-    }
-    for (int s = SAD_NUM_STAGES; s < nstages; s++) {
-        ms[s] = 0;
-        counts[s] = 0;
-    }
-    return SAD_OK;
+    return sad::trace_collect(ctx, ms, counts, nstages);
 }
 
 const char* sad_version(void) { return "sad-gb300 0.1 (sm_103a)"; }

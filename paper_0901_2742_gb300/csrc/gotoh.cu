@@ -634,6 +634,19 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
                 int best = -1;
                 double bc = 1e300;
                 const ScoreTuning& tu = ctx->tuning;
+                if (tu.filter) {
+                    // autotuning: one length bin, one forced variant, nothing else
+                    const int fv = variant_index(tu.force_R, tu.force_G);
+                    if (rows <= tu.lo || rows > tu.hi) continue;
+                    if (fv < 0 || !fits(fv)) {
+                        ctx->tuning.skipped = true;  // this variant cannot serve the whole bin
+                        continue;
+                    }
+                    by_var[fv].push_back(GotohItem{b, qp, v0, v1});
+                    cost_var[fv].push_back(packed_cost(std::max(rows, 1), navg, tu.force_R, tu.force_G) * (v1 - v0));
+                    rows_var[fv] = std::max(rows_var[fv], rows);
+                    continue;
+                }
                 for (int t = 0; t < tu.nbins && best < 0; t++)
                     if (rows <= tu.upper[t]) best = variant_index(tu.R[t], tu.G[t]);
                 if (best >= 0 && fits(best)) {
@@ -961,6 +974,91 @@ extern "C" int sad_scores_set_variants(sad_ctx* ctx_in, const int32_t* upper, co
         ctx->tuning.G[b] = G[b];
     }
     return SAD_OK;
+}
+
+extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                                   const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
+                                   int32_t gap_extend, const int32_t* bin_upper, int32_t nbins, int32_t reps,
+                                   int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(seqs && bucket_offsets && subst && bin_upper, SAD_EINVAL, "a required pointer is NULL");
+    SAD_CHECK(p >= 1 && nbins >= 1 && nbins <= ScoreTuning::kMaxBins && reps >= 1, SAD_EINVAL,
+              "invalid p, nbins or reps");
+    for (int32_t b = 1; b < nbins; b++) SAD_CHECK(bin_upper[b] > bin_upper[b - 1], SAD_EINVAL, "bins must increase");
+    SAD_CHECK(gap_open <= 0 && gap_extend <= 0, SAD_EINVAL, "gap costs must be <= 0");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    DevSeqs S;
+    SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
+    SAD_CHECK(fits_packed16(S, subst, gap_open, gap_extend), SAD_EINVAL,
+              "these sequences and costs need the 32-bit kernel; there is nothing to tune");
+    const int32_t n = S.n;
+    const int32_t* dbo = bucket_offsets;
+    const int32_t* dord = order;
+    if (mem == SAD_MEM_HOST) {
+        void* st = nullptr;
+        SAD_RET(workspace(ctx, WS_PART_OUT, 4ull * (p + 1 + n) + 1024, stream, &st));
+        SAD_CUDA(cudaMemcpyAsync(st, bucket_offsets, 4ull * (p + 1), cudaMemcpyHostToDevice, stream));
+        if (n) SAD_CUDA(cudaMemcpyAsync((int32_t*)st + p + 1, order, 4ull * n, cudaMemcpyHostToDevice, stream));
+        dbo = (const int32_t*)st;
+        dord = (const int32_t*)st + p + 1;
+    }
+    int64_t total = 0;
+    {
+        std::vector<int32_t> hbo((size_t)p + 1);
+        SAD_RET(arg_to_host(dbo, 4ull * (p + 1), SAD_MEM_DEVICE, stream, hbo.data()));
+        for (int32_t b = 0; b < p; b++) total += (int64_t)(hbo[b + 1] - hbo[b]) * (hbo[b + 1] - hbo[b] + 1) / 2;
+    }
+    void* sw = nullptr;
+    SAD_RET(workspace(ctx, WS_SCORE_OUT, 4ull * (total + 1), stream, &sw));
+    const bool trace_was_on = ctx->trace_on;
+    ScoreTuning table = ctx->tuning;
+    table.nbins = 0;
+    int rc = SAD_OK;
+    for (int32_t b = 0; b < nbins && rc == SAD_OK; b++) {
+        double best_ms = 1e300;
+        int best_R = 0, best_G = 0;
+        for (int ri = 0; ri < kNumR && rc == SAD_OK; ri++)
+            for (int gi = 0; gi < kNumG && rc == SAD_OK; gi++) {
+                ScoreTuning& tu = ctx->tuning;
+                tu.filter = true;
+                tu.lo = b == 0 ? 0 : bin_upper[b - 1];
+                tu.hi = bin_upper[b];
+                tu.force_R = kPackedR[ri];
+                tu.force_G = kPackedG[gi];
+                tu.skipped = false;
+                trace_reset(ctx, true);
+                for (int32_t r = 0; r <= reps && rc == SAD_OK; r++) {
+                    if (r == 1) trace_reset(ctx, true);  // the first run warms up
+                    int64_t tot = 0;
+                    rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend,
+                                              SAD_SCORES_PERSISTENT, nullptr, (int32_t*)sw, total, &tot, stream);
+                }
+                double ms[SAD_NUM_STAGES];
+                int32_t cnt[SAD_NUM_STAGES];
+                if (rc == SAD_OK) rc = trace_collect(ctx, ms, cnt, SAD_NUM_STAGES);
+                if (rc == SAD_OK && !ctx->tuning.skipped && cnt[SAD_STAGE_SCORES_PACKED] > 0 &&
+                    ms[SAD_STAGE_SCORES_PACKED] < best_ms) {
+                    best_ms = ms[SAD_STAGE_SCORES_PACKED];
+                    best_R = kPackedR[ri];
+                    best_G = kPackedG[gi];
+                }
+            }
+        if (best_R > 0) {
+            table.upper[table.nbins] = bin_upper[b];
+            table.R[table.nbins] = best_R;
+            table.G[table.nbins] = best_G;
+            table.nbins++;
+        }
+    }
+    table.filter = false;
+    ctx->tuning = table;
+    trace_reset(ctx, trace_was_on);
+    return rc;
 }
 
 extern "C" int sad_scores_get_variants(sad_ctx* ctx_in, int32_t* upper, int32_t* R, int32_t* G,

@@ -92,6 +92,11 @@ struct ScoreTuning {
     int32_t upper[kMaxBins] = {};
     int32_t R[kMaxBins] = {};
     int32_t G[kMaxBins] = {};
+    // autotuning in progress: only query pairs with lo < rows <= hi are
+    // scored, all with variant (force_R, force_G)
+    bool filter = false;
+    bool skipped = false;  // set when a pair of the bin did not fit the forced variant
+    int32_t lo = 0, hi = 0, force_R = 0, force_G = 0;
 };
 
 struct TraceStage {
@@ -175,6 +180,11 @@ int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t st
 constexpr int kAuxStreams = 8;  // forked streams for concurrent kernel variants
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Tracer internals (the caller holds ctx->mu): clear and switch on/off; wait
+// for the recorded events and report per-stage milliseconds and counts.
+int trace_reset(sad_ctx* ctx, bool on);
+int trace_collect(sad_ctx* ctx, double* ms, int32_t* counts, int32_t nstages);
 
 // Records CUDA events around a stage on `stream` when the context traces.
 class TraceScope {

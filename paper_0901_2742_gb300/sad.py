@@ -78,6 +78,8 @@ def load():
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
                                                   i32, P, P, i64, i32, P]),
         "sad_scores_set_variants": (ctypes.c_int, [P, P, P, P, i32]),
+        "sad_scores_autotune": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32, P, i32, i32,
+                                               i32, P]),
         "sad_scores_get_variants": (ctypes.c_int, [P, P, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_trace_enable": (ctypes.c_int, [P, i32]),
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
@@ -210,6 +212,24 @@ def set_score_variants(table, ctx=None):
     R = np.array([t[1] for t in table] or [0], np.int32)
     G = np.array([t[2] for t in table] or [0], np.int32)
     _check(load().sad_scores_set_variants(_ctx(ctx), up.ctypes.data, R.ctypes.data, G.ctypes.data, n))
+
+
+DEFAULT_TUNING_BINS = (64, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024, 1536, 2048, 4096, 2 ** 31 - 1)
+
+
+def autotune_scores(residues, offsets, alphabet, bucket_offsets, order, subst, gap_open, gap_extend,
+                    bins=DEFAULT_TUNING_BINS, reps=2, ctx=None, stream=None):
+    """sad_scores_autotune on this layout; returns the stored variant table."""
+    mem = _mode(residues, offsets, bucket_offsets, order)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    bo, od = _as(bucket_offsets, np.int32, mem), _as(order, np.int32, mem)
+    S = _host(subst, np.int8)
+    up = np.asarray(bins, np.int32)
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_scores_autotune(_ctx(ctx), ctypes.byref(ss), _ptr(bo), _ptr(od), bo.shape[0] - 1, S.ctypes.data,
+                                      gap_open, gap_extend, up.ctypes.data, len(up), reps, mem,
+                                      _stream(stream, mem)))
+    return get_score_variants(ctx)
 
 
 def get_score_variants(ctx=None):

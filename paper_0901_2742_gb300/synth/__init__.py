@@ -171,8 +171,7 @@ def workload(cfg: int, seed: int | None = None, n_override: int | None = None) -
         fams = [50] * (n // 50) + ([n % 50] if n % 50 else [])
         res, offs = families(seed, fams, 316, LEN_NORMAL, 316.0, 60.0, 50, 800)
         cap = 0 if cfg == 2 else 4
-        name = ("N=2000 L~N(316,60)[50,800] 40x50 families k=3 p=16"
-                + (" uint8 min-sum" if cap == 0 else " cap-4 planes"))
+        name = f"N={n} L~N(316,60)[50,800] {n // 50}x50 families k=3 p=16"
         return Workload(name, res, offs, k=3, p=16, cap=cap, kmer_alphabet=20, class_map=None,
                         **common)
     if cfg == 4:

@@ -298,3 +298,89 @@ def test_every_packed_variant_exact(sad, R, G):
         sad.set_score_variants([])
     np.testing.assert_array_equal(so, want_so)
     np.testing.assert_array_equal(sc, want_sc)
+
+
+def test_autotuned_variants_stay_exact(sad):
+    """The autotuner only picks speeds: after tuning on the paper-scale layout
+    the scores are still those of the oracle."""
+    w = synth.workload(2)
+    want = oracle_all(w, "cfg2")
+    bo, od = want[1]["bucket_offsets"], want[1]["order"]
+    table = sad.autotune_scores(w.residues, w.offsets, w.alphabet, bo, od, w.subst, w.gap_open, w.gap_extend,
+                                reps=1)
+    try:
+        assert len(table) >= 1
+        for upper, R, G in table:
+            assert R in (8, 12, 16, 20, 24, 32) and G in (8, 16, 32)
+        so, sc = sad.bucket_pair_scores(w.residues, w.offsets, w.alphabet, bo, od, w.subst, w.gap_open,
+                                        w.gap_extend, mode=1)
+        np.testing.assert_array_equal(sc, want[3])
+    finally:
+        sad.set_score_variants([])
+
+
+def test_large_uneven_batch_sampled_parity(sad):
+    """N = 20000 (400 Zipf families, lognormal lengths to 2000, 6-letter k = 4,
+    cap 4, p = 64) through sad_pipeline as the benchmark runs it. The oracle
+    recomputes sampled outputs one by one: whole k-mer rows and their D sums
+    (including every local ancestor's row), the global ancestor's choice among
+    them, the rank keys of sampled sequences, the complete partition of the
+    GPU's keys, and sampled alignment scores of every bucket."""
+    import torch
+    w = synth.workload(4)
+    n, p = w.n, w.p
+    res, offs = torch.from_numpy(w.residues).cuda(), torch.from_numpy(w.offsets).cuda()
+    o = sad.pipeline(res, offs, w.alphabet, w.k, p, w.subst, w.gap_open, w.gap_extend, cap=w.cap,
+                     kmer_alphabet=w.kmer_alphabet, class_map=w.class_map, mode=1)
+    torch.cuda.synchronize()
+    g = {k: to_np(v) for k, v in o.items()}
+    la, ga = g["la"], int(g["ga"][0])
+    rng = np.random.default_rng(20000)
+    rows = sorted(set(rng.choice(n, 24, replace=False).tolist()) | set(la.tolist()))
+    part = oracle.kmer_rows(w.residues, w.offsets, w.alphabet, w.k, p, rows, class_map=w.class_map,
+                            kmer_alphabet=w.kmer_alphabet)
+    np.testing.assert_array_equal(g["dloc"][rows], part["dloc"])
+    np.testing.assert_array_equal(g["dcen"][rows], part["dcen"])
+    # local ancestors: argmax of D-loc inside each block (lowest index on ties)
+    for b in range(p):
+        lo, hi = b * n // p, (b + 1) * n // p
+        assert la[b] == lo + int(np.argmax(g["dloc"][lo:hi]))
+    # global ancestor: the local ancestor with the largest fixed-point sum to all local ancestors
+    L = w.lengths().astype(np.int64)
+    ridx = {r: t for t, r in enumerate(rows)}
+    scores = []
+    for x in la:
+        s = 0
+        for y in la:
+            a = int(part["A_rows"][ridx[int(x)], int(y)])
+            b_ = min(L[x], L[y]) - w.k + 1
+            s += (a << 32) // b_ if b_ > 0 else 0
+        scores.append(s)
+    assert ga == int(la[int(np.argmax(scores))])
+    # keys of sampled sequences against GA
+    gr = oracle.kmer_rows(w.residues, w.offsets, w.alphabet, w.k, p, [ga], class_map=w.class_map,
+                          kmer_alphabet=w.kmer_alphabet)["A_rows"][0]
+    for i in rows:
+        b_ = min(L[i], L[ga]) - w.k + 1
+        want = (int(gr[i]), int(b_)) if b_ > 0 else (0, 1)
+        assert (int(g["key_a"][i]), int(g["key_b"][i])) == want
+    # the whole partition of the GPU keys
+    pt = oracle.partition(g["key_a"], g["key_b"], p)
+    np.testing.assert_array_equal(g["bucket_offsets"], pt["bucket_offsets"])
+    np.testing.assert_array_equal(g["order"][:n], pt["order"])
+    # sampled alignment scores: a few pairs of every bucket
+    bo, od, so, sc = g["bucket_offsets"], g["order"], g["score_offsets"], g["scores"]
+    checked = 0
+    for b in range(p):
+        nb = int(bo[b + 1] - bo[b])
+        if nb == 0:
+            continue
+        for _ in range(4):
+            u, v = sorted(rng.integers(0, nb, 2).tolist())
+            xi, yi = int(od[bo[b] + u]), int(od[bo[b] + v])
+            x = w.residues[w.offsets[xi]:w.offsets[xi + 1]]
+            y = w.residues[w.offsets[yi]:w.offsets[yi + 1]]
+            want = oracle.gotoh(x, y, w.subst, w.gap_open, w.gap_extend)
+            assert sc[so[b] + oracle.tri_index(u, v, nb)] == want
+            checked += 1
+    assert checked >= 4 * 60

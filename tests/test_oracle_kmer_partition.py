@@ -218,3 +218,16 @@ def test_partition_literal_pivot_positions(orc):
         ys.sort(key=lambda i: (ka[i], i))
         want = [ys[(m - 1) * p + p // 2 - 1] for m in range(1, p)]
         assert orc.partition(ka, kb, p)["pivot_idx"].tolist() == want
+
+
+def test_kmer_rows_agree_with_full_rank(orc):
+    # the row routine used for sampled checks at full size matches the full stage
+    w = synth.workload(4, n_override=400)
+    full = orc.kmer_rank(w.residues, w.offsets, w.alphabet, w.k, w.p, class_map=w.class_map,
+                         kmer_alphabet=w.kmer_alphabet)
+    rows = [0, 7, 199, 399, int(full["ga"])]
+    part = orc.kmer_rows(w.residues, w.offsets, w.alphabet, w.k, w.p, rows, class_map=w.class_map,
+                         kmer_alphabet=w.kmer_alphabet)
+    np.testing.assert_array_equal(part["A_rows"], full["A"][rows])
+    np.testing.assert_array_equal(part["dloc"], full["dloc"][rows])
+    np.testing.assert_array_equal(part["dcen"], full["dcen"][rows])
