@@ -280,6 +280,9 @@ def main():
     w.cap = args.cap
     n, p = w.n, w.p
     dev = torch.device("cuda", local)
+    # work on a created stream: the library replays its batched score graph there
+    # (the legacy default stream cannot be captured into a CUDA graph)
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     res_d = torch.from_numpy(w.residues).to(dev)
     offs_d = torch.from_numpy(w.offsets).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2

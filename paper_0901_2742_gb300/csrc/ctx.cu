@@ -354,6 +354,7 @@ int sad_ctx_destroy(sad_ctx* ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->score_graph) cudaGraphExecDestroy(ctx->score_graph);
     if (ctx->aux_ready) {
         for (int v = 0; v < sad::kAuxStreams; v++) {
             cudaStreamDestroy(ctx->aux[v]);

@@ -604,6 +604,17 @@ int ensure_aux_streams(sad_ctx* ctx) {
     return SAD_OK;
 }
 
+// One kernel launch of the batched score stage.
+struct PackedLaunch {
+    KernelFn fn;
+    int grid, block;
+    size_t smem;
+    const GotohItem* items;
+    int32_t n_items;
+    int32_t* head;
+    GotohArgs args;
+};
+
 int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_bo,
                   const std::vector<int32_t>& h_order, const std::vector<int32_t>& srt,
                   const GotohLaunch& base, cudaStream_t stream) {
@@ -742,13 +753,10 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         scratch = (int32_t*)sp;
     }
     SAD_RET(ensure_aux_streams(ctx));
-    TraceScope ts(ctx, SAD_STAGE_SCORES_PACKED, stream);
-    SAD_CUDA(cudaEventRecord(ctx->ev_fork, stream));
-    int used = 0;
-    for (int v = 0; v < kNumVariants; v++) {
-        if (shp[v].grid == 0) continue;
-        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
-        GotohArgs a;
+    // the launches of this call, as plain records (they also key the graph cache)
+    std::vector<PackedLaunch> recs;
+    auto common_args = [&](GotohArgs& a) {
+        memset(&a, 0, sizeof(a));
         a.res = S.res;
         a.pad_off = S.pad_off;
         a.len = S.len;
@@ -761,57 +769,107 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         a.alphabet = S.alphabet;
         a.go = base.go;
         a.ge = base.ge;
-        a.G = G;
-        a.prof_stride = shp[v].prof_stride;
-        a.scratch = shp[v].strips ? scratch + shp[v].scratch_off : nullptr;
         a.scratch_stride = stride;
-        cudaStream_t sv = ctx->aux[used % kAuxStreams];
-        SAD_CUDA(cudaStreamWaitEvent(sv, ctx->ev_fork, 0));
-        pair16_kernel_for(R)<<<shp[v].grid, kPackedThreads, shp[v].smem, sv>>>(
-            d_items + first[v], first[v + 1] - first[v], d_heads + v, a);
-        SAD_LAUNCHED();
-        used++;
+    };
+    for (int v = 0; v < kNumVariants; v++) {
+        if (shp[v].grid == 0) continue;
+        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+        PackedLaunch L;
+        memset(&L, 0, sizeof(L));
+        common_args(L.args);
+        L.args.G = G;
+        L.args.prof_stride = shp[v].prof_stride;
+        L.args.scratch = shp[v].strips ? scratch + shp[v].scratch_off : nullptr;
+        L.fn = pair16_kernel_for(R);
+        L.grid = shp[v].grid;
+        L.block = kPackedThreads;
+        L.smem = shp[v].smem;
+        L.items = d_items + first[v];
+        L.n_items = first[v + 1] - first[v];
+        L.head = d_heads + v;
+        recs.push_back(L);
     }
     if (!singles.empty()) {
         // queries too long for a packed profile: 32-bit kernel, int8 profile, G = 32, R = 32
         constexpr int R1 = 32, G1 = 32, T1 = 128;
-        KernelFn fn = kernel_for(R1);
-        GotohArgs a;
-        a.res = S.res;
-        a.pad_off = S.pad_off;
-        a.len = S.len;
-        a.order = base.order;
-        a.bucket_off = base.bucket_off;
-        a.srt = base.srt;
-        a.score_off = base.score_off;
-        a.scores = base.scores;
-        a.subst = base.subst;
-        a.alphabet = S.alphabet;
-        a.go = base.go;
-        a.ge = base.ge;
-        a.G = G1;
-        a.prof_stride = (int32_t)round_up(std::max<int32_t>(singles_rows, 1), R1 * G1);
-        a.scratch_stride = stride;
-        const size_t smem = (size_t)S.alphabet * a.prof_stride;
-        SAD_CHECK(smem <= ctx->smem_optin, SAD_EINVAL, "query profile of %zu bytes exceeds shared memory", smem);
-        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
+        PackedLaunch L;
+        memset(&L, 0, sizeof(L));
+        common_args(L.args);
+        L.fn = kernel_for(R1);
+        L.args.G = G1;
+        L.args.prof_stride = (int32_t)round_up(std::max<int32_t>(singles_rows, 1), R1 * G1);
+        L.smem = (size_t)S.alphabet * L.args.prof_stride;
+        SAD_CHECK(L.smem <= ctx->smem_optin, SAD_EINVAL, "query profile of %zu bytes exceeds shared memory",
+                  L.smem);
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)L.fn));
         int occ = 0;
-        SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, T1, smem));
-        const int grid = (int)std::min<int64_t>((int64_t)singles.size(), (int64_t)ctx->num_sms * std::max(occ, 1));
+        SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, T1, L.smem));
+        L.grid = (int)std::min<int64_t>((int64_t)singles.size(), (int64_t)ctx->num_sms * std::max(occ, 1));
         void* sp = nullptr;
-        SAD_RET(workspace(ctx, WS_SCORE_SCRATCH_LONG, sizeof(int32_t) * (size_t)grid * (T1 / G1) * stride, stream,
-                          &sp));
-        a.scratch = (int32_t*)sp;
-        cudaStream_t sv = ctx->aux[used % kAuxStreams];
-        SAD_CUDA(cudaStreamWaitEvent(sv, ctx->ev_fork, 0));
-        fn<<<grid, T1, smem, sv>>>(d_items + first_single, (int32_t)singles.size(), d_heads + kNumVariants, a);
-        SAD_LAUNCHED();
-        used++;
+        SAD_RET(workspace(ctx, WS_SCORE_SCRATCH_LONG, sizeof(int32_t) * (size_t)L.grid * (T1 / G1) * stride,
+                          stream, &sp));
+        L.args.scratch = (int32_t*)sp;
+        L.block = T1;
+        L.items = d_items + first_single;
+        L.n_items = (int32_t)singles.size();
+        L.head = d_heads + kNumVariants;
+        recs.push_back(L);
     }
-    for (int u = 0; u < std::min(used, kAuxStreams); u++) {
-        SAD_CUDA(cudaEventRecord(ctx->ev_join[u], ctx->aux[u]));
-        SAD_CUDA(cudaStreamWaitEvent(stream, ctx->ev_join[u], 0));
+    // queue heads to zero, fork onto the auxiliary streams, one launch each, join
+    auto enqueue = [&](cudaStream_t st) -> int {
+        SAD_CUDA(cudaMemsetAsync(d_heads, 0, heads_bytes, st));
+        SAD_CUDA(cudaEventRecord(ctx->ev_fork, st));
+        int used = 0;
+        for (const PackedLaunch& L : recs) {
+            cudaStream_t sv = ctx->aux[used % kAuxStreams];
+            SAD_CUDA(cudaStreamWaitEvent(sv, ctx->ev_fork, 0));
+            L.fn<<<L.grid, L.block, L.smem, sv>>>(L.items, L.n_items, L.head, L.args);
+            SAD_CUDA(cudaGetLastError());
+            used++;
+        }
+        for (int u = 0; u < std::min(used, kAuxStreams); u++) {
+            SAD_CUDA(cudaEventRecord(ctx->ev_join[u], ctx->aux[u]));
+            SAD_CUDA(cudaStreamWaitEvent(st, ctx->ev_join[u], 0));
+        }
+        return SAD_OK;
+    };
+    // replay the cached graph when this call launches exactly what the last one did
+    std::vector<char> sig(sizeof(PackedLaunch) * recs.size() + sizeof(void*) + sizeof(size_t));
+    {
+        char* q = sig.data();
+        memcpy(q, &d_heads, sizeof(void*));
+        memcpy(q + sizeof(void*), &heads_bytes, sizeof(size_t));
+        if (!recs.empty()) memcpy(q + sizeof(void*) + sizeof(size_t), recs.data(), sizeof(PackedLaunch) * recs.size());
     }
+    if (stream == nullptr) {
+        // the legacy default stream cannot be captured: launch directly
+        TraceScope ts(ctx, SAD_STAGE_SCORES_PACKED, stream);
+        SAD_RET(enqueue(stream));
+        for (size_t t = 0; t < recs.size(); t++) note_launch();
+        return SAD_OK;
+    }
+    if (!ctx->score_graph || ctx->score_graph_sig != sig) {
+        cudaGraph_t graph = nullptr;
+        SAD_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue(stream);
+        const cudaError_t ec = cudaStreamEndCapture(stream, &graph);
+        if (rc != SAD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        SAD_CUDA(ec);
+        if (ctx->score_graph) {
+            cudaGraphExecDestroy(ctx->score_graph);
+            ctx->score_graph = nullptr;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->score_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        SAD_CUDA(ei);
+        ctx->score_graph_sig = sig;
+    }
+    TraceScope ts(ctx, SAD_STAGE_SCORES_PACKED, stream);
+    SAD_CUDA(cudaGraphLaunch(ctx->score_graph, stream));
+    for (size_t t = 0; t < recs.size(); t++) note_launch();
     return SAD_OK;
 }
 
@@ -1008,26 +1066,60 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
         dord = (const int32_t*)st + p + 1;
     }
     int64_t total = 0;
+    std::vector<int32_t> hbo((size_t)p + 1), hord((size_t)n);
+    SAD_RET(arg_to_host(dbo, 4ull * (p + 1), SAD_MEM_DEVICE, stream, hbo.data()));
+    SAD_RET(arg_to_host(dord, 4ull * n, SAD_MEM_DEVICE, stream, hord.data()));
+    for (int32_t b = 0; b < p; b++) total += (int64_t)(hbo[b + 1] - hbo[b]) * (hbo[b + 1] - hbo[b] + 1) / 2;
+    // cells of every requested bin, then merge consecutive bins until each
+    // carries at least 3% of all cells: tiny bins would pick on timing noise
+    std::vector<double> bin_cells((size_t)nbins, 0.0);
     {
-        std::vector<int32_t> hbo((size_t)p + 1);
-        SAD_RET(arg_to_host(dbo, 4ull * (p + 1), SAD_MEM_DEVICE, stream, hbo.data()));
-        for (int32_t b = 0; b < p; b++) total += (int64_t)(hbo[b + 1] - hbo[b]) * (hbo[b + 1] - hbo[b] + 1) / 2;
+        std::vector<int32_t> srt;
+        std::vector<int64_t> so;
+        plan_buckets(hbo, hord, S.h_len, p, &srt, &so);
+        for (int32_t b = 0; b < p; b++) {
+            const int32_t lo = hbo[b], nb = hbo[b + 1] - lo;
+            auto len_at = [&](int32_t pos) { return (double)S.h_len[hord[lo + srt[lo + pos]]]; };
+            for (int32_t qp = 0; 2 * qp < nb; qp++) {
+                const double m1 = len_at(2 * qp), m2 = 2 * qp + 1 < nb ? len_at(2 * qp + 1) : 0.0;
+                const int32_t rows = (int32_t)std::max(m1, m2);
+                double sub = 0;
+                for (int32_t v = 2 * qp; v < nb; v++) sub += len_at(v);
+                int32_t bi = 0;
+                while (bi < nbins - 1 && rows > bin_upper[bi]) bi++;
+                bin_cells[bi] += (m1 + m2) * sub;
+            }
+        }
     }
+    double all_cells = 0;
+    for (double c : bin_cells) all_cells += c;
+    std::vector<int32_t> merged;
+    {
+        double acc = 0;
+        for (int32_t b = 0; b < nbins; b++) {
+            acc += bin_cells[b];
+            if (acc >= 0.03 * all_cells || b == nbins - 1) {
+                merged.push_back(bin_upper[b]);
+                acc = 0;
+            }
+        }
+    }
+    const int32_t nm = (int32_t)merged.size();
     void* sw = nullptr;
     SAD_RET(workspace(ctx, WS_SCORE_OUT, 4ull * (total + 1), stream, &sw));
     const bool trace_was_on = ctx->trace_on;
     ScoreTuning table = ctx->tuning;
     table.nbins = 0;
     int rc = SAD_OK;
-    for (int32_t b = 0; b < nbins && rc == SAD_OK; b++) {
+    for (int32_t b = 0; b < nm && rc == SAD_OK; b++) {
         double best_ms = 1e300;
         int best_R = 0, best_G = 0;
         for (int ri = 0; ri < kNumR && rc == SAD_OK; ri++)
             for (int gi = 0; gi < kNumG && rc == SAD_OK; gi++) {
                 ScoreTuning& tu = ctx->tuning;
                 tu.filter = true;
-                tu.lo = b == 0 ? 0 : bin_upper[b - 1];
-                tu.hi = bin_upper[b];
+                tu.lo = b == 0 ? 0 : merged[b - 1];
+                tu.hi = merged[b];
                 tu.force_R = kPackedR[ri];
                 tu.force_G = kPackedG[gi];
                 tu.skipped = false;
@@ -1049,7 +1141,7 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
                 }
             }
         if (best_R > 0) {
-            table.upper[table.nbins] = bin_upper[b];
+            table.upper[table.nbins] = merged[b];
             table.R[table.nbins] = best_R;
             table.G[table.nbins] = best_G;
             table.nbins++;

@@ -488,6 +488,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     std::vector<int32_t> nkb(n), blk(n);
     std::vector<uint64_t> q32(n);
     std::vector<uint32_t> r32(n);
+    std::vector<float> inv(n);
     std::vector<int64_t> exoff(n + 1);
     exoff[0] = 0;
     for (int32_t i = 0; i < n; i++) {
@@ -495,9 +496,11 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         if (nkb[i] >= 1) {
             q32[i] = (1ull << 32) / (uint64_t)nkb[i];
             r32[i] = (uint32_t)((1ull << 32) % (uint64_t)nkb[i]);
+            inv[i] = 1.0f / (float)nkb[i];
         } else {
             q32[i] = 0;
             r32[i] = 0;
+            inv[i] = 0.0f;
         }
         exoff[i + 1] = exoff[i] + (nkb[i] > 0 ? nkb[i] / (T + 1) : 0);
     }
@@ -513,7 +516,8 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         return o;
     };
     const size_t o_nkb = carve(4ull * n), o_blk = carve(4ull * n), o_q = carve(8ull * n),
-                 o_r = carve(4ull * n), o_exoff = carve(8ull * (n + 1)), o_nex = carve(4ull * n),
+                 o_r = carve(4ull * n), o_inv = carve(4ull * n), o_exoff = carve(8ull * (n + 1)),
+                 o_nex = carve(4ull * n),
                  o_sT = carve(4ull * n), o_hidx = carve(4ull * n), o_hlist = carve(4ull * n),
                  o_H = carve(16), o_gsum = carve(8ull * p);
     const size_t host_bytes = o_nex;  // the host-filled prefix
@@ -527,6 +531,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     memcpy(hp + o_blk, blk.data(), 4ull * n);
     memcpy(hp + o_q, q32.data(), 8ull * n);
     memcpy(hp + o_r, r32.data(), 4ull * n);
+    memcpy(hp + o_inv, inv.data(), 4ull * n);
     memcpy(hp + o_exoff, exoff.data(), 8ull * (n + 1));
     SAD_CUDA(cudaMemcpyAsync(misc, pin, host_bytes, cudaMemcpyHostToDevice, stream));
     char* dm = (char*)misc;
@@ -534,6 +539,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     tab.nkb = (const int32_t*)(dm + o_nkb);
     tab.q32 = (const uint64_t*)(dm + o_q);
     tab.r32 = (const uint32_t*)(dm + o_r);
+    tab.inv = (const float*)(dm + o_inv);
     tab.blk = (const int32_t*)(dm + o_blk);
     tab.hidx = (const int32_t*)(dm + o_hidx);
     tab.R = nullptr;

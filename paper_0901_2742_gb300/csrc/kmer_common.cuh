@@ -12,6 +12,7 @@ struct SeqTables {
     const int32_t* nkb;   // |x_i| - k + 1 (may be <= 0: no k-mer fits)
     const uint64_t* q32;  // floor(2^32 / nkb) for nkb >= 1
     const uint32_t* r32;  // 2^32 mod nkb for nkb >= 1
+    const float* inv;     // 1 / nkb rounded to fp32, for nkb >= 1
     const int32_t* blk;   // block of sequence i: largest b with floor(bN/p) <= i
     const int32_t* hidx;  // index among sequences with counts above the threshold, or -1
     const int32_t* R;     // H x H residual numerators of those sequences
@@ -30,6 +31,28 @@ __device__ __forceinline__ uint64_t fixed_term(uint32_t a, int32_t nki, uint64_t
     const uint32_t r = take_i ? ri : rj;
     if (b < 65536) return (uint64_t)a * q + (uint64_t)((a * r) / (uint32_t)b);
     return ((uint64_t)a << 32) / (uint64_t)b;
+}
+
+// The same value as fixed_term without an integer division: the quotient
+// floor(a r / b) (< b < 2^16) is estimated in fp32 from the reciprocal 1/b,
+// whose relative error with the two roundings is below 3 * 2^-24, i.e. below
+// 0.02 in absolute terms; one comparison in each direction then makes it exact.
+__device__ __forceinline__ uint64_t fixed_term_fast(uint32_t a, int32_t nki, uint64_t qi, uint32_t ri,
+                                                    float invi, int32_t nkj, uint64_t qj, uint32_t rj,
+                                                    float invj) {
+    const bool take_i = nki <= nkj;
+    const int32_t b = take_i ? nki : nkj;
+    if (b <= 0) return 0;
+    if (b >= 65536) return ((uint64_t)a << 32) / (uint64_t)b;
+    const uint64_t q = take_i ? qi : qj;
+    const uint32_t r = take_i ? ri : rj;
+    const float inv = take_i ? invi : invj;
+    const uint32_t x = a * r;
+    uint32_t qq = __float2uint_rz(__uint2float_rn(x) * inv);
+    const int64_t rem = (int64_t)x - (int64_t)qq * b;
+    if (rem < 0) qq--;
+    else if (rem >= b) qq++;
+    return (uint64_t)a * q + qq;
 }
 
 __device__ __forceinline__ int32_t residual_at(const SeqTables& t, int32_t hi, int32_t hj) {

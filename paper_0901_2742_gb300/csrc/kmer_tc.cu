@@ -10,19 +10,23 @@
 // the cap comes from the residual matrix of the sequences whose counts exceed
 // it.
 //
-// Kernel: one CTA per 128 x 128 tile of the upper triangle. Warp 0 streams
-// 128 x 128-byte k-blocks of both row panels with TMA (128B swizzle) into a
+// Kernel: persistent CTAs (one per SM) walk a list of 128 x BN tiles (BN = 256
+// when there are enough of them, else 128) in an L2-friendly order. Warp 0
+// streams 128-byte k-blocks of the row panels with TMA (128B swizzle) into a
 // ring of shared-memory stages; one thread of warp 1 issues
-// tcgen05.mma.kind::f8f6f4 (M = N = 128, K = 32 per instruction) into a TMEM
-// accumulator and releases stages with tcgen05.commit; then all four warps
-// read the accumulator with tcgen05.ld (warp w owns rows 32w..32w+31) and
-// reduce the fixed-point terms into the D sums. Every wait is bounded in time;
-// on expiry the kernel sets a status bit, waits (bounded) for its own copies,
+// tcgen05.mma.kind::f8f6f4 (M = 128, N = BN, K = 32 per instruction) into one
+// of two TMEM accumulators and releases stages with tcgen05.commit; warps 2-5
+// read the other accumulator with tcgen05.ld and reduce the fixed-point D
+// terms while the next tile's MMAs run. Every wait is bounded in time; on
+// expiry the kernel sets a status bit, waits (bounded) for its own copies,
 // frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "kmer_stage.cuh"
 
@@ -30,11 +34,8 @@ namespace sad {
 
 namespace {
 
-constexpr int kTM = 128;             // tile rows (M) and columns (N)
+constexpr int kTM = 128;             // tile rows (M)
 constexpr int kKB = 128;             // bytes (= e4m3 elements) per k-block
-constexpr int kStages = 6;
-constexpr int kStageBytes = kTM * kKB;   // one operand panel per stage
-constexpr uint32_t kTmemCols = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -102,18 +103,6 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: kind::f8f6f4, A = B = e4m3, D = f32, K-major A and B,
-// M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTM >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
-
-__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
-}
-
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      bar)
@@ -151,183 +140,249 @@ __device__ __forceinline__ uint64_t transpose_reduce32(uint64_t (&x)[32]) {
     return x[0];
 }
 
+// Column tables of one tile (staged in shared memory by the epilogue warps).
+template <int BN>
 struct ColTab {
-    int32_t nkb[kTM];
-    uint64_t q32[kTM];
-    uint32_t r32[kTM];
-    int32_t blk[kTM];
-    int32_t hidx[kTM];
+    int32_t nkb[BN];
+    uint64_t q32[BN];
+    uint32_t r32[BN];
+    float inv[BN];
+    int32_t blk[BN];
+    int32_t hidx[BN];
 };
 
-__global__ void __launch_bounds__(128, 1)
-k_plane_gemm(const __grid_constant__ CUtensorMap tmap, int32_t n, int32_t kblocks, int32_t ntiles,
-             SeqTables tab, uint64_t* __restrict__ dloc, uint64_t* __restrict__ dcen,
-             int32_t* __restrict__ A, uint32_t* __restrict__ status) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <int BN>
+__host__ __device__ constexpr int kStagesFor() {
+    return BN == 256 ? 4 : 6;
+}
+
+// Instruction descriptor: kind::f8f6f4, A = B = e4m3, D = f32, K-major, M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc_for() {
+    return (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
+
+template <int BN>
+__device__ __forceinline__ void mma_f8n(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc_for<BN>()), "r"(accum));
+}
+
+// Persistent all-pairs plane GEMM. Warp 0 streams the k-blocks of every tile
+// of this CTA with TMA; warp 1 (one thread) issues the MMAs into one of two
+// TMEM accumulators (BN columns each) and hands finished accumulators to the
+// epilogue; warps 2-5 read an accumulator (warp w owns rows 32(w%4)..+31),
+// release it and reduce the fixed-point D terms while the next tile's MMAs
+// run. A tile covers rows i0..i0+127 and columns j0..j0+BN-1; the pair (i, j)
+// is taken when i <= j (i < j: both D sums, i = j: its own), so every
+// unordered pair is counted exactly once whatever the tile shape.
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int32_t n,
+              int32_t kblocks, const int2* __restrict__ tiles, int32_t ntiles, SeqTables tab,
+              uint64_t* __restrict__ dloc, uint64_t* __restrict__ dcen, int32_t* __restrict__ A,
+              uint32_t* __restrict__ status) {
+    constexpr int S = kStagesFor<BN>();
+    constexpr uint32_t kA = kTM * kKB, kB = BN * kKB;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full[kStages];
-    __shared__ __align__(8) uint64_t bar_empty[kStages];
-    __shared__ __align__(8) uint64_t bar_done;
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ __align__(8) uint64_t empty[S];
+    __shared__ __align__(8) uint64_t tfull[2];
+    __shared__ __align__(8) uint64_t tempty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int32_t abort_flag;
-    __shared__ ColTab ct;
-    __shared__ unsigned long long colc[kTM], coll[kTM];
-
+    __shared__ int32_t epi_stop;
+    __shared__ ColTab<BN> ct;
+    __shared__ unsigned long long colc[BN], coll[BN];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // tile (ti, tj), ti <= tj, row-major over the upper triangle
-    const int64_t idx = blockIdx.x;
-    int32_t ti = (int32_t)floor(((2.0 * ntiles + 1.0) -
-                                 sqrt((2.0 * ntiles + 1.0) * (2.0 * ntiles + 1.0) - 8.0 * idx)) / 2.0);
-    if (ti < 0) ti = 0;
-    if (ti > ntiles - 1) ti = ntiles - 1;
-    while (ti > 0 && (int64_t)ti * ntiles - (int64_t)ti * (ti - 1) / 2 > idx) ti--;
-    while (ti + 1 < ntiles && (int64_t)(ti + 1) * ntiles - (int64_t)(ti + 1) * ti / 2 <= idx) ti++;
-    const int32_t tj = ti + (int32_t)(idx - ((int64_t)ti * ntiles - (int64_t)ti * (ti - 1) / 2));
-    const int32_t i0 = ti * kTM, j0 = tj * kTM;
-    const bool diag = ti == tj;
-
-    // 1024-byte aligned stage ring in dynamic shared memory
-    const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t ring = (raw + 1023u) & ~1023u;
-    auto stage_a = [&](int s) { return ring + (uint32_t)(2 * s) * kStageBytes; };
-    auto stage_b = [&](int s) { return ring + (uint32_t)(2 * s + 1) * kStageBytes; };
-
+    const uint32_t ring = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    auto stA = [&](int s) { return ring + (uint32_t)s * (kA + kB); };
+    auto stB = [&](int s) { return ring + (uint32_t)s * (kA + kB) + kA; };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; s++) {
-            mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), 1);
+        for (int s = 0; s < S; s++) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(&bar_done), 1);
+        for (int a = 0; a < 2; a++) {
+            mbar_init(smem_u32(&tfull[a]), 1);
+            mbar_init(smem_u32(&tempty[a]), 4);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
-                     "r"(kTmemCols));
+                     "r"((uint32_t)(2 * BN)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    // column tables of this tile
-    {
-        const int c = threadIdx.x;
-        const int32_t j = j0 + c;
-        const bool ok = j < n;
-        ct.nkb[c] = ok ? tab.nkb[j] : 0;
-        ct.q32[c] = ok ? tab.q32[j] : 0;
-        ct.r32[c] = ok ? tab.r32[j] : 0;
-        ct.blk[c] = ok ? tab.blk[j] : -1;
-        ct.hidx[c] = ok ? tab.hidx[j] : -1;
-        colc[c] = 0;
-        coll[c] = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
+    auto aborted = [&]() { return *(volatile int32_t*)&abort_flag != 0; };
+    auto give_up = [&]() { atomicExch(&abort_flag, 1); };
 
-    if (warp == 0 && lane == 0) {
-        // producer: TMA k-blocks of the row panels i0.. and j0..
-        for (int32_t kb = 0; kb < kblocks; kb++) {
-            const int s = kb % kStages;
-            if (kb >= kStages && !mbar_wait(smem_u32(&bar_empty[s]), ((kb / kStages) + 1) & 1, status)) {
-                atomicExch(&abort_flag, 1);
-                break;
-            }
-            if (*(volatile int32_t*)&abort_flag) break;
-            const uint32_t fb = smem_u32(&bar_full[s]);
-            mbar_expect_tx(fb, 2 * kStageBytes);
-            tma_load_2d(stage_a(s), &tmap, fb, kb * kKB, i0);
-            tma_load_2d(stage_b(s), &tmap, fb, kb * kKB, j0);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        bool ok = true;
-        for (int32_t kb = 0; kb < kblocks && ok; kb++) {
-            const int s = kb % kStages;
-            if (!mbar_wait(smem_u32(&bar_full[s]), (kb / kStages) & 1, status)) {
-                atomicExch(&abort_flag, 1);
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-            for (int k = 0; k < kKB / 32; k++) {
-                const uint64_t da = smem_desc(stage_a(s) + 32u * k);
-                const uint64_t db = smem_desc(stage_b(s) + 32u * k);
-                mma_f8(tmem, da, db, (kb > 0 || k > 0) ? 1u : 0u);
-            }
-            mma_commit(smem_u32(&bar_empty[s]));
-        }
-        mma_commit(smem_u32(&bar_done));
-    }
-    __syncwarp();
-    // epilogue: every warp waits for the accumulator
-    const bool done_ok = mbar_wait(smem_u32(&bar_done), 0, status);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool valid = done_ok && !*(volatile int32_t*)&abort_flag;
-
-    const int32_t r = warp * 32 + lane;
-    const int32_t i = i0 + r;
-    const bool oki = i < n;
-    const int32_t nki = oki ? tab.nkb[i] : 0;
-    const uint64_t qi = oki ? tab.q32[i] : 0;
-    const uint32_t ri = oki ? tab.r32[i] : 0;
-    const int32_t bli = oki ? tab.blk[i] : -2;
-    const int32_t hxi = oki ? tab.hidx[i] : -1;
-    uint64_t rs_c = 0, rs_l = 0;
-#pragma unroll 1
-    for (int c = 0; c < kTM / 32; c++) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * c), v);
-        uint64_t cc[32], cl[32];
-#pragma unroll
-        for (int q = 0; q < 32; q++) {
-            const int col = 32 * c + q;
-            const int32_t j = j0 + col;
-            uint64_t t = 0, tl = 0;
-            if (valid && oki && j < n) {
-                const uint32_t a = (uint32_t)__uint_as_float(v[q]) +
-                                   (uint32_t)residual_at(tab, hxi, ct.hidx[col]);
-                t = fixed_term(a, nki, qi, ri, ct.nkb[col], ct.q32[col], ct.r32[col]);
-                tl = (bli == ct.blk[col]) ? t : 0;
-                if (A) {
-                    A[(int64_t)i * n + j] = (int32_t)a;
-                    if (!diag) A[(int64_t)j * n + i] = (int32_t)a;
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;  // k-blocks issued so far
+            for (int32_t t = blockIdx.x; t < ntiles && !aborted(); t += gridDim.x) {
+                const int32_t i0 = tiles[t].x * kTM, j0 = tiles[t].y * BN;
+                for (int32_t kb = 0; kb < kblocks; kb++) {
+                    const int s = (int)(g % S);
+                    if (g >= (uint32_t)S && !mbar_wait(smem_u32(&empty[s]), ((g / S) + 1) & 1, status)) {
+                        give_up();
+                        break;
+                    }
+                    if (aborted()) break;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, kA + kB);
+                    tma_load_2d(stA(s), &tmA, fb, kb * kKB, i0);
+                    tma_load_2d(stB(s), &tmB, fb, kb * kKB, j0);
+                    g++;
                 }
             }
-            rs_c += t;
-            rs_l += tl;
-            cc[q] = t;
-            cl[q] = tl;
+            // on abort, the last copy issued into every stage lands before the CTA exits (bounded)
+            if (aborted())
+                for (uint32_t h = (g > (uint32_t)S ? g - S : 0); h < g; h++)
+                    mbar_wait(smem_u32(&full[h % S]), (h / S) & 1, status);
         }
-        if (!diag) {
-            const uint64_t sc = transpose_reduce32(cc);
-            const uint64_t sl = transpose_reduce32(cl);
-            if (sc) atomicAdd(&colc[32 * c + lane], (unsigned long long)sc);
-            if (sl) atomicAdd(&coll[32 * c + lane], (unsigned long long)sl);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            int32_t lt = 0;
+            for (int32_t t = blockIdx.x; t < ntiles && !aborted(); t += gridDim.x, lt++) {
+                const int a = lt & 1;
+                if (lt >= 2 && !mbar_wait(smem_u32(&tempty[a]), ((lt >> 1) + 1) & 1, status)) {
+                    give_up();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(a * BN);
+                for (int32_t kb = 0; kb < kblocks; kb++, g++) {
+                    const int s = (int)(g % S);
+                    if (!mbar_wait(smem_u32(&full[s]), (g / S) & 1, status)) {
+                        give_up();
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                    for (int k = 0; k < kKB / 32; k++)
+                        mma_f8n<BN>(acc, smem_desc(stA(s) + 32u * k), smem_desc(stB(s) + 32u * k),
+                                    (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                mma_commit(smem_u32(&tfull[a]));
+            }
         }
-    }
-    if (oki && valid) {
-        if (rs_c) atomicAdd((unsigned long long*)&dcen[i], (unsigned long long)rs_c);
-        if (rs_l) atomicAdd((unsigned long long*)&dloc[i], (unsigned long long)rs_l);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (!diag && valid) {
-        const int32_t j = j0 + threadIdx.x;
-        if (j < n) {
-            if (colc[threadIdx.x]) atomicAdd((unsigned long long*)&dcen[j], colc[threadIdx.x]);
-            if (coll[threadIdx.x]) atomicAdd((unsigned long long*)&dloc[j], coll[threadIdx.x]);
+        __syncwarp();
+    } else {
+        // epilogue warps 2..5; TMEM lane quadrant q = warp % 4
+        const int q = warp & 3;
+        const int et = threadIdx.x - 64;  // 0..127
+        int32_t lt = 0;
+        for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
+            const int a = lt & 1;
+            const int32_t i0 = tiles[t].x * kTM, j0 = tiles[t].y * BN;
+            // one thread samples the abort flag so that all 128 leave together
+            if (et == 0) epi_stop = aborted() ? 1 : 0;
+            epi_barrier();  // also: the previous tile's tables and column sums are no longer read
+            if (epi_stop) break;
+            for (int c = et; c < BN; c += 128) {
+                const int32_t j = j0 + c;
+                const bool ok = j < n;
+                ct.nkb[c] = ok ? tab.nkb[j] : 0;
+                ct.q32[c] = ok ? tab.q32[j] : 0;
+                ct.r32[c] = ok ? tab.r32[j] : 0;
+                ct.inv[c] = ok ? tab.inv[j] : 0.f;
+                ct.blk[c] = ok ? tab.blk[j] : -1;
+                ct.hidx[c] = ok ? tab.hidx[j] : -1;
+                colc[c] = 0;
+                coll[c] = 0;
+            }
+            epi_barrier();
+            const bool ok_wait = mbar_wait(smem_u32(&tfull[a]), (lt >> 1) & 1, status);
+            if (!ok_wait) give_up();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool valid = ok_wait && !aborted();
+            const int32_t i = i0 + 32 * q + lane;
+            const bool oki = i < n;
+            const int32_t nki = oki ? tab.nkb[i] : 0;
+            const uint64_t qi = oki ? tab.q32[i] : 0;
+            const uint32_t ri = oki ? tab.r32[i] : 0;
+            const float invi = oki ? tab.inv[i] : 0.f;
+            const int32_t bli = oki ? tab.blk[i] : -2;
+            const int32_t hxi = oki ? tab.hidx[i] : -1;
+            uint64_t rs_c = 0, rs_l = 0;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; c++) {
+                uint32_t v[32];
+                tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
+                uint64_t cc[32], cl[32];
+#pragma unroll
+                for (int u = 0; u < 32; u++) {
+                    const int col = 32 * c + u;
+                    const int32_t j = j0 + col;
+                    uint64_t tv = 0, tl = 0;
+                    if (valid && oki && j < n && i <= j) {
+                        const uint32_t av = (uint32_t)__uint_as_float(v[u]) +
+                                            (uint32_t)residual_at(tab, hxi, ct.hidx[col]);
+                        tv = fixed_term_fast(av, nki, qi, ri, invi, ct.nkb[col], ct.q32[col], ct.r32[col],
+                                             ct.inv[col]);
+                        tl = (bli == ct.blk[col]) ? tv : 0;
+                        if (A) {
+                            A[(int64_t)i * n + j] = (int32_t)av;
+                            if (i != j) A[(int64_t)j * n + i] = (int32_t)av;
+                        }
+                        rs_c += tv;
+                        rs_l += tl;
+                        if (i == j) {  // the diagonal counts once, for its own row
+                            tv = 0;
+                            tl = 0;
+                        }
+                    }
+                    cc[u] = tv;
+                    cl[u] = tl;
+                }
+                const uint64_t sc = transpose_reduce32(cc);
+                const uint64_t sl = transpose_reduce32(cl);
+                if (sc) atomicAdd(&colc[32 * c + lane], (unsigned long long)sc);
+                if (sl) atomicAdd(&coll[32 * c + lane], (unsigned long long)sl);
+            }
+            // the accumulator is read: hand it back to the MMA warp
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[a]));
+            if (oki && valid) {
+                if (rs_c) atomicAdd((unsigned long long*)&dcen[i], (unsigned long long)rs_c);
+                if (rs_l) atomicAdd((unsigned long long*)&dloc[i], (unsigned long long)rs_l);
+            }
+            epi_barrier();
+            if (valid)
+                for (int c = et; c < BN; c += 128) {
+                    const int32_t j = j0 + c;
+                    if (j < n) {
+                        if (colc[c]) atomicAdd((unsigned long long*)&dcen[j], colc[c]);
+                        if (coll[c]) atomicAdd((unsigned long long*)&dloc[j], coll[c]);
+                    }
+                }
         }
-    }
-    if (warp == 0 && lane == 0 && *(volatile int32_t*)&abort_flag) {
-        // let copies already issued land before the CTA exits (bounded)
-        for (int s = 0; s < kStages; s++) mbar_wait(smem_u32(&bar_full[s]), 0, status);
     }
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols));
+                     "r"((uint32_t)(2 * BN)));
     }
 }
 
@@ -355,22 +410,59 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
     if (n == 0) return SAD_OK;
     SAD_CHECK(K % 16 == 0, SAD_EINVAL, "plane row length %d is not a multiple of 16 bytes", K);
     SAD_RET(get_encoder());
-    CUtensorMap tmap;
+    const int32_t nti = (n + kTM - 1) / kTM;
+    // 128 x 256 tiles when there are enough of them to fill the GPU, else 128 x 128
+    auto count_tiles = [&](int BN) {
+        const int32_t ntj = (n + BN - 1) / BN;
+        int64_t c = 0;
+        for (int32_t ti = 0; ti < nti; ti++)
+            for (int32_t tj = 0; tj < ntj; tj++)
+                if ((int64_t)BN * tj + BN - 1 >= (int64_t)kTM * ti) c++;
+        return c;
+    };
+    const int BN = count_tiles(256) >= ctx->num_sms ? 256 : 128;
+    const int32_t ntj = (n + BN - 1) / BN;
+    // L2-friendly order: groups of 8 row tiles sweep the column tiles together
+    std::vector<int2> tiles;
+    for (int32_t ib = 0; ib < nti; ib += 8)
+        for (int32_t tj = 0; tj < ntj; tj++)
+            for (int32_t ti = ib; ti < std::min(nti, ib + 8); ti++)
+                if ((int64_t)BN * tj + BN - 1 >= (int64_t)kTM * ti) tiles.push_back(make_int2(ti, tj));
+    void* dt = nullptr;
+    SAD_RET(workspace(ctx, WS_GEMM_TILES, sizeof(int2) * tiles.size(), stream, &dt));
+    void* pin = nullptr;
+    SAD_RET(pinned(ctx, sizeof(int2) * tiles.size(), stream, &pin));
+    SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may feed an earlier copy
+    memcpy(pin, tiles.data(), sizeof(int2) * tiles.size());
+    SAD_CUDA(cudaMemcpyAsync(dt, pin, sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, stream));
+    CUtensorMap tmA, tmB;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)K};
-    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)kTM};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult cr = g_encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)planes, dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    const cuuint32_t boxA[2] = {(cuuint32_t)kKB, (cuuint32_t)kTM};
+    const cuuint32_t boxB[2] = {(cuuint32_t)kKB, (cuuint32_t)BN};
+    CUresult cr = g_encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)planes, dims, strides, boxA, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     SAD_CHECK(cr == CUDA_SUCCESS, SAD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-    const int32_t ntiles = (n + kTM - 1) / kTM;
-    const int64_t ntri = (int64_t)ntiles * (ntiles + 1) / 2;
+    cr = g_encode(&tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)planes, dims, strides, boxB, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    SAD_CHECK(cr == CUDA_SUCCESS, SAD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     const int32_t kblocks = (K + kKB - 1) / kKB;
-    const size_t smem = (size_t)2 * kStages * kStageBytes + 1024;
-    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm));
-    k_plane_gemm<<<(unsigned)ntri, 128, smem, stream>>>(tmap, n, kblocks, ntiles, tab, dloc, dcen, A,
-                                                        ctx->d_status);
+    const int32_t ntiles = (int32_t)tiles.size();
+    const int grid = std::min<int32_t>(ntiles, ctx->num_sms);
+    if (BN == 256) {
+        const size_t smem = (size_t)kStagesFor<256>() * (kTM + 256) * kKB + 1024;
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<256>));
+        k_plane_gemm2<256><<<grid, 192, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
+                                                        dloc, dcen, A, ctx->d_status);
+    } else {
+        const size_t smem = (size_t)kStagesFor<128>() * (kTM + 128) * kKB + 1024;
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<128>));
+        k_plane_gemm2<128><<<grid, 192, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
+                                                        dloc, dcen, A, ctx->d_status);
+    }
     SAD_LAUNCHED();
     return SAD_OK;
 }

@@ -76,6 +76,7 @@ enum Slot : int {
     WS_SCORE_ITEMS,    // packed-kernel work items and queue heads
     WS_SCORE_SCRATCH_LONG,  // strip boundaries of queries too long to pack
     WS_PIPE,           // pipeline intermediates
+    WS_GEMM_TILES,     // tile list of the plane GEMM
     WS_NUM_SLOTS
 };
 
@@ -119,6 +120,8 @@ struct sad_ctx {
     size_t h_pinned_bytes = 0;
     std::mutex mu;
     sad::ScoreTuning tuning;
+    cudaGraphExec_t score_graph = nullptr;  // last batched score launch set, replayed while unchanged
+    std::vector<char> score_graph_sig;
     bool aux_ready = false;
     cudaStream_t aux[8] = {};
     cudaEvent_t ev_fork = nullptr;

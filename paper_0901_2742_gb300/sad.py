@@ -218,7 +218,7 @@ DEFAULT_TUNING_BINS = (64, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024
 
 
 def autotune_scores(residues, offsets, alphabet, bucket_offsets, order, subst, gap_open, gap_extend,
-                    bins=DEFAULT_TUNING_BINS, reps=2, ctx=None, stream=None):
+                    bins=DEFAULT_TUNING_BINS, reps=3, ctx=None, stream=None):
     """sad_scores_autotune on this layout; returns the stored variant table."""
     mem = _mode(residues, offsets, bucket_offsets, order)
     res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)

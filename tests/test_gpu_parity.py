@@ -384,3 +384,41 @@ def test_large_uneven_batch_sampled_parity(sad):
             assert sc[so[b] + oracle.tri_index(u, v, nb)] == want
             checked += 1
     assert checked >= 4 * 60
+
+
+def test_batched_scores_graph_capture_and_replay(sad):
+    """On a created stream the batched score launches are captured into a CUDA
+    graph once and replayed while the launch set is unchanged; a different
+    layout recaptures. Every run is exact."""
+    import torch
+    w = synth.workload(2)
+    want = oracle_all(w, "cfg2")
+    bo, od = want[1]["bucket_offsets"], want[1]["order"]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        res, offs = torch.from_numpy(w.residues).cuda(), torch.from_numpy(w.offsets).cuda()
+        dbo, dod = torch.from_numpy(bo).cuda(), torch.from_numpy(od).cuda()
+        l0 = sad.launch_count()
+        for _ in range(3):
+            so, sc = sad.bucket_pair_scores(res, offs, w.alphabet, dbo, dod, w.subst, w.gap_open, w.gap_extend,
+                                            mode=1)
+            s.synchronize()
+            np.testing.assert_array_equal(sc.cpu().numpy(), want[3])
+        assert sad.launch_count() > l0
+        # a different layout (one bucket fewer) must not replay the old graph
+        bo2 = np.array([0, bo[2]] + list(bo[3:]), np.int32)
+        want2 = oracle.bucket_pair_scores(w.residues, w.offsets, bo2, od, w.subst, w.gap_open, w.gap_extend)
+        so2, sc2 = sad.bucket_pair_scores(res, offs, w.alphabet, torch.from_numpy(bo2).cuda(), dod, w.subst,
+                                          w.gap_open, w.gap_extend, mode=1)
+        s.synchronize()
+        np.testing.assert_array_equal(sc2.cpu().numpy(), want2[1])
+
+
+def test_planes_wide_tiles_full_matrix(sad):
+    """N = 5000 (enough 128 x 256 tiles to fill the GPU): the persistent wide-tile
+    GEMM with double-buffered accumulators, every numerator of the full matrix,
+    every D sum and key, with heavy excess residuals (6-letter alphabet, k = 4)."""
+    w = synth.workload(4, n_override=5000)
+    want = oracle_all(w)
+    got = run_rank_only(sad, w, 4)
+    assert_rank_equal(got, want[0])
