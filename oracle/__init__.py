@@ -53,6 +53,10 @@ def _bind(lib):
     lib.orc_kmer_rank.argtypes = [P, P, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P, P]
     lib.orc_kmer_rows.restype = ctypes.c_int
     lib.orc_kmer_rows.argtypes = [P, P, i32, i32, P, i32, i32, i32, P, i32, i32, P, P, P]
+    lib.orc_global_rank.restype = ctypes.c_int
+    lib.orc_global_rank.argtypes = [P, P, i32, P, i32, i32, i32, i32, i32, P, P, P]
+    lib.orc_partition_keys64.restype = ctypes.c_int
+    lib.orc_partition_keys64.argtypes = [i32, P, i32, P, P, P]
     lib.orc_partition.restype = ctypes.c_int
     lib.orc_partition.argtypes = [i32, P, P, i32, P, P, P]
     lib.orc_gotoh.restype = i64
@@ -143,6 +147,36 @@ def kmer_rows(residues, offsets, alphabet, k, p, rows, class_map=None, kmer_alph
     if rc != 0:
         raise ValueError("oracle kmer_rows: invalid arguments")
     return dict(A_rows=A, dloc=dloc, dcen=dcen)
+
+
+def global_rank(residues, offsets, k, p, s, dloc, class_map=None, kmer_alphabet=20, nthreads=None, lib=None):
+    """Globalized rank sums G[n] against s samples per block, and the sample indices [p*s]."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    n = len(offs) - 1
+    cm = None if class_map is None else _c(class_map, np.uint8)
+    dl = _c(dloc, np.uint64)
+    G = np.zeros(max(n, 1), np.uint64)
+    smp = np.zeros(p * s, np.int32)
+    rc = lib.orc_global_rank(_ptr(res), _ptr(offs), n, _ptr(cm), kmer_alphabet, k, p, s,
+                             nthreads or default_threads(), _ptr(dl), _ptr(G), _ptr(smp))
+    if rc != 0:
+        raise ValueError("oracle global_rank: invalid arguments")
+    return G[:n], smp
+
+
+def partition_keys64(keys, p, lib=None):
+    """Regular sampling on uint64 keys: dict(bucket_offsets, order, pivot_idx)."""
+    lib = lib or _load()
+    ky = _c(keys, np.uint64)
+    n = len(ky)
+    bo = np.zeros(p + 1, np.int32)
+    order = np.zeros(max(n, 1), np.int32)
+    piv = np.zeros(max(p - 1, 1), np.int32)
+    rc = lib.orc_partition_keys64(n, _ptr(ky), p, _ptr(bo), _ptr(order), _ptr(piv))
+    if rc != 0:
+        raise ValueError("oracle partition_keys64: invalid arguments")
+    return dict(bucket_offsets=bo, order=order[:n], pivot_idx=piv[:max(p - 1, 0)])
 
 
 def partition(key_a, key_b, p, lib=None):

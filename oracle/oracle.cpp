@@ -112,6 +112,51 @@ struct KeyLess {
 
 }  // namespace
 
+/* Regular-sampling redistribution (Section 2.3.2) under a strict total order
+ * `less` on sequence indices. Each of the p contiguous blocks is sorted, p-1
+ * regular samples are taken per non-empty block (positions floor(j*w/p)),
+ * all samples are sorted, and pivot m (1-based) is the sample at 1-based
+ * position (m-1)*q + max(1, floor(q/2)) where q counts the non-empty blocks.
+ * A sequence goes to the bucket numbered by how many pivots rank strictly
+ * below it. */
+template <class Less>
+void regular_sampling(int32_t n, int32_t p, Less less, int32_t* bucket_offsets, int32_t* order,
+                      int32_t* pivot_idx) {
+    std::vector<int32_t> samples;
+    int32_t q = 0;  // blocks that hold at least one sequence
+    for (int32_t b = 0; b < p; b++) {
+        int64_t lo = block_begin(b, n, p), hi = block_begin(b + 1, n, p);
+        int64_t w = hi - lo;
+        if (w == 0) continue;
+        q++;
+        std::vector<int32_t> blk;
+        for (int64_t i = lo; i < hi; i++) blk.push_back((int32_t)i);
+        std::sort(blk.begin(), blk.end(), less);
+        for (int64_t j = 1; j <= p - 1; j++) samples.push_back(blk[(j * w) / p]);
+    }
+    std::sort(samples.begin(), samples.end(), less);
+    std::vector<int32_t> piv;
+    for (int32_t m = 1; m <= p - 1; m++) {
+        if (q == 0) { pivot_idx[m - 1] = -1; continue; }
+        int64_t pos1 = (int64_t)(m - 1) * q + std::max(1, q / 2);  // 1-based
+        int32_t s = samples[pos1 - 1];
+        pivot_idx[m - 1] = s;
+        piv.push_back(s);
+    }
+    std::vector<int32_t> bucket(n);
+    std::vector<int32_t> count(p, 0);
+    for (int32_t i = 0; i < n; i++) {
+        int32_t c = 0;
+        for (int32_t s : piv) if (less(s, i)) c++;
+        bucket[i] = c;
+        count[c]++;
+    }
+    bucket_offsets[0] = 0;
+    for (int32_t b = 0; b < p; b++) bucket_offsets[b + 1] = bucket_offsets[b] + count[b];
+    std::vector<int32_t> fill(bucket_offsets, bucket_offsets + p);
+    for (int32_t i = 0; i < n; i++) order[fill[bucket[i]]++] = i;
+}
+
 extern "C" {
 
 /* Per-sequence k-mer histograms flattened as (sequence, code, count) triples,
@@ -254,49 +299,70 @@ int orc_kmer_rows(const uint8_t* res, const int64_t* offs, int32_t n, int32_t al
     return 0;
 }
 
-/* Regular-sampling redistribution by rank key (Section 2.3.2).
- * bucket_offsets: p+1; order: n (members of a bucket ascending by index);
- * pivot_idx: p-1 sequence indices of the pivots (-1 when there is none).
+/* Globalized k-mer rank (Section 2.3.1; algorithm box: a sample set of s
+ * sequences per processor, sent to all processors, every sequence ranked
+ * against the s*p samples). Each block is sorted by its local rank (dloc, then
+ * index); its samples are the members at 0-based positions
+ * floor((2j+1) w_b / (2s)), j = 0..s-1 (evenly spaced strata; a member may be
+ * taken twice when w_b < s). G_i = sum over the s*p samples sigma of
+ * floor(a_i,sigma 2^32 / b_i,sigma), a sample taken twice counting twice.
+ * sample_idx: p*s entries, -1 for the slots of an empty block.
  * Returns 0, or -1 on invalid arguments. */
+int orc_global_rank(const uint8_t* res, const int64_t* offs, int32_t n, const uint8_t* class_map,
+                    int32_t kmer_alphabet, int32_t k, int32_t p, int32_t s, int32_t nthreads,
+                    const uint64_t* dloc, uint64_t* G, int32_t* sample_idx) {
+    if (n < 0 || k < 1 || p < 1 || s < 1) return -1;
+    std::vector<int32_t> samples;
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t lo = block_begin(b, n, p), hi = block_begin(b + 1, n, p), w = hi - lo;
+        std::vector<int32_t> blk;
+        for (int64_t i = lo; i < hi; i++) blk.push_back((int32_t)i);
+        std::sort(blk.begin(), blk.end(), [&](int32_t x, int32_t y) {
+            return dloc[x] != dloc[y] ? dloc[x] < dloc[y] : x < y;
+        });
+        for (int32_t j = 0; j < s; j++) {
+            int32_t v = -1;
+            if (w > 0) {
+                v = blk[(size_t)(((int64_t)(2 * j + 1) * w) / (2 * (int64_t)s))];
+                samples.push_back(v);
+            }
+            sample_idx[(int64_t)b * s + j] = v;
+        }
+    }
+    std::vector<KmerCounts> cnt(n);
+    std::vector<int64_t> len(n);
+    parallel_for(n, nthreads, [&](int64_t i) {
+        len[i] = offs[i + 1] - offs[i];
+        cnt[i] = count_kmers(res + offs[i], len[i], class_map, kmer_alphabet, k);
+    });
+    parallel_for(n, nthreads, [&](int64_t i) {
+        uint64_t g = 0;
+        for (int32_t v : samples) g += fixed_ratio(shared_kmers(cnt[i], cnt[v]), denom(len[i], len[v], k));
+        G[i] = g;
+    });
+    return 0;
+}
+
+/* Regular sampling on 64-bit integer rank keys (the globalized rank G), ties
+ * by index. Returns 0, or -1 on invalid arguments. */
+int orc_partition_keys64(int32_t n, const uint64_t* keys, int32_t p, int32_t* bucket_offsets,
+                         int32_t* order, int32_t* pivot_idx) {
+    if (n < 0 || p < 1) return -1;
+    auto less = [&](int32_t i, int32_t j) { return keys[i] != keys[j] ? keys[i] < keys[j] : i < j; };
+    regular_sampling(n, p, less, bucket_offsets, order, pivot_idx);
+    return 0;
+}
+
+/* Regular-sampling redistribution by the rational rank key a/b (Section
+ * 2.3.2). bucket_offsets: p+1; order: n (members of a bucket ascending by
+ * index); pivot_idx: p-1 sequence indices of the pivots (-1 when there is
+ * none). Returns 0, or -1 on invalid arguments. */
 int orc_partition(int32_t n, const int32_t* key_a, const int32_t* key_b, int32_t p,
                   int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx) {
     if (n < 0 || p < 1) return -1;
     for (int32_t i = 0; i < n; i++)
         if (key_a[i] < 0 || key_b[i] < 1 || key_a[i] > key_b[i]) return -1;
-    KeyLess less{key_a, key_b};
-    std::vector<int32_t> samples;
-    int32_t q = 0;  // blocks that hold at least one sequence
-    for (int32_t b = 0; b < p; b++) {
-        int64_t lo = block_begin(b, n, p), hi = block_begin(b + 1, n, p);
-        int64_t w = hi - lo;
-        if (w == 0) continue;
-        q++;
-        std::vector<int32_t> blk;
-        for (int64_t i = lo; i < hi; i++) blk.push_back((int32_t)i);
-        std::sort(blk.begin(), blk.end(), less);
-        for (int64_t j = 1; j <= p - 1; j++) samples.push_back(blk[(j * w) / p]);
-    }
-    std::sort(samples.begin(), samples.end(), less);
-    std::vector<int32_t> piv;
-    for (int32_t m = 1; m <= p - 1; m++) {
-        if (q == 0) { pivot_idx[m - 1] = -1; continue; }
-        int64_t pos1 = (int64_t)(m - 1) * q + std::max(1, q / 2);  // 1-based
-        int32_t s = samples[pos1 - 1];
-        pivot_idx[m - 1] = s;
-        piv.push_back(s);
-    }
-    std::vector<int32_t> bucket(n);
-    std::vector<int32_t> count(p, 0);
-    for (int32_t i = 0; i < n; i++) {
-        int32_t c = 0;
-        for (int32_t s : piv) if (less(s, i)) c++;
-        bucket[i] = c;
-        count[c]++;
-    }
-    bucket_offsets[0] = 0;
-    for (int32_t b = 0; b < p; b++) bucket_offsets[b + 1] = bucket_offsets[b] + count[b];
-    std::vector<int32_t> fill(bucket_offsets, bucket_offsets + p);
-    for (int32_t i = 0; i < n; i++) order[fill[bucket[i]]++] = i;
+    regular_sampling(n, p, KeyLess{key_a, key_b}, bucket_offsets, order, pivot_idx);
     return 0;
 }
 

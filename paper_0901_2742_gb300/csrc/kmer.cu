@@ -472,6 +472,9 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     }
     const int32_t Vs = (int32_t)round_up(V, 64);
     const int32_t T = cap > 0 ? cap : 255;
+    SAD_CHECK(cap == 0 || S.max_len - k + 1 < 65536, SAD_EINVAL,
+              "the threshold-plane path takes sequences of fewer than 65536 k-mers (longest: %d); use cap = 0",
+              S.max_len - k + 1);
     ClassMap cm;
     memset(&cm, 0, sizeof(cm));
     for (int32_t r = 0; r < S.alphabet; r++) cm.c[r] = kp->class_map ? kp->class_map[r] : (uint8_t)r;

@@ -15,7 +15,7 @@
 // streams 128-byte k-blocks of the row panels with TMA (128B swizzle) into a
 // ring of shared-memory stages; one thread of warp 1 issues
 // tcgen05.mma.kind::f8f6f4 (M = 128, N = BN, K = 32 per instruction) into one
-// of two TMEM accumulators and releases stages with tcgen05.commit; warps 2-5
+// of two TMEM accumulators and releases stages with tcgen05.commit; warps 2-9
 // read the other accumulator with tcgen05.ld and reduce the fixed-point D
 // terms while the next tile's MMAs run. Every wait is bounded in time; on
 // expiry the kernel sets a status bit, waits (bounded) for its own copies,
@@ -140,22 +140,46 @@ __device__ __forceinline__ uint64_t transpose_reduce32(uint64_t (&x)[32]) {
     return x[0];
 }
 
-// Column tables of one tile (staged in shared memory by the epilogue warps).
-template <int BN>
-struct ColTab {
-    int32_t nkb[BN];
-    uint64_t q32[BN];
-    uint32_t r32[BN];
-    float inv[BN];
-    int32_t blk[BN];
-    int32_t hidx[BN];
+// Per-column table entry of one tile, staged in shared memory by the epilogue
+// warps; all lanes read the same entry (broadcast), two 16-byte loads.
+struct __align__(16) ColRec {
+    int32_t nkb;
+    uint32_t q32;  // floor(2^32 / nkb) for nkb >= 2 (nkb = 1 is handled apart)
+    uint32_t r32;
+    float inv;
 };
+
+// Less frequently needed per-column fields: block (local D) and excess index.
+struct __align__(8) ColAux {
+    int32_t blk;
+    int32_t hidx;
+};
+
+// floor(a 2^32 / b), b = min(nk_i, nk_j) < 2^16, from 32-bit per-sequence tables
+// (see fixed_term_fast); b = 1 gives a << 32, b <= 0 gives 0.
+__device__ __forceinline__ uint64_t fixed_term32(uint32_t a, int32_t nki, uint32_t qi, uint32_t ri, float invi,
+                                                 const ColRec& c) {
+    const bool take_i = nki <= c.nkb;
+    const int32_t b = take_i ? nki : c.nkb;
+    const uint32_t q = take_i ? qi : c.q32;
+    const uint32_t r = take_i ? ri : c.r32;
+    const float inv = take_i ? invi : c.inv;
+    const uint32_t x = a * r;
+    uint32_t qq = __float2uint_rz(__uint2float_rn(x) * inv);
+    const int32_t rem = (int32_t)(x - qq * (uint32_t)b);  // |rem| < 2b < 2^17
+    qq = rem < 0 ? qq - 1 : (rem >= b ? qq + 1 : qq);
+    const uint64_t t = (uint64_t)a * q + qq;
+    return b <= 0 ? 0ull : (b == 1 ? ((uint64_t)a << 32) : t);
+}
+
+constexpr int kEpiWarps = 8;                       // two per TMEM lane quadrant
+constexpr int kGemmThreads = (2 + kEpiWarps) * 32;  // producer, MMA issuer, epilogue
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 template <int BN>
 __host__ __device__ constexpr int kStagesFor() {
@@ -180,13 +204,13 @@ __device__ __forceinline__ void mma_f8n(uint32_t d_tmem, uint64_t a, uint64_t b,
 // Persistent all-pairs plane GEMM. Warp 0 streams the k-blocks of every tile
 // of this CTA with TMA; warp 1 (one thread) issues the MMAs into one of two
 // TMEM accumulators (BN columns each) and hands finished accumulators to the
-// epilogue; warps 2-5 read an accumulator (warp w owns rows 32(w%4)..+31),
-// release it and reduce the fixed-point D terms while the next tile's MMAs
-// run. A tile covers rows i0..i0+127 and columns j0..j0+BN-1; the pair (i, j)
+// epilogue; warps 2-9 read an accumulator (warp w owns rows 32(w%4)..+31 and
+// one half of the columns), release it and reduce the fixed-point D terms
+// while the next tile's MMAs run. A tile covers rows i0..i0+127 and columns j0..j0+BN-1; the pair (i, j)
 // is taken when i <= j (i < j: both D sums, i = j: its own), so every
 // unordered pair is counted exactly once whatever the tile shape.
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
 k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int32_t n,
               int32_t kblocks, const int2* __restrict__ tiles, int32_t ntiles, SeqTables tab,
               uint64_t* __restrict__ dloc, uint64_t* __restrict__ dcen, int32_t* __restrict__ A,
@@ -201,8 +225,10 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __shared__ uint32_t tmem_slot;
     __shared__ int32_t abort_flag;
     __shared__ int32_t epi_stop;
-    __shared__ ColTab<BN> ct;
-    __shared__ unsigned long long colc[BN], coll[BN];
+    __shared__ ColRec ct[BN];
+    __shared__ ColAux cx[BN];
+    __shared__ int32_t tile_loc;  // does this tile touch a block on both axes?
+    __shared__ unsigned long long colw_c[4][BN], colw_l[4][BN];  // column sums per lane quadrant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t ring = (smem_u32(smem_raw) + 1023u) & ~1023u;
     auto stA = [&](int s) { return ring + (uint32_t)s * (kA + kB); };
@@ -214,7 +240,7 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(smem_u32(&tfull[a]), 1);
-            mbar_init(smem_u32(&tempty[a]), 4);
+            mbar_init(smem_u32(&tempty[a]), kEpiWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -287,45 +313,68 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         __syncwarp();
     } else {
-        // epilogue warps 2..5; TMEM lane quadrant q = warp % 4
+        // epilogue warps 2..9: TMEM lane quadrant q = warp % 4 (rows 32q..32q+31),
+        // column half h; the two warps of a quadrant split the tile's columns
+        const int ew = warp - 2;
         const int q = warp & 3;
-        const int et = threadIdx.x - 64;  // 0..127
+        const int h = ew >> 2;
+        const int et = threadIdx.x - 64;  // 0..255
+        constexpr int kChunks = BN / 64;  // 32-column chunks per warp
         int32_t lt = 0;
         for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
             const int a = lt & 1;
             const int32_t i0 = tiles[t].x * kTM, j0 = tiles[t].y * BN;
-            // one thread samples the abort flag so that all 128 leave together
+            // one thread samples the abort flag so that all epilogue warps leave together
             if (et == 0) epi_stop = aborted() ? 1 : 0;
             epi_barrier();  // also: the previous tile's tables and column sums are no longer read
             if (epi_stop) break;
-            for (int c = et; c < BN; c += 128) {
+            for (int c = et; c < BN; c += 256) {
                 const int32_t j = j0 + c;
-                const bool ok = j < n;
-                ct.nkb[c] = ok ? tab.nkb[j] : 0;
-                ct.q32[c] = ok ? tab.q32[j] : 0;
-                ct.r32[c] = ok ? tab.r32[j] : 0;
-                ct.inv[c] = ok ? tab.inv[j] : 0.f;
-                ct.blk[c] = ok ? tab.blk[j] : -1;
-                ct.hidx[c] = ok ? tab.hidx[j] : -1;
-                colc[c] = 0;
-                coll[c] = 0;
+                ColRec r;
+                ColAux x;
+                if (j < n) {
+                    r.nkb = tab.nkb[j];
+                    r.q32 = (uint32_t)tab.q32[j];  // < 2^31 for nkb >= 2
+                    r.r32 = tab.r32[j];
+                    r.inv = tab.inv[j];
+                    x.blk = tab.blk[j];
+                    x.hidx = tab.hidx[j];
+                } else {
+                    r.nkb = 0;
+                    r.q32 = 0;
+                    r.r32 = 0;
+                    r.inv = 0.f;
+                    x.blk = -1;
+                    x.hidx = -1;
+                }
+                ct[c] = r;
+                cx[c] = x;
+            }
+            if (et == 0) {
+                // blocks are contiguous index ranges: the tile has same-block pairs
+                // only if its row and column block ranges overlap
+                const int32_t ilast = min(i0 + kTM, n) - 1, jlast = min(j0 + BN, n) - 1;
+                tile_loc = (i0 < n && j0 < n && tab.blk[ilast] >= tab.blk[j0] && tab.blk[jlast] >= tab.blk[i0]) ? 1
+                                                                                                          : 0;
             }
             epi_barrier();
+            const bool any_loc = tile_loc != 0;
             const bool ok_wait = mbar_wait(smem_u32(&tfull[a]), (lt >> 1) & 1, status);
             if (!ok_wait) give_up();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool valid = ok_wait && !aborted();
             const int32_t i = i0 + 32 * q + lane;
-            const bool oki = i < n;
+            const bool oki = valid && i < n;
             const int32_t nki = oki ? tab.nkb[i] : 0;
-            const uint64_t qi = oki ? tab.q32[i] : 0;
+            const uint32_t qi = oki ? (uint32_t)tab.q32[i] : 0;
             const uint32_t ri = oki ? tab.r32[i] : 0;
             const float invi = oki ? tab.inv[i] : 0.f;
             const int32_t bli = oki ? tab.blk[i] : -2;
             const int32_t hxi = oki ? tab.hidx[i] : -1;
             uint64_t rs_c = 0, rs_l = 0;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; c++) {
+            for (int cc0 = 0; cc0 < kChunks; cc0++) {
+                const int c = h * kChunks + cc0;
                 uint32_t v[32];
                 tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
                 uint64_t cc[32], cl[32];
@@ -333,47 +382,47 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 for (int u = 0; u < 32; u++) {
                     const int col = 32 * c + u;
                     const int32_t j = j0 + col;
-                    uint64_t tv = 0, tl = 0;
-                    if (valid && oki && j < n && i <= j) {
-                        const uint32_t av = (uint32_t)__uint_as_float(v[u]) +
-                                            (uint32_t)residual_at(tab, hxi, ct.hidx[col]);
-                        tv = fixed_term_fast(av, nki, qi, ri, invi, ct.nkb[col], ct.q32[col], ct.r32[col],
-                                             ct.inv[col]);
-                        tl = (bli == ct.blk[col]) ? tv : 0;
-                        if (A) {
-                            A[(int64_t)i * n + j] = (int32_t)av;
-                            if (i != j) A[(int64_t)j * n + i] = (int32_t)av;
-                        }
-                        rs_c += tv;
-                        rs_l += tl;
-                        if (i == j) {  // the diagonal counts once, for its own row
-                            tv = 0;
-                            tl = 0;
-                        }
+                    const ColRec r = ct[col];
+                    const bool use = oki && j < n && i <= j;
+                    uint32_t av = (uint32_t)__uint_as_float(v[u]);
+                    if (hxi >= 0) {
+                        const int32_t hj = cx[col].hidx;
+                        if (hj >= 0) av += (uint32_t)tab.R[(int64_t)hxi * tab.H + hj];
                     }
-                    cc[u] = tv;
-                    cl[u] = tl;
+                    uint64_t tv = fixed_term32(av, nki, qi, ri, invi, r);
+                    tv = use ? tv : 0;
+                    const uint64_t tl = (any_loc && bli == cx[col].blk) ? tv : 0;
+                    if (A && use) {
+                        A[(int64_t)i * n + j] = (int32_t)av;
+                        if (i != j) A[(int64_t)j * n + i] = (int32_t)av;
+                    }
+                    rs_c += tv;
+                    rs_l += tl;
+                    const bool off_diag = i != j;  // the diagonal counts once, for its own row
+                    cc[u] = off_diag ? tv : 0;
+                    cl[u] = off_diag ? tl : 0;
                 }
-                const uint64_t sc = transpose_reduce32(cc);
-                const uint64_t sl = transpose_reduce32(cl);
-                if (sc) atomicAdd(&colc[32 * c + lane], (unsigned long long)sc);
-                if (sl) atomicAdd(&coll[32 * c + lane], (unsigned long long)sl);
+                // lane l now sums column 32c + l over this warp's 32 rows
+                colw_c[q][32 * c + lane] = transpose_reduce32(cc);
+                colw_l[q][32 * c + lane] = any_loc ? transpose_reduce32(cl) : 0ull;
             }
             // the accumulator is read: hand it back to the MMA warp
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty[a]));
-            if (oki && valid) {
+            if (oki) {
                 if (rs_c) atomicAdd((unsigned long long*)&dcen[i], (unsigned long long)rs_c);
                 if (rs_l) atomicAdd((unsigned long long*)&dloc[i], (unsigned long long)rs_l);
             }
             epi_barrier();
             if (valid)
-                for (int c = et; c < BN; c += 128) {
+                for (int c = et; c < BN; c += 256) {
                     const int32_t j = j0 + c;
                     if (j < n) {
-                        if (colc[c]) atomicAdd((unsigned long long*)&dcen[j], colc[c]);
-                        if (coll[c]) atomicAdd((unsigned long long*)&dloc[j], coll[c]);
+                        const unsigned long long sc = colw_c[0][c] + colw_c[1][c] + colw_c[2][c] + colw_c[3][c];
+                        const unsigned long long sl = colw_l[0][c] + colw_l[1][c] + colw_l[2][c] + colw_l[3][c];
+                        if (sc) atomicAdd((unsigned long long*)&dcen[j], sc);
+                        if (sl) atomicAdd((unsigned long long*)&dloc[j], sl);
                     }
                 }
         }
@@ -455,12 +504,12 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
     if (BN == 256) {
         const size_t smem = (size_t)kStagesFor<256>() * (kTM + 256) * kKB + 1024;
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<256>));
-        k_plane_gemm2<256><<<grid, 192, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
+        k_plane_gemm2<256><<<grid, kGemmThreads, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
                                                         dloc, dcen, A, ctx->d_status);
     } else {
         const size_t smem = (size_t)kStagesFor<128>() * (kTM + 128) * kKB + 1024;
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<128>));
-        k_plane_gemm2<128><<<grid, 192, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
+        k_plane_gemm2<128><<<grid, kGemmThreads, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
                                                         dloc, dcen, A, ctx->d_status);
     }
     SAD_LAUNCHED();

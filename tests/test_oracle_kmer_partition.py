@@ -231,3 +231,43 @@ def test_kmer_rows_agree_with_full_rank(orc):
     np.testing.assert_array_equal(part["A_rows"], full["A"][rows])
     np.testing.assert_array_equal(part["dloc"], full["dloc"][rows])
     np.testing.assert_array_equal(part["dcen"], full["dcen"][rows])
+
+
+def test_globalized_rank_with_every_sequence_sampled_is_centralized(orc):
+    # s = block size: the strata positions floor((2j+1) w / 2w) = j take every
+    # member once, so the sample set is the whole set and G = D-cen exactly
+    w = synth.workload(1, seed=31)
+    n, p = w.n, w.p
+    r = orc.kmer_rank(w.residues, w.offsets, 20, w.k, p)
+    assert n % p == 0
+    G, smp = orc.global_rank(w.residues, w.offsets, w.k, p, n // p, r["dloc"])
+    assert sorted(smp.tolist()) == list(range(n))
+    np.testing.assert_array_equal(G, r["dcen"])
+
+
+def test_globalized_rank_hand_example(orc):
+    # the second golden case (class map, k=1): blocks {0,1} and {2,3,4};
+    # local D: (1.5, 1.5 | 8/3, 2, 5/3) x 2^32. One sample per block:
+    # position floor(w/2): block0 sorted (0,1) -> x1; block1 sorted by dloc (4,3,2) -> x3.
+    # G_i = T(i, x1) + T(i, x3) with F column x1 = (1/2, 1, 1, 1, 0), x3 = (1, 1, 1, 1, 0).
+    import json
+    case = json.load(open(os.path.join(GOLD, "kmer_rank_tiny.json")))["cases"][1]
+    res, offs = synth.pack(case["seqs"])
+    G, smp = orc.global_rank(res, offs, 1, 2, 1, np.array(case["dloc"], np.uint64),
+                             class_map=case["class_map"], kmer_alphabet=2)
+    assert smp.tolist() == [1, 3]
+    two32 = 1 << 32
+    assert G.tolist() == [two32 // 2 + two32, 2 * two32, 2 * two32, 2 * two32, 0]
+
+
+def test_partition_keys64_matches_rational_partition(orc):
+    # 64-bit keys K = floor(a 2^32 / b) order the rational keys exactly for b <= 2^16
+    rng = np.random.default_rng(12)
+    kb = rng.integers(1, 300, 700).astype(np.int32)
+    ka = (rng.random(700) * (kb + 1)).astype(np.int32).clip(0, kb)
+    keys = (ka.astype(np.uint64) << np.uint64(32)) // kb.astype(np.uint64)
+    for p in (1, 2, 7, 16):
+        a = orc.partition(ka, kb, p)
+        b = orc.partition_keys64(keys, p)
+        for f in ("bucket_offsets", "order", "pivot_idx"):
+            np.testing.assert_array_equal(a[f], b[f])
