@@ -259,6 +259,8 @@ def main():
     ap.add_argument("--cap", type=int, default=4, help="0: uint8 CUDA-core k-mer path; >0 planes")
     ap.add_argument("--mode", type=int, default=1, help="0: per-bucket launches, 1: persistent")
     ap.add_argument("--no-tune", action="store_true", help="skip the per-length-bin variant autotuner")
+    ap.add_argument("--global-samples", type=int, default=0,
+                    help="s > 0: partition by the globalized rank against s samples per block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -286,7 +288,9 @@ def main():
     res_d = torch.from_numpy(w.residues).to(dev)
     offs_d = torch.from_numpy(w.offsets).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
-    kw = dict(cap=w.cap, kmer_alphabet=w.kmer_alphabet, class_map=w.class_map, mode=args.mode)
+    gs = args.global_samples
+    kw = dict(cap=w.cap, kmer_alphabet=w.kmer_alphabet, class_map=w.class_map, mode=args.mode,
+              global_samples=gs)
     out_d = sad.pipeline(res_d, offs_d, w.alphabet, w.k, p, w.subst, w.gap_open, w.gap_extend, **kw)
     torch.cuda.synchronize()
     bo = out_d["bucket_offsets"].cpu().numpy()
@@ -362,6 +366,9 @@ def main():
                  "dloc": pinned(n, torch.int64).view(np.uint64), "dcen": pinned(n, torch.int64).view(np.uint64),
                  "la": pinned(p, torch.int32), "ga": pinned(1, torch.int32), "key_a": pinned(n, torch.int32),
                  "key_b": pinned(n, torch.int32)}
+        if gs > 0:
+            out_h["G"] = pinned(n, torch.int64).view(np.uint64)
+            out_h["sample_idx"] = pinned(p * gs, torch.int32)
 
         def step_h():
             sad.pipeline(res_h, offs_h, w.alphabet, w.k, p, w.subst, w.gap_open, w.gap_extend,
@@ -379,6 +386,7 @@ def main():
         e2e_s = sum(times) / len(times)
         h2d = w.residues.nbytes + w.offsets.nbytes
         d2h = 4 * pairs_scored + 8 * (p + 1) + 4 * (p + 1) + 4 * n + 8 * n * 2 + 4 * p + 4 + 4 * n * 2
+        d2h += (8 * n + 4 * p * gs) if gs > 0 else 0
         e2e = {"value": ws * cells / e2e_s / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
 
@@ -397,6 +405,8 @@ def main():
         "config": {"workload": w.name, "n": n, "p": p, "k": w.k,
                    "kmer_path": "uint8 min-sum, CUDA cores" if w.cap == 0 else f"cap-{w.cap} threshold planes, tensor cores",
                    "scores_mode": "persistent" if args.mode == 1 else "one launch per bucket",
+                   "rank": (f"globalized, {gs} samples per block" if gs > 0
+                            else "centralized against the global ancestor"),
                    "parallelism": f"replicas x{ws}", "l2": "flushed between timed steps (256 MiB write)",
                    "score_variants": ([{"rows_le": u, "R": r, "G": g} for u, r, g in tuning]
                                       if tuning else "cost model"),
@@ -419,6 +429,11 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
+    if gs > 0:
+        from paper_0901_2742_gb300 import rank_stats
+        line["rank_table"] = rank_stats.rank_table(out_d["dcen"][:n].cpu().numpy().view(np.uint64),
+                                                   out_d["G"][:n].cpu().numpy().view(np.uint64),
+                                                   out_d["sample_idx"].cpu().numpy())
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -6,7 +6,10 @@
  *      Section 2.3.2 "Redistribution Based on k-mer Rank"):
  *        sad_kmer_rank   counts, all-pairs k-mer similarity, local and global
  *                        ancestors, rank keys against the global ancestor
+ *                        and, optionally, the globalized rank against the
+ *                        sample sets of all blocks (Section 2.3.1)
  *        sad_partition   regular-sampling splitters and p buckets
+ *                        (sad_partition_keys64 for the globalized rank)
  *   2. per-bucket alignment (algorithm box "align sequences in each processor
  *      using any sequential multiple alignment system", Section 2.3.3):
  *        sad_bucket_pair_scores  all-pairs global affine-gap (Gotoh) scores
@@ -88,7 +91,12 @@ typedef struct sad_kmer_params {
     const uint8_t* class_map; /* host, `alphabet` entries, or NULL */
     int32_t cap;             /* 0, or 1..8 */
     int32_t p;               /* number of blocks / buckets, >= 1 */
+    int32_t global_samples;  /* 0, or s in 1..SAD_MAX_GLOBAL_SAMPLES: also compute the
+                              * globalized rank G against s samples per block
+                              * (sad_rank_out.G); sad_pipeline then partitions by G */
 } sad_kmer_params;
+
+#define SAD_MAX_GLOBAL_SAMPLES 1024
 
 /* Outputs of sad_kmer_rank (caller-owned, in `mem` space).
  * With b_ij = min(|x_i|,|x_j|) - k + 1 and a_ij = sum_tau min(n_xi(tau), n_xj(tau))
@@ -107,7 +115,20 @@ typedef struct sad_kmer_params {
  *            of Section 2 is monotone, so sequences are ordered by
  *            key_a/key_b (compared by 64-bit cross-multiplication), then by
  *            index.
- *   A        NULL, or n*n int32 row-major receiving a_ij. */
+ *   A        NULL, or n*n int32 row-major receiving a_ij.
+ * With params->global_samples = s >= 1, the globalized rank of Section 2.3.1
+ * (each processor sends a sample set of s sequences to all others, and every
+ * sequence is ranked against all s*p samples):
+ *   sample_idx[p*s]  the samples of block b at [b*s, (b+1)*s): the block is
+ *            ordered by (dloc, index) ascending and sample j (j = 0..s-1) is
+ *            its member at 0-based position floor((2j+1) w_b / (2s)), w_b the
+ *            block size (evenly spaced strata; with w_b < s a member is taken
+ *            more than once); -1 for every slot of an empty block
+ *   G[n]     sum over the p*s sample slots sigma (a slot taken twice counts
+ *            twice, -1 slots count 0) of floor(a_i,sigma 2^32 / b_i,sigma);
+ *            below 2^52. Sorted ascending with ties by index it gives the
+ *            globalized order (sad_partition_keys64).
+ * Both may be NULL when global_samples = 0. */
 typedef struct sad_rank_out {
     uint64_t* dloc;
     uint64_t* dcen;
@@ -116,6 +137,8 @@ typedef struct sad_rank_out {
     int32_t* key_a;
     int32_t* key_b;
     int32_t* A;
+    uint64_t* G;
+    int32_t* sample_idx;
 } sad_rank_out;
 
 /* ---- context ---------------------------------------------------------- */
@@ -142,7 +165,8 @@ const char* sad_version(void);
 #define SAD_STAGE_PARTITION 4  /* regular-sampling partition */
 #define SAD_STAGE_SCORES 5     /* alignment-score kernels, 32-bit DP */
 #define SAD_STAGE_SCORES_PACKED 6 /* alignment-score kernels, two problems per 16x2 lane */
-#define SAD_NUM_STAGES 7
+#define SAD_STAGE_GLOBAL 7     /* globalized rank: sample selection and sums against the samples */
+#define SAD_NUM_STAGES 8
 
 /* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
  * accumulated times. */
@@ -177,10 +201,19 @@ int sad_kmer_rank(sad_ctx* ctx, const sad_seqset* seqs, const sad_kmer_params* p
  * Inputs key_a[n], key_b[n] (0 <= key_a <= key_b, key_b >= 1).
  * Outputs: bucket_offsets[p+1] (CSR), order[n] (members of each bucket in
  * ascending index), pivot_idx[p-1] (sequence index of each pivot; may be
- * NULL). Errors: SAD_EINVAL (n < 0, p < 1, p > 4096, a bad key), SAD_ECUDA. */
+ * NULL). Errors: SAD_EINVAL (n < 0, p < 1, p > 1024, a bad key), SAD_ECUDA. */
 int sad_partition(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_t* key_b,
                   int32_t p, int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
                   int32_t mem, void* stream);
+
+/* The same regular-sampling partition on unsigned 64-bit integer rank keys
+ * (the globalized rank G of sad_rank_out), ascending, ties by index.
+ * keys[n], bucket_offsets[p+1], order[n], pivot_idx[p-1] (nullable) in `mem`
+ * space. Errors: SAD_EINVAL (n < 0, p outside 1..1024, a NULL pointer),
+ * SAD_ECUDA. */
+int sad_partition_keys64(sad_ctx* ctx, int32_t n, const uint64_t* keys, int32_t p,
+                         int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                         int32_t mem, void* stream);
 
 /* ---- stage 1: partition without any allocation ------------------------- */
 
@@ -273,7 +306,9 @@ int sad_scores_autotune(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* buc
  * every intermediate kept on the device. rank (may have NULL members: those
  * outputs are skipped), bucket_offsets[p+1], order[n], score_offsets[p+1],
  * scores[scores_capacity] are in `mem` space. SAD_ERANGE when the scores do
- * not fit (score_offsets then holds the layout). */
+ * not fit (score_offsets then holds the layout). With
+ * params->global_samples >= 1 the buckets come from the globalized rank G
+ * (sad_partition_keys64) instead of the keys against the global ancestor. */
 int sad_pipeline(sad_ctx* ctx, const sad_seqset* seqs, const sad_kmer_params* params,
                  const int8_t* subst, int32_t gap_open, int32_t gap_extend, int32_t mode,
                  const sad_rank_out* rank, int32_t* bucket_offsets, int32_t* order,

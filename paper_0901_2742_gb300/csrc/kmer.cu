@@ -193,6 +193,75 @@ constexpr int kTile = 64;
 constexpr int kKC = 64;             // bytes of k per stage
 constexpr int kRowB = kKC + 16;     // smem row pitch (bank spread)
 
+// One 64 x 64 tile of sum_tau |x_tau - y_tau| over uint8 count rows of Vs
+// bytes (a multiple of kKC): acc[r][c] for the A row ty + 16r and the B row
+// tx + 16c. Every thread stages 16 bytes of row lr = tid / 4 of A and of B per
+// kKC-byte chunk from ga / gb (its own row pointers, offset by its byte lc;
+// va / vb false: a zero row), double-buffered through As / Bs. With kClamp
+// every byte is first clamped to T (T4 holds T in each byte), so the sums are
+// those of min(count, T).
+__device__ __forceinline__ uint4 clamp_bytes(uint4 v, uint32_t T4) {
+    return make_uint4(__vminu4(v.x, T4), __vminu4(v.y, T4), __vminu4(v.z, T4), __vminu4(v.w, T4));
+}
+
+template <bool kClamp>
+__device__ __forceinline__ void sad_tile_64(const uint8_t* __restrict__ ga, const uint8_t* __restrict__ gb,
+                                            bool va, bool vb, int32_t Vs, uint32_t T4,
+                                            uint8_t (*As)[kTile][kRowB], uint8_t (*Bs)[kTile][kRowB],
+                                            uint32_t (&acc)[4][4]) {
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int lr = tid >> 2, lc = (tid & 3) * 16;
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0;
+    const int nchunks = Vs / kKC;
+    uint4 ra = va ? *(const uint4*)ga : make_uint4(0, 0, 0, 0);
+    uint4 rb = vb ? *(const uint4*)gb : make_uint4(0, 0, 0, 0);
+    if (kClamp) {
+        ra = clamp_bytes(ra, T4);
+        rb = clamp_bytes(rb, T4);
+    }
+    *(uint4*)&As[0][lr][lc] = ra;
+    *(uint4*)&Bs[0][lr][lc] = rb;
+    __syncthreads();
+    for (int ch = 0; ch < nchunks; ch++) {
+        const int cur = ch & 1;
+        if (ch + 1 < nchunks) {
+            ra = va ? *(const uint4*)(ga + (int64_t)(ch + 1) * kKC) : make_uint4(0, 0, 0, 0);
+            rb = vb ? *(const uint4*)(gb + (int64_t)(ch + 1) * kKC) : make_uint4(0, 0, 0, 0);
+            if (kClamp) {
+                ra = clamp_bytes(ra, T4);
+                rb = clamp_bytes(rb, T4);
+            }
+        }
+#pragma unroll
+        for (int kq = 0; kq < kKC; kq += 16) {
+            uint4 a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) a[r] = *(const uint4*)&As[cur][ty + 16 * r][kq];
+#pragma unroll
+            for (int c = 0; c < 4; c++) b[c] = *(const uint4*)&Bs[cur][tx + 16 * c][kq];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    uint32_t s = acc[r][c];
+                    s = absdiff4_add(a[r].x, b[c].x, s);
+                    s = absdiff4_add(a[r].y, b[c].y, s);
+                    s = absdiff4_add(a[r].z, b[c].z, s);
+                    s = absdiff4_add(a[r].w, b[c].w, s);
+                    acc[r][c] = s;
+                }
+        }
+        if (ch + 1 < nchunks) {
+            *(uint4*)&As[cur ^ 1][lr][lc] = ra;
+            *(uint4*)&Bs[cur ^ 1][lr][lc] = rb;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_allpairs_u8(int32_t n, int32_t Vs, int32_t ntiles, const uint8_t* __restrict__ C8,
               const uint32_t* __restrict__ sT, SeqTables tab, uint64_t* __restrict__ dloc,
@@ -222,47 +291,7 @@ k_allpairs_u8(int32_t n, int32_t Vs, int32_t ntiles, const uint8_t* __restrict__
     const uint8_t* ga = C8 + (int64_t)(i0 + lr) * Vs + lc;
     const uint8_t* gb = C8 + (int64_t)(j0 + lr) * Vs + lc;
     uint32_t acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; r++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) acc[r][c] = 0;
-    const int nchunks = Vs / kKC;
-    uint4 ra = va ? *(const uint4*)ga : make_uint4(0, 0, 0, 0);
-    uint4 rb = vb ? *(const uint4*)gb : make_uint4(0, 0, 0, 0);
-    *(uint4*)&As[0][lr][lc] = ra;
-    *(uint4*)&Bs[0][lr][lc] = rb;
-    __syncthreads();
-    for (int ch = 0; ch < nchunks; ch++) {
-        const int cur = ch & 1;
-        if (ch + 1 < nchunks) {
-            ra = va ? *(const uint4*)(ga + (int64_t)(ch + 1) * kKC) : make_uint4(0, 0, 0, 0);
-            rb = vb ? *(const uint4*)(gb + (int64_t)(ch + 1) * kKC) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int kq = 0; kq < kKC; kq += 16) {
-            uint4 a[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; r++) a[r] = *(const uint4*)&As[cur][ty + 16 * r][kq];
-#pragma unroll
-            for (int c = 0; c < 4; c++) b[c] = *(const uint4*)&Bs[cur][tx + 16 * c][kq];
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-#pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    uint32_t s = acc[r][c];
-                    s = absdiff4_add(a[r].x, b[c].x, s);
-                    s = absdiff4_add(a[r].y, b[c].y, s);
-                    s = absdiff4_add(a[r].z, b[c].z, s);
-                    s = absdiff4_add(a[r].w, b[c].w, s);
-                    acc[r][c] = s;
-                }
-        }
-        if (ch + 1 < nchunks) {
-            *(uint4*)&As[cur ^ 1][lr][lc] = ra;
-            *(uint4*)&Bs[cur ^ 1][lr][lc] = rb;
-        }
-        __syncthreads();
-    }
+    sad_tile_64<false>(ga, gb, va, vb, Vs, 0u, As, Bs, acc);
     // epilogue: exact numerators, fixed-point terms, row/column sums
     int32_t ci[4], cnk[4], cbl[4], chx[4];
     uint64_t cq[4];
@@ -458,6 +487,101 @@ __global__ void k_key_column(int32_t n, const int32_t* __restrict__ ga_ptr,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Globalized rank (Section 2.3.1: every block's sample set goes to all blocks
+// and every sequence is ranked against the s*p samples).
+
+// Position of every sequence in its block ordered by (dloc, index):
+// grid (p, chunks of 256 members); sorted[lo + r] = i.
+__global__ void k_block_order(int32_t n, int32_t p, const uint64_t* __restrict__ dloc,
+                              int32_t* __restrict__ sorted) {
+    __shared__ unsigned long long tile[1024];
+    const int32_t b = blockIdx.x;
+    const int64_t lo = (int64_t)b * n / p, hi = (int64_t)(b + 1) * n / p;
+    const int64_t i = lo + (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (lo + (int64_t)blockIdx.y * blockDim.x >= hi) return;  // whole CTA idle (uniform)
+    const unsigned long long d = i < hi ? dloc[i] : 0ull;
+    int32_t r = 0;
+    for (int64_t t0 = lo; t0 < hi; t0 += 1024) {
+        const int64_t m = min((int64_t)1024, hi - t0);
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < m; t += blockDim.x) tile[t] = dloc[t0 + t];
+        __syncthreads();
+        for (int64_t t = 0; t < m; t++) {
+            const unsigned long long v = tile[t];
+            r += (v < d) | ((v == d) & (t0 + t < i));
+        }
+    }
+    if (i < hi) sorted[lo + r] = (int32_t)i;
+}
+
+// Sample slot (b, j): the member at 0-based position floor((2j+1) w / (2s)) of
+// block b in (dloc, index) order; -1 for an empty block.
+__global__ void k_pick_samples(int32_t n, int32_t p, int32_t s, const int32_t* __restrict__ sorted,
+                               int32_t* __restrict__ samples) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)p * s) return;
+    const int64_t b = t / s, j = t % s;
+    const int64_t lo = b * n / p, hi = (b + 1) * n / p, w = hi - lo;
+    samples[t] = w > 0 ? sorted[lo + ((2 * j + 1) * w) / (2 * (int64_t)s)] : -1;
+}
+
+// G_i = sum over the sample slots of floor(a_i,sigma 2^32 / b_i,sigma): one CTA
+// per 64 rows x 64 slots, the numerators from the byte sums clamped to T (plus
+// the residual above T), each row's 64 terms summed and added to G_i.
+template <bool kClamp>
+__global__ void __launch_bounds__(256)
+k_sample_sums(int32_t n, int32_t nslots, int32_t Vs, uint32_t T, const uint8_t* __restrict__ C8,
+              const uint32_t* __restrict__ sT, SeqTables tab, const int32_t* __restrict__ samples,
+              uint64_t* __restrict__ G) {
+    __shared__ __align__(16) uint8_t As[2][kTile][kRowB];
+    __shared__ __align__(16) uint8_t Bs[2][kTile][kRowB];
+    const int32_t i0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int lr = tid >> 2, lc = (tid & 3) * 16;
+    const int32_t sl = j0 + lr < nslots ? samples[j0 + lr] : -1;
+    const bool va = i0 + lr < n, vb = sl >= 0;
+    const uint8_t* ga = C8 + (int64_t)(va ? i0 + lr : 0) * Vs + lc;
+    const uint8_t* gb = C8 + (int64_t)(vb ? sl : 0) * Vs + lc;
+    uint32_t acc[4][4];
+    sad_tile_64<kClamp>(ga, gb, va, vb, Vs, T * 0x01010101u, As, Bs, acc);
+    int32_t cnk[4], chx[4];
+    uint64_t cq[4];
+    uint32_t cr[4], cs[4];
+    bool cok[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int32_t j = j0 + tx + 16 * c;
+        const int32_t sg = j < nslots ? samples[j] : -1;
+        cok[c] = sg >= 0;
+        cnk[c] = cok[c] ? tab.nkb[sg] : 0;
+        cq[c] = cok[c] ? tab.q32[sg] : 0;
+        cr[c] = cok[c] ? tab.r32[sg] : 0;
+        chx[c] = cok[c] ? tab.hidx[sg] : -1;
+        cs[c] = cok[c] ? sT[sg] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int32_t i = i0 + ty + 16 * r;
+        const bool oki = i < n;
+        const int32_t nki = oki ? tab.nkb[i] : 0;
+        const uint64_t qi = oki ? tab.q32[i] : 0;
+        const uint32_t ri = oki ? tab.r32[i] : 0;
+        const int32_t hxi = oki ? tab.hidx[i] : -1;
+        const uint32_t si = oki ? sT[i] : 0;
+        uint64_t rs = 0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            if (!oki || !cok[c]) continue;
+            const uint32_t a = ((si + cs[c] - acc[r][c]) >> 1) + (uint32_t)residual_at(tab, hxi, chx[c]);
+            rs += fixed_term(a, nki, qi, ri, cnk[c], cq[c], cr[c]);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+        if (tx == 0 && oki && rs) atomicAdd((unsigned long long*)&G[i], (unsigned long long)rs);
+    }
+}
+
 }  // namespace
 
 int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
@@ -484,6 +608,8 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     if (n == 0) {
         SAD_CUDA(cudaMemsetAsync(out.la, 0xff, sizeof(int32_t) * p, stream));
         SAD_CUDA(cudaMemsetAsync(out.ga, 0xff, sizeof(int32_t), stream));
+        if (kp->global_samples > 0 && out.samples)
+            SAD_CUDA(cudaMemsetAsync(out.samples, 0xff, 4ull * p * kp->global_samples, stream));
         return SAD_OK;
     }
 
@@ -618,6 +744,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     }
     }
     // ancestors and keys
+    {
     TraceScope ts(ctx, SAD_STAGE_RANK, stream);
     k_local_ancestors<<<p, 256, 0, stream>>>(n, p, out.dloc, out.la);
     SAD_LAUNCHED();
@@ -628,6 +755,31 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     k_key_column<<<(n + 7) / 8, 256, 0, stream>>>(n, out.ga, (const uint8_t*)c8, Vs, (uint32_t)T,
                                                   tab, out.key_a, out.key_b);
     SAD_LAUNCHED();
+    }
+    // globalized rank against s samples per block
+    const int32_t gs = kp->global_samples;
+    if (gs > 0 && out.G && out.samples) {
+        TraceScope ts(ctx, SAD_STAGE_GLOBAL, stream);
+        void* so = nullptr;
+        SAD_RET(workspace(ctx, WS_GLOBAL, 4ull * n, stream, &so));
+        int32_t* sorted = (int32_t*)so;
+        const int64_t wmax = (n + p - 1) / p + 1;
+        k_block_order<<<dim3((unsigned)p, (unsigned)((wmax + 255) / 256)), 256, 0, stream>>>(
+            n, p, out.dloc, sorted);
+        SAD_LAUNCHED();
+        const int64_t nslots = (int64_t)p * gs;
+        k_pick_samples<<<(unsigned)((nslots + 255) / 256), 256, 0, stream>>>(n, p, gs, sorted, out.samples);
+        SAD_LAUNCHED();
+        SAD_CUDA(cudaMemsetAsync(out.G, 0, 8ull * n, stream));
+        const dim3 grid((unsigned)((n + kTile - 1) / kTile), (unsigned)((nslots + kTile - 1) / kTile));
+        if (T < 255)
+            k_sample_sums<true><<<grid, 256, 0, stream>>>(n, (int32_t)nslots, Vs, (uint32_t)T,
+                                                          (const uint8_t*)c8, d_sT, tab, out.samples, out.G);
+        else
+            k_sample_sums<false><<<grid, 256, 0, stream>>>(n, (int32_t)nslots, Vs, (uint32_t)T,
+                                                           (const uint8_t*)c8, d_sT, tab, out.samples, out.G);
+        SAD_LAUNCHED();
+    }
     return SAD_OK;
 }
 
@@ -636,6 +788,8 @@ int validate_kmer_params(const sad_seqset* s, const sad_kmer_params* kp) {
     SAD_CHECK(kp->k >= 1, SAD_EINVAL, "k = %d < 1", kp->k);
     SAD_CHECK(kp->p >= 1 && kp->p <= 1024, SAD_EINVAL, "p = %d outside 1..1024", kp->p);
     SAD_CHECK(kp->cap >= 0 && kp->cap <= 8, SAD_EINVAL, "cap = %d outside 0..8", kp->cap);
+    SAD_CHECK(kp->global_samples >= 0 && kp->global_samples <= SAD_MAX_GLOBAL_SAMPLES, SAD_EINVAL,
+              "global_samples = %d outside 0..%d", kp->global_samples, SAD_MAX_GLOBAL_SAMPLES);
     SAD_CHECK(kp->kmer_alphabet >= 1 && kp->kmer_alphabet <= SAD_MAX_ALPHABET, SAD_EINVAL,
               "kmer_alphabet = %d outside 1..%d", kp->kmer_alphabet, SAD_MAX_ALPHABET);
     int64_t V = 1;
@@ -671,6 +825,9 @@ extern "C" int sad_kmer_rank(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_
               SAD_EINVAL, "an output pointer of sad_rank_out is NULL");
     SAD_CHECK(seqs != nullptr, SAD_EINVAL, "seqs is NULL");
     SAD_RET(validate_kmer_params(seqs, params));
+    const int32_t gs = params->global_samples;
+    SAD_CHECK(gs == 0 || (out->G && out->sample_idx), SAD_EINVAL,
+              "global_samples = %d needs the G and sample_idx outputs", gs);
     sad_ctx* ctx = nullptr;
     SAD_RET(resolve_ctx(ctx_in, &ctx));
     std::lock_guard<std::mutex> lock(ctx->mu);
@@ -679,14 +836,20 @@ extern "C" int sad_kmer_rank(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_
     DevSeqs S;
     SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
     const int32_t n = S.n, p = params->p;
+    const size_t nslots = (size_t)p * gs;
     KmerOutDev d;
     void* stage = nullptr;
     if (mem == SAD_MEM_DEVICE) {
         d = KmerOutDev{out->dloc, out->dcen, out->la, out->ga, out->key_a, out->key_b, out->A};
+        if (gs > 0) {
+            d.G = out->G;
+            d.samples = out->sample_idx;
+        }
     } else {
         const size_t nn = (size_t)(n > 0 ? n : 1);
         const size_t bytes = 8 * nn * 2 + 4 * (size_t)p + 16 + 4 * nn * 2 +
-                             (out->A ? 4 * (size_t)n * n : 0) + 6 * 256;
+                             (out->A ? 4 * (size_t)n * n : 0) + (gs > 0 ? 8 * nn + 4 * nslots : 0) +
+                             10 * 256;
         SAD_RET(workspace(ctx, WS_RANK_OUT, bytes, stream, &stage));
         char* c = (char*)stage;
         size_t o = 0;
@@ -702,6 +865,10 @@ extern "C" int sad_kmer_rank(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_
         d.key_a = (int32_t*)take(4 * nn);
         d.key_b = (int32_t*)take(4 * nn);
         d.A = out->A ? (int32_t*)take(4 * (size_t)n * n) : nullptr;
+        if (gs > 0) {
+            d.G = (uint64_t*)take(8 * nn);
+            d.samples = (int32_t*)take(4 * nslots);
+        }
     }
     SAD_RET(kmer_rank_device(ctx, S, params, d, stream));
     if (mem == SAD_MEM_HOST) {
@@ -713,6 +880,10 @@ extern "C" int sad_kmer_rank(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_
         SAD_CUDA(cudaMemcpyAsync(out->key_b, d.key_b, 4ull * n, cudaMemcpyDeviceToHost, stream));
         if (out->A)
             SAD_CUDA(cudaMemcpyAsync(out->A, d.A, 4ull * n * n, cudaMemcpyDeviceToHost, stream));
+        if (gs > 0) {
+            if (n > 0) SAD_CUDA(cudaMemcpyAsync(out->G, d.G, 8ull * n, cudaMemcpyDeviceToHost, stream));
+            SAD_CUDA(cudaMemcpyAsync(out->sample_idx, d.samples, 4 * nslots, cudaMemcpyDeviceToHost, stream));
+        }
     }
     SAD_RET(status_check(ctx, stream));
     return SAD_OK;

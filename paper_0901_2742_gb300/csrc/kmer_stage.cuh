@@ -15,6 +15,8 @@ struct KmerOutDev {
     int32_t* key_a;
     int32_t* key_b;
     int32_t* A;  // nullable
+    uint64_t* G = nullptr;        // globalized rank (with kp->global_samples > 0)
+    int32_t* samples = nullptr;   // p * global_samples sample slots
 };
 
 int validate_kmer_params(const sad_seqset* s, const sad_kmer_params* kp);

@@ -7,6 +7,9 @@
 // For b <= 2^16 two different fractions differ by at least 2^-32, so the
 // fixed-point part orders them exactly and equal fractions tie; the index
 // breaks ties. Every comparison below is then a plain 64-bit comparison.
+// Integer rank keys G_i (the globalized rank sums, up to about 2^52) are packed
+// as the 128-bit integer G_i << 32 | i; the kernels are templated on the key
+// type and the two forms share every step.
 #include <cstring>
 
 #include "partition_stage.cuh"
@@ -17,6 +20,12 @@ namespace sad {
 namespace {
 
 constexpr uint32_t STATUS_BAD_KEY = 1u << 3;
+
+using u128 = unsigned __int128;
+
+// sequence index carried in the low bits of a packed key
+__device__ __forceinline__ int32_t key_index(uint64_t v) { return (int32_t)(v & 0x7fffffffull); }
+__device__ __forceinline__ int32_t key_index(u128 v) { return (int32_t)(uint32_t)v; }
 
 __global__ void k_part_keys(int32_t n, const int32_t* __restrict__ ka, const int32_t* __restrict__ kb,
                             uint64_t* __restrict__ K, uint32_t* __restrict__ status) {
@@ -32,15 +41,23 @@ __global__ void k_part_keys(int32_t n, const int32_t* __restrict__ ka, const int
     K[i] = (fx << 31) | (uint64_t)i;
 }
 
+// G_i << 32 | i
+__global__ void k_part_keys128(int32_t n, const uint64_t* __restrict__ G, u128* __restrict__ K) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    K[i] = ((u128)G[i] << 32) | (u128)(uint32_t)i;
+}
+
 // rank of every key inside its block: grid (p, chunks of 256 elements)
-__global__ void k_part_block_rank(int32_t n, int32_t p, const uint64_t* __restrict__ K,
+template <class KeyT>
+__global__ void k_part_block_rank(int32_t n, int32_t p, const KeyT* __restrict__ K,
                                   int32_t* __restrict__ rank) {
-    __shared__ uint64_t tile[1024];
+    __shared__ KeyT tile[1024];
     const int32_t b = blockIdx.x;
     const int64_t lo = (int64_t)b * n / p, hi = (int64_t)(b + 1) * n / p;
     const int64_t i = lo + (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     if (lo + (int64_t)blockIdx.y * blockDim.x >= hi) return;  // whole CTA idle (uniform)
-    const uint64_t key = i < hi ? K[i] : 0;
+    const KeyT key = i < hi ? K[i] : (KeyT)0;
     int32_t r = 0;
     for (int64_t t0 = lo; t0 < hi; t0 += 1024) {
         const int64_t m = min((int64_t)1024, hi - t0);
@@ -54,8 +71,9 @@ __global__ void k_part_block_rank(int32_t n, int32_t p, const uint64_t* __restri
 
 // samples: element of rank r in block b is sample j for every j in 1..p-1 with
 // floor(j w / p) = r, i.e. j in [ceil(r p / w), ceil((r+1) p / w) - 1]
-__global__ void k_part_samples(int32_t n, int32_t p, const uint64_t* __restrict__ K,
-                               const int32_t* __restrict__ rank, uint64_t* __restrict__ Y) {
+template <class KeyT>
+__global__ void k_part_samples(int32_t n, int32_t p, const KeyT* __restrict__ K,
+                               const int32_t* __restrict__ rank, KeyT* __restrict__ Y) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     // block of i: largest b with floor(b n / p) <= i
@@ -71,11 +89,12 @@ __global__ void k_part_samples(int32_t n, int32_t p, const uint64_t* __restrict_
 }
 
 // position of every sample in sorted order (equal samples keep their slot order)
-__global__ void k_part_sample_rank(int32_t M, const uint64_t* __restrict__ Y,
-                                   uint64_t* __restrict__ Ysorted) {
-    __shared__ uint64_t tile[1024];
+template <class KeyT>
+__global__ void k_part_sample_rank(int32_t M, const KeyT* __restrict__ Y,
+                                   KeyT* __restrict__ Ysorted) {
+    __shared__ KeyT tile[1024];
     const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t key = s < M ? Y[s] : 0;
+    const KeyT key = s < M ? Y[s] : (KeyT)0;
     int32_t r = 0;
     for (int32_t t0 = 0; t0 < M; t0 += 1024) {
         const int32_t m = min(1024, M - t0);
@@ -83,7 +102,7 @@ __global__ void k_part_sample_rank(int32_t M, const uint64_t* __restrict__ Y,
         for (int32_t t = threadIdx.x; t < m; t += blockDim.x) tile[t] = Y[t0 + t];
         __syncthreads();
         for (int32_t t = 0; t < m; t++) {
-            const uint64_t v = tile[t];
+            const KeyT v = tile[t];
             r += (v < key) | ((v == key) & (t0 + t < s));
         }
     }
@@ -91,29 +110,31 @@ __global__ void k_part_sample_rank(int32_t M, const uint64_t* __restrict__ Y,
 }
 
 // pivot m = sorted sample at 1-based (m-1) q + max(1, floor(q/2)), q = non-empty blocks
-__global__ void k_part_pivots(int32_t n, int32_t p, const uint64_t* __restrict__ Ysorted,
-                              uint64_t* __restrict__ piv, int32_t* __restrict__ pivot_idx) {
+template <class KeyT>
+__global__ void k_part_pivots(int32_t n, int32_t p, const KeyT* __restrict__ Ysorted,
+                              KeyT* __restrict__ piv, int32_t* __restrict__ pivot_idx) {
     const int32_t m = blockIdx.x * blockDim.x + threadIdx.x + 1;
     if (m > p - 1) return;
     const int64_t q = n < p ? n : p;
     if (q == 0) {
-        piv[m - 1] = ~0ull;
+        piv[m - 1] = ~(KeyT)0;
         if (pivot_idx) pivot_idx[m - 1] = -1;
         return;
     }
     const int64_t pos1 = (int64_t)(m - 1) * q + (q / 2 > 1 ? q / 2 : 1);
-    const uint64_t v = Ysorted[pos1 - 1];
+    const KeyT v = Ysorted[pos1 - 1];
     piv[m - 1] = v;
-    if (pivot_idx) pivot_idx[m - 1] = (int32_t)(v & 0x7fffffffull);
+    if (pivot_idx) pivot_idx[m - 1] = key_index(v);
 }
 
 // bucket = number of pivots strictly below the key (pivots are sorted)
-__global__ void k_part_bucket(int32_t n, int32_t p, const uint64_t* __restrict__ K,
-                              const uint64_t* __restrict__ piv, int32_t* __restrict__ bucket,
+template <class KeyT>
+__global__ void k_part_bucket(int32_t n, int32_t p, const KeyT* __restrict__ K,
+                              const KeyT* __restrict__ piv, int32_t* __restrict__ bucket,
                               int32_t* __restrict__ count) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint64_t key = K[i];
+    const KeyT key = K[i];
     int32_t lo = 0, hi = p - 1;  // first pivot >= key
     while (lo < hi) {
         const int32_t mid = (lo + hi) >> 1;
@@ -153,27 +174,32 @@ __global__ void k_part_scatter(int32_t n, int32_t p, const int32_t* __restrict__
 
 }  // namespace
 
-int partition_device(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_t* key_b,
-                     int32_t p, int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
-                     cudaStream_t stream) {
+namespace {
+
+// The partition steps on packed keys of type KeyT; fill_keys(K) launches the
+// kernel that writes the n keys.
+template <class KeyT, class FillKeys>
+int partition_run(sad_ctx* ctx, int32_t n, int32_t p, FillKeys fill_keys, int32_t* bucket_offsets,
+                  int32_t* order, int32_t* pivot_idx, cudaStream_t stream) {
     const int64_t M = (int64_t)p * (p - 1);
+    const size_t kb = sizeof(KeyT);
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         size_t o = off;
         off = (size_t)round_up((int64_t)(off + bytes), 256);
         return o;
     };
-    const size_t oK = carve(8ull * (n + 1)), oRank = carve(4ull * (n + 1)), oY = carve(8ull * (M + 1)),
-                 oYs = carve(8ull * (M + 1)), oPiv = carve(8ull * p), oBucket = carve(4ull * (n + 1)),
+    const size_t oK = carve(kb * (n + 1)), oRank = carve(4ull * (n + 1)), oY = carve(kb * (M + 1)),
+                 oYs = carve(kb * (M + 1)), oPiv = carve(kb * p), oBucket = carve(4ull * (n + 1)),
                  oCount = carve(4ull * p);
     void* ws = nullptr;
     SAD_RET(workspace(ctx, WS_PART, off, stream, &ws));
     char* w = (char*)ws;
-    uint64_t* K = (uint64_t*)(w + oK);
+    KeyT* K = (KeyT*)(w + oK);
     int32_t* rank = (int32_t*)(w + oRank);
-    uint64_t* Y = (uint64_t*)(w + oY);
-    uint64_t* Ys = (uint64_t*)(w + oYs);
-    uint64_t* piv = (uint64_t*)(w + oPiv);
+    KeyT* Y = (KeyT*)(w + oY);
+    KeyT* Ys = (KeyT*)(w + oYs);
+    KeyT* piv = (KeyT*)(w + oPiv);
     int32_t* bucket = (int32_t*)(w + oBucket);
     int32_t* count = (int32_t*)(w + oCount);
     SAD_CUDA(cudaMemsetAsync(count, 0, 4ull * p, stream));
@@ -184,28 +210,51 @@ int partition_device(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_
     }
     const int nb = (n + 255) / 256;
     TraceScope ts(ctx, SAD_STAGE_PARTITION, stream);
-    k_part_keys<<<nb, 256, 0, stream>>>(n, key_a, key_b, K, ctx->d_status);
+    fill_keys(K);
     SAD_LAUNCHED();
     if (p > 1) {
         const int64_t wmax = (n + p - 1) / p + 1;
         dim3 g((unsigned)p, (unsigned)((wmax + 255) / 256));
-        k_part_block_rank<<<g, 256, 0, stream>>>(n, p, K, rank);
+        k_part_block_rank<<<g, 256, 0, stream>>>(n, p, (const KeyT*)K, rank);
         SAD_LAUNCHED();
-        SAD_CUDA(cudaMemsetAsync(Y, 0xff, 8ull * M, stream));
-        k_part_samples<<<nb, 256, 0, stream>>>(n, p, K, rank, Y);
+        SAD_CUDA(cudaMemsetAsync(Y, 0xff, kb * M, stream));
+        k_part_samples<<<nb, 256, 0, stream>>>(n, p, (const KeyT*)K, rank, Y);
         SAD_LAUNCHED();
-        k_part_sample_rank<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>((int32_t)M, Y, Ys);
+        k_part_sample_rank<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>((int32_t)M, (const KeyT*)Y, Ys);
         SAD_LAUNCHED();
-        k_part_pivots<<<(p - 1 + 255) / 256, 256, 0, stream>>>(n, p, Ys, piv, pivot_idx);
+        k_part_pivots<<<(p - 1 + 255) / 256, 256, 0, stream>>>(n, p, (const KeyT*)Ys, piv, pivot_idx);
         SAD_LAUNCHED();
     }
-    k_part_bucket<<<nb, 256, 0, stream>>>(n, p, K, piv, bucket, count);
+    k_part_bucket<<<nb, 256, 0, stream>>>(n, p, (const KeyT*)K, (const KeyT*)piv, bucket, count);
     SAD_LAUNCHED();
     k_part_offsets<<<1, 32, 0, stream>>>(p, count, bucket_offsets);
     SAD_LAUNCHED();
     k_part_scatter<<<(p + 7) / 8, 256, 0, stream>>>(n, p, bucket, bucket_offsets, order);
     SAD_LAUNCHED();
     return SAD_OK;
+}
+
+}  // namespace
+
+int partition_device(sad_ctx* ctx, int32_t n, const int32_t* key_a, const int32_t* key_b,
+                     int32_t p, int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                     cudaStream_t stream) {
+    uint32_t* status = ctx->d_status;
+    return partition_run<uint64_t>(
+        ctx, n, p,
+        [&](uint64_t* K) {
+            k_part_keys<<<(n + 255) / 256, 256, 0, stream>>>(n, key_a, key_b, K, status);
+        },
+        bucket_offsets, order, pivot_idx, stream);
+}
+
+int partition_keys64_device(sad_ctx* ctx, int32_t n, const uint64_t* keys, int32_t p,
+                            int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                            cudaStream_t stream) {
+    return partition_run<u128>(
+        ctx, n, p,
+        [&](u128* K) { k_part_keys128<<<(n + 255) / 256, 256, 0, stream>>>(n, keys, K); },
+        bucket_offsets, order, pivot_idx, stream);
 }
 
 }  // namespace sad
@@ -256,6 +305,44 @@ extern "C" int sad_partition(sad_ctx* ctx_in, int32_t n, const int32_t* key_a,
     uint32_t s = *ctx->h_status;
     SAD_CHECK(!(s & STATUS_BAD_KEY), SAD_EINVAL,
               "a rank key violates 0 <= key_a <= key_b, 1 <= key_b <= 65536");
+    return SAD_OK;
+}
+
+extern "C" int sad_partition_keys64(sad_ctx* ctx_in, int32_t n, const uint64_t* keys, int32_t p,
+                                    int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
+                                    int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(n >= 0, SAD_EINVAL, "n = %d < 0", n);
+    SAD_CHECK(p >= 1 && p <= kMaxPartitionP, SAD_EINVAL, "p = %d outside 1..%d", p, kMaxPartitionP);
+    SAD_CHECK(bucket_offsets && (n == 0 || (order && keys)), SAD_EINVAL, "a required pointer is NULL");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    SAD_RET(status_clear(ctx, stream));
+    const uint64_t* dkeys = keys;
+    int32_t *dbo = bucket_offsets, *dord = order, *dpiv = pivot_idx;
+    if (mem == SAD_MEM_HOST) {
+        void* st = nullptr;
+        const size_t nn = (size_t)n + 1;
+        SAD_RET(workspace(ctx, WS_PART_OUT, 8 * nn + 4 * (nn + (size_t)p * 2 + 8) + 1024, stream, &st));
+        uint64_t* sk = (uint64_t*)st;
+        dord = (int32_t*)(sk + nn);
+        dbo = dord + nn;
+        dpiv = pivot_idx ? dbo + p + 1 : nullptr;
+        if (n > 0) SAD_CUDA(cudaMemcpyAsync(sk, keys, 8ull * n, cudaMemcpyHostToDevice, stream));
+        dkeys = sk;
+    }
+    SAD_RET(partition_keys64_device(ctx, n, dkeys, p, dbo, dord, dpiv, stream));
+    if (mem == SAD_MEM_HOST) {
+        SAD_CUDA(cudaMemcpyAsync(bucket_offsets, dbo, 4ull * (p + 1), cudaMemcpyDeviceToHost, stream));
+        if (n > 0) SAD_CUDA(cudaMemcpyAsync(order, dord, 4ull * n, cudaMemcpyDeviceToHost, stream));
+        if (pivot_idx && p > 1)
+            SAD_CUDA(cudaMemcpyAsync(pivot_idx, dpiv, 4ull * (p - 1), cudaMemcpyDeviceToHost, stream));
+    }
+    SAD_RET(status_check(ctx, stream));
     return SAD_OK;
 }
 

@@ -50,6 +50,9 @@ extern "C" int sad_pipeline(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_k
     const size_t o_dloc = carve(8 * nn), o_dcen = carve(8 * nn), o_la = carve(4ull * p),
                  o_ga = carve(16), o_ka = carve(4 * nn), o_kb = carve(4 * nn),
                  o_bo = carve(4ull * (p + 1)), o_ord = carve(4 * nn), o_so = carve(8ull * (p + 1));
+    const int32_t gs = params->global_samples;
+    const size_t nslots = (size_t)p * gs;
+    const size_t o_G = carve(gs > 0 ? 8 * nn : 0), o_smp = carve(4 * nslots);
     void* w = nullptr;
     SAD_RET(workspace(ctx, WS_PIPE, off, stream, &w));
     char* c = (char*)w;
@@ -59,8 +62,15 @@ extern "C" int sad_pipeline(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_k
     int32_t* dbo = (int32_t*)(c + o_bo);
     int32_t* dord = (int32_t*)(c + o_ord);
     int64_t* dso = (int64_t*)(c + o_so);
+    if (gs > 0) {
+        d.G = (uint64_t*)(c + o_G);
+        d.samples = (int32_t*)(c + o_smp);
+    }
     SAD_RET(kmer_rank_device(ctx, S, params, d, stream));
-    SAD_RET(partition_device(ctx, n, d.key_a, d.key_b, p, dbo, dord, nullptr, stream));
+    if (gs > 0)
+        SAD_RET(partition_keys64_device(ctx, n, d.G, p, dbo, dord, nullptr, stream));
+    else
+        SAD_RET(partition_device(ctx, n, d.key_a, d.key_b, p, dbo, dord, nullptr, stream));
     int32_t* dsc = scores;
     int64_t total = 0;
     if (mem == SAD_MEM_HOST) {
@@ -98,6 +108,9 @@ extern "C" int sad_pipeline(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_k
         if (rank->ga) SAD_CUDA(cudaMemcpyAsync(rank->ga, d.ga, 4, k, stream));
         if (rank->key_a) SAD_CUDA(cudaMemcpyAsync(rank->key_a, d.key_a, 4ull * n, k, stream));
         if (rank->key_b) SAD_CUDA(cudaMemcpyAsync(rank->key_b, d.key_b, 4ull * n, k, stream));
+        if (gs > 0 && rank->G) SAD_CUDA(cudaMemcpyAsync(rank->G, d.G, 8ull * n, k, stream));
+        if (gs > 0 && rank->sample_idx)
+            SAD_CUDA(cudaMemcpyAsync(rank->sample_idx, d.samples, 4 * nslots, k, stream));
     }
     SAD_RET(status_check(ctx, stream));
     return SAD_OK;

@@ -77,6 +77,7 @@ enum Slot : int {
     WS_SCORE_SCRATCH_LONG,  // strip boundaries of queries too long to pack
     WS_PIPE,           // pipeline intermediates
     WS_GEMM_TILES,     // tile list of the plane GEMM
+    WS_GLOBAL,         // block order of the globalized rank
     WS_NUM_SLOTS
 };
 

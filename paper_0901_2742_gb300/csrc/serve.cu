@@ -96,7 +96,8 @@ int64_t estimate_job_bytes(int32_t n, int64_t total, const sad_kmer_params& kp) 
     int64_t b = 2 * total + 48ll * n + 64 * 1024;         // residues (raw + padded), tables
     b += rows * Vs * (1 + kp.cap);                          // counts, planes
     b += 8 * total;                                         // excess lists (upper bound)
-    b += 32ll * n + 16 * p * p;                             // partition
+    b += 48ll * n + 40 * p * p;                             // partition (up to 16-byte keys)
+    b += 12ll * n + 4 * p * kp.global_samples;              // globalized rank
     b += 4 * score_ints + 16ll * n;                         // scores, plan
     b += 8ll * 1024 * 1024;                                 // residual matrix and kernel scratch headroom
     return b;
@@ -132,6 +133,8 @@ void run_job(sad_server* s, int slot, Job* job) {
     const size_t o_dloc = carve(8 * nn), o_dcen = carve(8 * nn), o_la = carve(4ull * p), o_ga = carve(16),
                  o_ka = carve(4 * nn), o_kb = carve(4 * nn), o_bo = carve(4ull * (p + 1)),
                  o_ord = carve(4 * nn), o_so = carve(8ull * (p + 1));
+    const int32_t gs = job->kp.global_samples;
+    const size_t o_G = carve(gs > 0 ? 8 * nn : 0), o_smp = carve(4ull * p * gs);
     void* w = nullptr;
     rc = workspace(ctx, WS_PIPE, off, stream, &w);
     if (rc != SAD_OK) return fail(rc);
@@ -141,12 +144,17 @@ void run_job(sad_server* s, int slot, Job* job) {
     int32_t* dbo = (int32_t*)(c + o_bo);
     int32_t* dord = (int32_t*)(c + o_ord);
     int64_t* dso = (int64_t*)(c + o_so);
+    if (gs > 0) {
+        d.G = (uint64_t*)(c + o_G);
+        d.samples = (int32_t*)(c + o_smp);
+    }
     sad_kmer_params kp = job->kp;
     kp.class_map = job->class_map.empty() ? nullptr : job->class_map.data();
     rc = kmer_rank_device(ctx, S, &kp, d, stream);
     if (rc != SAD_OK) return fail(rc);
     if (job->cancel.load()) return fail(SAD_ECANCELED);
-    rc = partition_device(ctx, n, d.key_a, d.key_b, p, dbo, dord, nullptr, stream);
+    rc = gs > 0 ? partition_keys64_device(ctx, n, d.G, p, dbo, dord, nullptr, stream)
+                : partition_device(ctx, n, d.key_a, d.key_b, p, dbo, dord, nullptr, stream);
     if (rc != SAD_OK) return fail(rc);
     job->bucket_offsets.assign((size_t)p + 1, 0);
     if (cudaMemcpyAsync(job->bucket_offsets.data(), dbo, 4ull * (p + 1), cudaMemcpyDeviceToHost, stream) !=

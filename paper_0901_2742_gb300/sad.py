@@ -39,13 +39,14 @@ class SeqSet(ctypes.Structure):
 
 class KmerParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("kmer_alphabet", ctypes.c_int32),
-                ("class_map", ctypes.c_void_p), ("cap", ctypes.c_int32), ("p", ctypes.c_int32)]
+                ("class_map", ctypes.c_void_p), ("cap", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("global_samples", ctypes.c_int32)]
 
 
 class RankOut(ctypes.Structure):
     _fields_ = [("dloc", ctypes.c_void_p), ("dcen", ctypes.c_void_p), ("la", ctypes.c_void_p),
                 ("ga", ctypes.c_void_p), ("key_a", ctypes.c_void_p), ("key_b", ctypes.c_void_p),
-                ("A", ctypes.c_void_p)]
+                ("A", ctypes.c_void_p), ("G", ctypes.c_void_p), ("sample_idx", ctypes.c_void_p)]
 
 
 _lib = None
@@ -73,6 +74,7 @@ def load():
         "sad_kmer_rank": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), ctypes.POINTER(KmerParams),
                                          ctypes.POINTER(RankOut), i32, P]),
         "sad_partition": (ctypes.c_int, [P, i32, P, P, i32, P, P, P, i32, P]),
+        "sad_partition_keys64": (ctypes.c_int, [P, i32, P, i32, P, P, P, i32, P]),
         "sad_partition_noalloc": (ctypes.c_int, [i32, P, P, i32, P, P, P, P]),
         "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
@@ -189,7 +191,7 @@ def _ctx(ctx):
     return None if ctx is None else ctx.handle
 
 
-STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed")
+STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global")
 
 
 def trace_enable(on: bool = True, ctx=None):
@@ -248,24 +250,31 @@ def launch_count() -> int:
 # ---- the calls --------------------------------------------------------------
 
 def kmer_rank(residues, offsets, alphabet: int, k: int, p: int, cap: int = 0,
-              kmer_alphabet: int | None = None, class_map=None, want_A: bool = False, ctx=None,
-              stream=None) -> dict:
-    """sad_kmer_rank: dict(dloc, dcen, la, ga, key_a, key_b, A)."""
+              kmer_alphabet: int | None = None, class_map=None, want_A: bool = False,
+              global_samples: int = 0, ctx=None, stream=None) -> dict:
+    """sad_kmer_rank: dict(dloc, dcen, la, ga, key_a, key_b, A, G, sample_idx).
+
+    With ``global_samples`` = s >= 1 the globalized rank G[n] against s
+    samples per block and the sample slots sample_idx[p*s] are filled too.
+    """
     mem = _mode(residues, offsets)
     res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
     n = offs.shape[0] - 1
     cm = None if class_map is None else _host(class_map, np.uint8)
     ka = kmer_alphabet if kmer_alphabet is not None else alphabet
-    params = KmerParams(k, ka, None if cm is None else cm.ctypes.data, cap, p)
+    params = KmerParams(k, ka, None if cm is None else cm.ctypes.data, cap, p, global_samples)
+    gs = global_samples
     out = dict(dloc=_empty(max(n, 0), np.uint64, mem, offs), dcen=_empty(max(n, 0), np.uint64, mem, offs),
                la=_empty(p, np.int32, mem, offs), ga=_empty(1, np.int32, mem, offs),
                key_a=_empty(max(n, 0), np.int32, mem, offs), key_b=_empty(max(n, 0), np.int32, mem, offs),
-               A=_empty((n, n), np.int32, mem, offs) if want_A else None)
-    ro = RankOut(*[_ptr(out[x]) if out[x] is not None and (n > 0 or x in ("la", "ga")) else None
-                   for x in ("dloc", "dcen", "la", "ga", "key_a", "key_b", "A")])
+               A=_empty((n, n), np.int32, mem, offs) if want_A else None,
+               G=_empty(max(n, 0), np.uint64, mem, offs) if gs > 0 else None,
+               sample_idx=_empty(p * gs, np.int32, mem, offs) if gs > 0 else None)
+    ro = RankOut(*[_ptr(out[x]) if out[x] is not None and (n > 0 or x in ("la", "ga", "sample_idx")) else None
+                   for x in ("dloc", "dcen", "la", "ga", "key_a", "key_b", "A", "G", "sample_idx")])
     # the C side requires non-NULL output pointers even for n == 0
     dummy = _empty(8, np.int64, mem, offs)
-    for f in ("dloc", "dcen", "key_a", "key_b"):
+    for f in ("dloc", "dcen", "key_a", "key_b") + (("G",) if gs > 0 else ()):
         if getattr(ro, f) is None:
             setattr(ro, f, _ptr(dummy))
     ss = _seqset(res, offs, alphabet)
@@ -285,6 +294,19 @@ def partition(key_a, key_b, p: int, ctx=None, stream=None) -> dict:
     piv = _empty(max(p - 1, 0), np.int32, mem, ka)
     _check(load().sad_partition(_ctx(ctx), n, _ptr(ka), _ptr(kb), p, _ptr(bo), _ptr(order),
                                 _ptr(piv) if p > 1 else None, mem, _stream(stream, mem)))
+    return dict(bucket_offsets=bo, order=order, pivot_idx=piv)
+
+
+def partition_keys64(keys, p: int, ctx=None, stream=None) -> dict:
+    """sad_partition_keys64 on uint64 rank keys: dict(bucket_offsets, order, pivot_idx)."""
+    mem = _mode(keys)
+    ky = _as(keys, np.uint64, mem)
+    n = ky.shape[0]
+    bo = _empty(p + 1, np.int32, mem, ky)
+    order = _empty(n, np.int32, mem, ky)
+    piv = _empty(max(p - 1, 0), np.int32, mem, ky)
+    _check(load().sad_partition_keys64(_ctx(ctx), n, _ptr(ky), p, _ptr(bo), _ptr(order),
+                                       _ptr(piv) if p > 1 else None, mem, _stream(stream, mem)))
     return dict(bucket_offsets=bo, order=order, pivot_idx=piv)
 
 
@@ -318,7 +340,8 @@ def bucket_pair_scores(residues, offsets, alphabet: int, bucket_offsets, order, 
 
 def pipeline(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: int, gap_extend: int,
              cap: int = 0, kmer_alphabet: int | None = None, class_map=None, mode: int = PERSISTENT,
-             capacity: int | None = None, want_rank: bool = True, ctx=None, stream=None, out=None) -> dict:
+             capacity: int | None = None, want_rank: bool = True, global_samples: int = 0, ctx=None,
+             stream=None, out=None) -> dict:
     """sad_pipeline: rank outputs, bucket layout and scores in one call.
 
     ``out`` may carry preallocated buffers (keys as in the returned dict) so
@@ -329,7 +352,7 @@ def pipeline(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: 
     n = offs.shape[0] - 1
     cm = None if class_map is None else _host(class_map, np.uint8)
     ka = kmer_alphabet if kmer_alphabet is not None else alphabet
-    params = KmerParams(k, ka, None if cm is None else cm.ctypes.data, cap, p)
+    params = KmerParams(k, ka, None if cm is None else cm.ctypes.data, cap, p, global_samples)
     S = _host(subst, np.int8)
     if capacity is None:
         capacity = n * (n + 1) // 2  # any layout fits
@@ -343,8 +366,12 @@ def pipeline(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: 
         for key, shape, dt in (("dloc", n, np.uint64), ("dcen", n, np.uint64), ("la", p, np.int32),
                                ("ga", 1, np.int32), ("key_a", n, np.int32), ("key_b", n, np.int32)):
             o.setdefault(key, _empty(max(shape, 1), dt, mem, offs))
+        if global_samples > 0:
+            o.setdefault("G", _empty(max(n, 1), np.uint64, mem, offs))
+            o.setdefault("sample_idx", _empty(p * global_samples, np.int32, mem, offs))
         ro = RankOut(_ptr(o["dloc"]), _ptr(o["dcen"]), _ptr(o["la"]), _ptr(o["ga"]), _ptr(o["key_a"]),
-                     _ptr(o["key_b"]), None)
+                     _ptr(o["key_b"]), None, _ptr(o.get("G")) if global_samples > 0 else None,
+                     _ptr(o.get("sample_idx")) if global_samples > 0 else None)
     ss = _seqset(res, offs, alphabet)
     _check(load().sad_pipeline(_ctx(ctx), ctypes.byref(ss), ctypes.byref(params), S.ctypes.data, gap_open,
                                gap_extend, mode, ctypes.byref(ro) if ro is not None else None,
@@ -411,11 +438,12 @@ class Server:
         self._keep = {}
 
     def submit(self, residues, offsets, alphabet, k, p, subst, gap_open, gap_extend, cap=0,
-               kmer_alphabet=None, class_map=None) -> int:
+               kmer_alphabet=None, class_map=None, global_samples=0) -> int:
         res, offs = _host(residues, np.uint8), _host(offsets, np.int64)
         S = _host(subst, np.int8)
         cm = None if class_map is None else _host(class_map, np.uint8)
-        kp = KmerParams(k, kmer_alphabet or alphabet, None if cm is None else cm.ctypes.data, cap, p)
+        kp = KmerParams(k, kmer_alphabet or alphabet, None if cm is None else cm.ctypes.data, cap, p,
+                        global_samples)
         job = Job(res.ctypes.data, offs.ctypes.data, len(offs) - 1, alphabet, kp, S.ctypes.data, gap_open,
                   gap_extend)
         jid = ctypes.c_uint64()

@@ -52,9 +52,14 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     from paper_0901_2742_gb300 import sad
     res = np.zeros(4, np.uint8)
     offs = np.array([0, 4], np.int64)
-    for kw in (dict(k=0, p=2), dict(k=3, p=0), dict(k=3, p=2, cap=9), dict(k=9, p=2)):
+    for kw in (dict(k=0, p=2), dict(k=3, p=0), dict(k=3, p=2, cap=9), dict(k=9, p=2),
+               dict(k=3, p=2, global_samples=-1), dict(k=3, p=2, global_samples=1025)):
         with pytest.raises(sad.SadError) as e:
             sad.kmer_rank(res, offs, 20, **kw)
+        assert e.value.code == sad.SAD_EINVAL
+    for p in (0, 1025):
+        with pytest.raises(sad.SadError) as e:
+            sad.partition_keys64(np.zeros(3, np.uint64), p)
         assert e.value.code == sad.SAD_EINVAL
     # asymmetric substitution matrix and positive gap costs
     S = np.zeros((20, 20), np.int8)
