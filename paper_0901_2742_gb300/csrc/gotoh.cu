@@ -385,6 +385,167 @@ __device__ void align_pair16(const uint32_t* __restrict__ prof, int32_t m1, int3
     }
 }
 
+// The same alignment with two subject columns per lane step. In step c the
+// lane takes columns j1 = 2c+1 and j2 = 2c+2; sub-step r updates row r to
+// column j1 and row r-1 to column j2 (a skew of one row), so the two column
+// chains F -> H -> H+go+ge are independent and interleave. The instruction
+// count per cell is unchanged; a step hands two (H, F) pairs and two letters
+// to the next lane.
+template <int R>
+__device__ void align_pair16x2(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2,
+                               const uint8_t* __restrict__ y, int32_t n, int32_t nsteps_warp,
+                               const GotohArgs& a, int32_t* __restrict__ bnd, int lane, unsigned gmask,
+                               int32_t* r1, int32_t* r2) {
+    const int G = a.G;
+    const int32_t go = a.go, ge = a.ge;
+    const uint32_t NEG2 = pk2(NEG16, NEG16);
+    const uint32_t ge2 = pk2(ge, ge), goe2 = pk2(go + ge, go + ge);
+    const int32_t strip_h = G * R;
+    const int32_t mrows = max(m1, m2);
+    const int32_t strips = (mrows + strip_h - 1) / strip_h;
+    const int32_t npairs = (n + 1) >> 1;
+    for (int32_t s = 0; s < strips; s++) {
+        const int32_t row0 = s * strip_h + lane * R;
+        uint32_t H[R], Hg[R], E[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int32_t b0 = go + (row0 + r + 1) * ge;
+            H[r] = pk2(b0, b0);
+            Hg[r] = __viaddmax_s16x2(H[r], goe2, NEG2);
+            E[r] = NEG2;
+        }
+        const int32_t d0 = (row0 == 0) ? 0 : go + row0 * ge;
+        uint32_t hdiag = pk2(d0, d0);  // H(row0 - 1, j1 - 1)
+        uint32_t hin1 = 0, fin1 = NEG2, hin2 = 0, fin2 = NEG2, yin = 0, yword = 0;
+        const bool last_strip = s == strips - 1;
+        for (int32_t tau = 0; tau < nsteps_warp; tau++) {
+            if (lane == 0 && tau < npairs) {
+                // letters y_{2tau+1}, y_{2tau+2} (0-based 2tau, 2tau+1); the padding is zeros
+                if ((tau & 1) == 0) yword = *(const uint32_t*)(y + 2 * tau);
+                yin = (yword >> (16 * (tau & 1))) & 0xffffu;
+                const int32_t j1 = 2 * tau + 1;
+                if (s == 0) {
+                    const int32_t b1 = go + j1 * ge, b2 = b1 + ge;
+                    hin1 = pk2(b1, b1);
+                    hin2 = pk2(b2, b2);
+                    fin1 = NEG2;
+                    fin2 = NEG2;
+                } else {
+                    hin1 = (uint32_t)bnd[2 * j1];
+                    fin1 = (uint32_t)bnd[2 * j1 + 1];
+                    if (j1 < n) {  // column j1 + 1 exists (the buffer holds columns 0..n)
+                        hin2 = (uint32_t)bnd[2 * j1 + 2];
+                        fin2 = (uint32_t)bnd[2 * j1 + 3];
+                    }
+                }
+            }
+            const int32_t c = tau - lane;
+            const int32_t j1 = 2 * c + 1, j2 = j1 + 1;
+            uint32_t hout1 = hin1, fout1 = fin1, hout2 = hin2, fout2 = fin2;
+            if (c >= 0 && j1 <= n) {
+                const bool two = j2 <= n;
+                const int64_t chunk = (int64_t)(row0 / R) * rpad<R>();
+                uint32_t sc1[R];
+                load_profile32<R>(prof + (int64_t)(yin & 0xffu) * a.prof_stride + chunk, sc1);
+                uint32_t fu1 = fin1, hgu1 = __viaddmax_s16x2(hin1, goe2, NEG2), hd1 = hdiag;
+                if (two) {
+                    // both columns: no branch inside the unrolled rows, so the two
+                    // chains interleave
+                    uint32_t sc2[R];
+                    load_profile32<R>(prof + (int64_t)(yin >> 8) * a.prof_stride + chunk, sc2);
+                    uint32_t fu2 = fin2, hgu2 = __viaddmax_s16x2(hin2, goe2, NEG2), hd2 = hin1;
+#pragma unroll
+                    for (int r = 0; r <= R; r++) {
+                        if (r >= 1) {  // column j2, row r - 1 (its left neighbour is column j1)
+                            const int q = r - 1;
+                            const uint32_t e = __viaddmax_s16x2(E[q], ge2, Hg[q]);
+                            const uint32_t f = __viaddmax_s16x2(fu2, ge2, hgu2);
+                            const uint32_t t = __viaddmax_s16x2(hd2, sc2[q], NEG2);
+                            const uint32_t h = __vimax3_s16x2(t, e, f);
+                            hd2 = H[q];
+                            H[q] = h;
+                            Hg[q] = __viaddmax_s16x2(h, goe2, NEG2);
+                            E[q] = e;
+                            fu2 = f;
+                            hgu2 = Hg[q];
+                        }
+                        if (r < R) {  // column j1, row r
+                            const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
+                            const uint32_t f = __viaddmax_s16x2(fu1, ge2, hgu1);
+                            const uint32_t t = __viaddmax_s16x2(hd1, sc1[r], NEG2);
+                            const uint32_t h = __vimax3_s16x2(t, e, f);
+                            hd1 = H[r];
+                            H[r] = h;
+                            Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
+                            E[r] = e;
+                            fu1 = f;
+                            hgu1 = Hg[r];
+                            if (r == R - 1) {
+                                hout1 = h;
+                                fout1 = f;
+                            }
+                        }
+                    }
+                    hout2 = H[R - 1];
+                    fout2 = fu2;
+                } else {
+                    // the last column of an odd-length subject
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
+                        const uint32_t f = __viaddmax_s16x2(fu1, ge2, hgu1);
+                        const uint32_t t = __viaddmax_s16x2(hd1, sc1[r], NEG2);
+                        const uint32_t h = __vimax3_s16x2(t, e, f);
+                        hd1 = H[r];
+                        H[r] = h;
+                        Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
+                        E[r] = e;
+                        fu1 = f;
+                        hgu1 = Hg[r];
+                    }
+                    hout1 = H[R - 1];
+                    fout1 = fu1;
+                }
+                hdiag = hin2;
+                if (!last_strip && lane == G - 1) {
+                    bnd[2 * j1] = (int32_t)hout1;
+                    bnd[2 * j1 + 1] = (int32_t)fout1;
+                    if (two) {
+                        bnd[2 * j2] = (int32_t)hout2;
+                        bnd[2 * j2 + 1] = (int32_t)fout2;
+                    }
+                }
+            }
+            hin1 = __shfl_up_sync(gmask, hout1, 1, G);
+            fin1 = __shfl_up_sync(gmask, fout1, 1, G);
+            hin2 = __shfl_up_sync(gmask, hout2, 1, G);
+            fin2 = __shfl_up_sync(gmask, fout2, 1, G);
+            yin = __shfl_up_sync(gmask, yin, 1, G);
+        }
+        __syncwarp(gmask);
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int32_t mq = q == 0 ? m1 : m2;
+            if (mq >= 1 && (mq - 1) / strip_h == s) {
+                const int32_t rr = (mq - 1) - s * strip_h;
+                const int owner = rr / R, rsel = rr % R;
+                uint32_t v = 0;
+#pragma unroll
+                for (int r = 0; r < R; r++) v = (r == rsel) ? H[r] : v;
+                v = __shfl_sync(gmask, v, owner, G);
+                if (q == 0) *r1 = lo16(v);
+                else *r2 = hi16(v);
+            }
+        }
+    }
+}
+
+// Columns per lane step of the packed kernel for R rows per lane.
+template <int R>
+__host__ __device__ constexpr int pair_cols() {
+    return 2;
+}
+
 // Work item (bucket, query pair qp, subjects [v0, v1)): queries are the
 // members at length-order positions 2qp and 2qp+1 of the bucket.
 template <int R>
@@ -442,12 +603,18 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
                 ys = a.order[boff + uv];
                 n = a.len[ys];
             }
-            const int32_t need = (have && mrows > 0 && n > 0) ? n + G - 1 : 0;
+            constexpr int kC = pair_cols<R>();
+            const int32_t need = (have && mrows > 0 && n > 0) ? (n + kC - 1) / kC + G - 1 : 0;
             const int32_t steps = (__reduce_max_sync(0xffffffffu, need) + 3) & ~3;
             int32_t s1 = 0, s2 = 0;
-            if (steps > 0)
-                align_pair16<R>(prof32, m1, m2, a.res + a.pad_off[have ? ys : x1], (have && mrows > 0) ? n : 0,
-                                steps, a, bnd, lane, gmask, &s1, &s2);
+            if (steps > 0) {
+                const uint8_t* yp = a.res + a.pad_off[have ? ys : x1];
+                const int32_t ny = (have && mrows > 0) ? n : 0;
+                if constexpr (kC == 2)
+                    align_pair16x2<R>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
+                else
+                    align_pair16<R>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
+            }
             if (have && lane == 0) {
                 const int32_t mq[2] = {m1, m2};
                 int32_t sc[2] = {s1, s2};
