@@ -256,7 +256,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", type=int, default=2, help="2: N=2000 paper scale; 4: N=20000")
-    ap.add_argument("--cap", type=int, default=4, help="0: uint8 CUDA-core k-mer path; >0 planes")
+    ap.add_argument("--cap", type=int, default=4,
+                    help="0: uint8 CUDA-core k-mer path; >0 tensor-core planes; -1 sorted k-mer lists")
     ap.add_argument("--mode", type=int, default=1, help="0: per-bucket launches, 1: persistent")
     ap.add_argument("--no-tune", action="store_true", help="skip the per-length-bin variant autotuner")
     ap.add_argument("--global-samples", type=int, default=0,
@@ -403,7 +404,8 @@ def main():
         "vs_baseline": None, "dtype": "int16x2" if packed else "int32",
         "data": "synthetic (seeded tree-evolved families)",
         "config": {"workload": w.name, "n": n, "p": p, "k": w.k,
-                   "kmer_path": "uint8 min-sum, CUDA cores" if w.cap == 0 else f"cap-{w.cap} threshold planes, tensor cores",
+                   "kmer_path": ("sorted k-mer lists, CUDA cores" if w.cap < 0 else "uint8 min-sum, CUDA cores"
+                                 if w.cap == 0 else f"cap-{w.cap} threshold planes, tensor cores"),
                    "scores_mode": "persistent" if args.mode == 1 else "one launch per bucket",
                    "rank": (f"globalized, {gs} samples per block" if gs > 0
                             else "centralized against the global ancestor"),

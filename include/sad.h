@@ -62,7 +62,9 @@ extern "C" {
 
 /* Limits of this build (checked; violating one gives SAD_EINVAL). */
 #define SAD_MAX_ALPHABET 32     /* residue codes 0..alphabet-1 */
-#define SAD_MAX_KMER_SPACE 49152 /* kmer_alphabet^k */
+#define SAD_MAX_KMER_SPACE 49152 /* kmer_alphabet^k on the dense count-row paths */
+#define SAD_MAX_SPARSE_KMER_SPACE 2147483647 /* kmer_alphabet^k on the sorted-list path */
+#define SAD_MAX_SPARSE_KMERS 8192 /* |x| - k + 1 of any sequence on the sorted-list path */
 
 typedef struct sad_ctx sad_ctx;
 
@@ -87,14 +89,27 @@ typedef struct sad_seqset {
  *            cap, contracted on the tensor cores; exact for any count. */
 typedef struct sad_kmer_params {
     int32_t k;               /* >= 1 */
-    int32_t kmer_alphabet;   /* >= 1; kmer_alphabet^k <= SAD_MAX_KMER_SPACE */
+    int32_t kmer_alphabet;   /* >= 1; kmer_alphabet^k <= SAD_MAX_KMER_SPACE, or
+                              * SAD_MAX_SPARSE_KMER_SPACE on the sorted-list path */
     const uint8_t* class_map; /* host, `alphabet` entries, or NULL */
-    int32_t cap;             /* 0, or 1..8 */
+    int32_t cap;             /* k-mer similarity path:
+                              *   0      uint8 count rows, CUDA cores (the sorted-list
+                              *          path when kmer_alphabet^k > SAD_MAX_KMER_SPACE)
+                              *   1..8   threshold planes [count >= t], t <= cap, on the
+                              *          tensor cores, counts above cap by a residual
+                              *   SAD_KMER_SPARSE  sorted (k-mer, count) lists per
+                              *          sequence, work proportional to the distinct
+                              *          k-mers (any kmer_alphabet^k up to
+                              *          SAD_MAX_SPARSE_KMER_SPACE; every sequence at
+                              *          most SAD_MAX_SPARSE_KMERS k-mers)
+                              * every path gives identical results */
     int32_t p;               /* number of blocks / buckets, >= 1 */
     int32_t global_samples;  /* 0, or s in 1..SAD_MAX_GLOBAL_SAMPLES: also compute the
                               * globalized rank G against s samples per block
                               * (sad_rank_out.G); sad_pipeline then partitions by G */
 } sad_kmer_params;
+
+#define SAD_KMER_SPARSE (-1)
 
 #define SAD_MAX_GLOBAL_SAMPLES 1024
 

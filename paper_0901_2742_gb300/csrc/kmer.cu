@@ -15,10 +15,6 @@ namespace {
 
 constexpr int kCountThreads = 256;
 
-struct ClassMap {
-    uint8_t c[SAD_MAX_ALPHABET];
-};
-
 // ---------------------------------------------------------------------------
 // K1: one CTA per sequence. k-mer histogram in shared memory, then
 //   C8[i][tau]        = min(count, 255)                       (uint8, stride Vs)
@@ -584,20 +580,31 @@ k_sample_sums(int32_t n, int32_t nslots, int32_t Vs, uint32_t T, const uint8_t* 
 
 }  // namespace
 
+bool uses_sparse_path(const sad_kmer_params* kp) {
+    if (kp->cap == SAD_KMER_SPARSE) return true;
+    int64_t V = 1;
+    for (int t = 0; t < kp->k; t++) {
+        V *= kp->kmer_alphabet;
+        if (V > SAD_MAX_KMER_SPACE) return true;
+    }
+    return false;
+}
+
 int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
                      const KmerOutDev& out, cudaStream_t stream) {
     const int32_t n = S.n;
-    const int32_t k = kp->k, A2 = kp->kmer_alphabet, p = kp->p, cap = kp->cap;
+    const int32_t k = kp->k, A2 = kp->kmer_alphabet, p = kp->p;
+    const bool sparse = uses_sparse_path(kp);
+    const int32_t cap = sparse ? 0 : kp->cap;
     int64_t V = 1;
-    for (int t = 0; t < k; t++) {
-        V *= A2;
-        SAD_CHECK(V <= SAD_MAX_KMER_SPACE, SAD_EINVAL,
-                  "k-mer space %d^%d exceeds SAD_MAX_KMER_SPACE (%d)", A2, k, SAD_MAX_KMER_SPACE);
-    }
-    const int32_t Vs = (int32_t)round_up(V, 64);
+    for (int t = 0; t < k; t++) V = std::min<int64_t>(V * A2, (int64_t)1 << 40);
+    const int32_t Vs = sparse ? 0 : (int32_t)round_up(V, 64);
     const int32_t T = cap > 0 ? cap : 255;
     SAD_CHECK(cap == 0 || S.max_len - k + 1 < 65536, SAD_EINVAL,
               "the threshold-plane path takes sequences of fewer than 65536 k-mers (longest: %d); use cap = 0",
+              S.max_len - k + 1);
+    SAD_CHECK(!sparse || S.max_len - k + 1 <= SAD_MAX_SPARSE_KMERS, SAD_EINVAL,
+              "the sorted-list path takes sequences of at most %d k-mers (longest: %d)", SAD_MAX_SPARSE_KMERS,
               S.max_len - k + 1);
     ClassMap cm;
     memset(&cm, 0, sizeof(cm));
@@ -618,8 +625,9 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     std::vector<uint64_t> q32(n);
     std::vector<uint32_t> r32(n);
     std::vector<float> inv(n);
-    std::vector<int64_t> exoff(n + 1);
+    std::vector<int64_t> exoff(n + 1), loff(n + 1);
     exoff[0] = 0;
+    loff[0] = 0;
     for (int32_t i = 0; i < n; i++) {
         nkb[i] = S.h_len[i] - k + 1;
         if (nkb[i] >= 1) {
@@ -632,6 +640,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
             inv[i] = 0.0f;
         }
         exoff[i + 1] = exoff[i] + (nkb[i] > 0 ? nkb[i] / (T + 1) : 0);
+        loff[i + 1] = loff[i] + std::max(nkb[i], 0);
     }
     for (int32_t b = 0; b < p; b++) {
         const int64_t lo = (int64_t)b * n / p, hi = (int64_t)(b + 1) * n / p;
@@ -646,7 +655,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     };
     const size_t o_nkb = carve(4ull * n), o_blk = carve(4ull * n), o_q = carve(8ull * n),
                  o_r = carve(4ull * n), o_inv = carve(4ull * n), o_exoff = carve(8ull * (n + 1)),
-                 o_nex = carve(4ull * n),
+                 o_loff = carve(8ull * (n + 1)), o_nex = carve(4ull * n), o_nd = carve(4ull * n),
                  o_sT = carve(4ull * n), o_hidx = carve(4ull * n), o_hlist = carve(4ull * n),
                  o_H = carve(16), o_gsum = carve(8ull * p);
     const size_t host_bytes = o_nex;  // the host-filled prefix
@@ -662,6 +671,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     memcpy(hp + o_r, r32.data(), 4ull * n);
     memcpy(hp + o_inv, inv.data(), 4ull * n);
     memcpy(hp + o_exoff, exoff.data(), 8ull * (n + 1));
+    memcpy(hp + o_loff, loff.data(), 8ull * (n + 1));
     SAD_CUDA(cudaMemcpyAsync(misc, pin, host_bytes, cudaMemcpyHostToDevice, stream));
     char* dm = (char*)misc;
     SeqTables tab;
@@ -680,10 +690,12 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     int32_t* d_H = (int32_t*)(dm + o_H);
     uint64_t* d_gsum = (uint64_t*)(dm + o_gsum);
 
-    // counts (+ planes)
+    // counts (+ planes), or the sorted (code, count) lists
     void* c8 = nullptr;
     const int64_t nrows = round_up(n, 128);
-    SAD_RET(workspace(ctx, WS_COUNTS, (size_t)(nrows * Vs), stream, &c8));
+    SAD_RET(workspace(ctx, WS_COUNTS, sparse ? (size_t)(8 * std::max<int64_t>(loff[n], 1)) : (size_t)(nrows * Vs),
+                      stream, &c8));
+    SparseLists L{(const uint2*)c8, (const int64_t*)(dm + o_loff), (const int32_t*)(dm + o_nd)};
     uint8_t* planes = nullptr;
     if (cap > 0) {
         void* pl = nullptr;
@@ -703,17 +715,31 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     int32_t H = 0;
     {
     TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
-    if (smem > 48 * 1024)
-        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_count));
-    k_count<<<n, kCountThreads, smem, stream>>>(S.res, S.pad_off, S.len, k, A2, Vs, cm, T, cap,
-                                               (uint8_t*)c8, planes, (const int64_t*)(dm + o_exoff),
-                                               ex_tau, ex_val, d_nex, d_sT);
-    SAD_LAUNCHED();
+    if (sparse) {
+        SAD_RET(sparse_count(ctx, S, k, A2, cm, T, (const int64_t*)(dm + o_loff), (uint2*)c8,
+                             (int32_t*)(dm + o_nd), (const int64_t*)(dm + o_exoff), ex_tau, ex_val, d_nex,
+                             stream));
+    } else {
+        if (smem > 40 * 1024)  // with the static shared memory above the default 48 KiB
+            SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_count));
+        k_count<<<n, kCountThreads, smem, stream>>>(S.res, S.pad_off, S.len, k, A2, Vs, cm, T, cap,
+                                                   (uint8_t*)c8, planes, (const int64_t*)(dm + o_exoff),
+                                                   ex_tau, ex_val, d_nex, d_sT);
+        SAD_LAUNCHED();
+    }
     k_heavy_index<<<1, 1024, 0, stream>>>(n, d_nex, d_hidx, d_hlist, d_H);
     SAD_LAUNCHED();
     }
     SAD_CUDA(cudaMemcpyAsync(&H, d_H, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    // the sorted-list path sizes its hash tables from the distinct k-mer counts
+    std::vector<int32_t> nd_host;
+    int32_t max_nd = 0;
+    if (sparse) {
+        nd_host.resize(n);
+        SAD_CUDA(cudaMemcpyAsync(nd_host.data(), dm + o_nd, 4ull * n, cudaMemcpyDeviceToHost, stream));
+    }
     SAD_CUDA(cudaStreamSynchronize(stream));
+    for (int32_t v : nd_host) max_nd = std::max(max_nd, v);
     if (H > 0) {
         TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
         SAD_CHECK((int64_t)H * H <= (1ll << 29), SAD_ENOMEM,
@@ -733,7 +759,9 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     // all pairs
     {
     TraceScope ts(ctx, SAD_STAGE_ALLPAIRS, stream);
-    if (cap > 0) {
+    if (sparse) {
+        SAD_RET(sparse_allpairs(ctx, n, L, tab, nd_host.data(), V, out.dloc, out.dcen, out.A, stream));
+    } else if (cap > 0) {
         SAD_RET(allpairs_planes(ctx, n, cap * Vs, planes, tab, out.dloc, out.dcen, out.A, stream));
     } else {
         const int32_t ntiles = (int32_t)((n + kTile - 1) / kTile);
@@ -748,13 +776,21 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     TraceScope ts(ctx, SAD_STAGE_RANK, stream);
     k_local_ancestors<<<p, 256, 0, stream>>>(n, p, out.dloc, out.la);
     SAD_LAUNCHED();
-    k_ga_sums<<<p, 256, 0, stream>>>(p, out.la, (const uint8_t*)c8, Vs, (uint32_t)T, tab, d_gsum);
-    SAD_LAUNCHED();
+    if (sparse) {
+        SAD_RET(sparse_ga_sums(ctx, n, p, out.la, L, tab, max_nd, V, d_gsum, stream));
+    } else {
+        k_ga_sums<<<p, 256, 0, stream>>>(p, out.la, (const uint8_t*)c8, Vs, (uint32_t)T, tab, d_gsum);
+        SAD_LAUNCHED();
+    }
     k_ga_select<<<1, 32, 0, stream>>>(p, out.la, d_gsum, out.ga);
     SAD_LAUNCHED();
-    k_key_column<<<(n + 7) / 8, 256, 0, stream>>>(n, out.ga, (const uint8_t*)c8, Vs, (uint32_t)T,
-                                                  tab, out.key_a, out.key_b);
-    SAD_LAUNCHED();
+    if (sparse) {
+        SAD_RET(sparse_key_column(ctx, n, out.ga, L, tab, max_nd, V, out.key_a, out.key_b, stream));
+    } else {
+        k_key_column<<<(n + 7) / 8, 256, 0, stream>>>(n, out.ga, (const uint8_t*)c8, Vs, (uint32_t)T,
+                                                      tab, out.key_a, out.key_b);
+        SAD_LAUNCHED();
+    }
     }
     // globalized rank against s samples per block
     const int32_t gs = kp->global_samples;
@@ -772,7 +808,9 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         SAD_LAUNCHED();
         SAD_CUDA(cudaMemsetAsync(out.G, 0, 8ull * n, stream));
         const dim3 grid((unsigned)((n + kTile - 1) / kTile), (unsigned)((nslots + kTile - 1) / kTile));
-        if (T < 255)
+        if (sparse)
+            SAD_RET(sparse_sample_sums(ctx, n, (int32_t)nslots, out.samples, L, tab, max_nd, V, out.G, stream));
+        else if (T < 255)
             k_sample_sums<true><<<grid, 256, 0, stream>>>(n, (int32_t)nslots, Vs, (uint32_t)T,
                                                           (const uint8_t*)c8, d_sT, tab, out.samples, out.G);
         else
@@ -787,17 +825,20 @@ int validate_kmer_params(const sad_seqset* s, const sad_kmer_params* kp) {
     SAD_CHECK(kp != nullptr, SAD_EINVAL, "params is NULL");
     SAD_CHECK(kp->k >= 1, SAD_EINVAL, "k = %d < 1", kp->k);
     SAD_CHECK(kp->p >= 1 && kp->p <= 1024, SAD_EINVAL, "p = %d outside 1..1024", kp->p);
-    SAD_CHECK(kp->cap >= 0 && kp->cap <= 8, SAD_EINVAL, "cap = %d outside 0..8", kp->cap);
+    SAD_CHECK(kp->cap >= SAD_KMER_SPARSE && kp->cap <= 8, SAD_EINVAL, "cap = %d outside -1..8", kp->cap);
     SAD_CHECK(kp->global_samples >= 0 && kp->global_samples <= SAD_MAX_GLOBAL_SAMPLES, SAD_EINVAL,
               "global_samples = %d outside 0..%d", kp->global_samples, SAD_MAX_GLOBAL_SAMPLES);
     SAD_CHECK(kp->kmer_alphabet >= 1 && kp->kmer_alphabet <= SAD_MAX_ALPHABET, SAD_EINVAL,
               "kmer_alphabet = %d outside 1..%d", kp->kmer_alphabet, SAD_MAX_ALPHABET);
+    const bool sparse = uses_sparse_path(kp);
+    SAD_CHECK(kp->cap <= 0 || !sparse, SAD_EINVAL,
+              "k-mer space %d^%d exceeds SAD_MAX_KMER_SPACE (%d) of the threshold-plane path",
+              kp->kmer_alphabet, kp->k, SAD_MAX_KMER_SPACE);
     int64_t V = 1;
     for (int t = 0; t < kp->k; t++) {
         V *= kp->kmer_alphabet;
-        SAD_CHECK(V <= SAD_MAX_KMER_SPACE, SAD_EINVAL,
-                  "k-mer space %d^%d exceeds SAD_MAX_KMER_SPACE (%d)", kp->kmer_alphabet, kp->k,
-                  SAD_MAX_KMER_SPACE);
+        SAD_CHECK(V <= SAD_MAX_SPARSE_KMER_SPACE, SAD_EINVAL,
+                  "k-mer space %d^%d exceeds SAD_MAX_SPARSE_KMER_SPACE", kp->kmer_alphabet, kp->k);
     }
     SAD_CHECK(s->alphabet >= 1 && s->alphabet <= SAD_MAX_ALPHABET, SAD_EINVAL,
               "alphabet %d outside 1..%d", s->alphabet, SAD_MAX_ALPHABET);

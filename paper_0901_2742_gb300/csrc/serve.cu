@@ -88,13 +88,14 @@ int64_t kmer_space(const sad_kmer_params& kp) {
 // planes, excess lists, per-sequence tables, partition scratch, and the scores
 // of buckets within the regular-sampling bound (each < 2N/p + p members).
 int64_t estimate_job_bytes(int32_t n, int64_t total, const sad_kmer_params& kp) {
-    const int64_t Vs = round_up(kmer_space(kp), 64);
+    const bool sparse = uses_sparse_path(&kp);
+    const int64_t Vs = sparse ? 0 : round_up(kmer_space(kp), 64);
     const int64_t rows = round_up(std::max<int32_t>(n, 1), 128);
     const int64_t p = kp.p;
     const int64_t w = 2 * ((int64_t)n + p - 1) / p + p;
     const int64_t score_ints = std::min<int64_t>((int64_t)n * (n + 1) / 2, p * w * (w + 1) / 2);
     int64_t b = 2 * total + 48ll * n + 64 * 1024;         // residues (raw + padded), tables
-    b += rows * Vs * (1 + kp.cap);                          // counts, planes
+    b += sparse ? 8 * total : rows * Vs * (1 + kp.cap);     // sorted lists, or counts and planes
     b += 8 * total;                                         // excess lists (upper bound)
     b += 48ll * n + 40 * p * p;                             // partition (up to 16-byte keys)
     b += 12ll * n + 4 * p * kp.global_samples;              // globalized rank

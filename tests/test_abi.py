@@ -53,7 +53,8 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     res = np.zeros(4, np.uint8)
     offs = np.array([0, 4], np.int64)
     for kw in (dict(k=0, p=2), dict(k=3, p=0), dict(k=3, p=2, cap=9), dict(k=9, p=2),
-               dict(k=3, p=2, global_samples=-1), dict(k=3, p=2, global_samples=1025)):
+               dict(k=3, p=2, global_samples=-1), dict(k=3, p=2, global_samples=1025),
+               dict(k=4, p=2, cap=4), dict(k=3, p=2, cap=-2), dict(k=8, p=2, cap=-1)):
         with pytest.raises(sad.SadError) as e:
             sad.kmer_rank(res, offs, 20, **kw)
         assert e.value.code == sad.SAD_EINVAL
