@@ -14,6 +14,8 @@
  *      using any sequential multiple alignment system", Section 2.3.3):
  *        sad_bucket_pair_scores  all-pairs global affine-gap (Gotoh) scores
  *                                inside every bucket
+ *        sad_align_pairs         the alignments themselves (traceback) of
+ *                                given pairs
  * plus sad_pipeline (both stages in one call) and a continuous-batching
  * serving loop (sad_server_*).
  *
@@ -181,7 +183,8 @@ const char* sad_version(void);
 #define SAD_STAGE_SCORES 5     /* alignment-score kernels, 32-bit DP */
 #define SAD_STAGE_SCORES_PACKED 6 /* alignment-score kernels, two problems per 16x2 lane */
 #define SAD_STAGE_GLOBAL 7     /* globalized rank: sample selection and sums against the samples */
-#define SAD_NUM_STAGES 8
+#define SAD_STAGE_ALIGN 8      /* alignments with traceback (sad_align_pairs) */
+#define SAD_NUM_STAGES 9
 
 /* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
  * accumulated times. */
@@ -314,6 +317,30 @@ int sad_scores_autotune(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* buc
                         const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
                         int32_t gap_extend, const int32_t* bin_upper, int32_t nbins, int32_t reps,
                         int32_t mem, void* stream);
+
+/* ---- alignments (traceback) ----------------------------------------------- */
+
+/* Column codes of an alignment. */
+#define SAD_COL_MATCH 'M'  /* x_i aligned with y_j */
+#define SAD_COL_XGAP 'X'   /* x_i against a gap */
+#define SAD_COL_YGAP 'Y'   /* a gap against y_j */
+
+/* Optimal global affine-gap alignments (not only their scores) of the pairs
+ * (x, y) = (pairs[2k], pairs[2k+1]), sequence ids of seqs; the same gap model
+ * and score as sad_bucket_pair_scores (a run of g gap columns of one kind costs
+ * gap_open + g * gap_extend). The per-processor aligner of Section 2.3.3 turns
+ * pair scores into alignments; among equally good alignments any one may be
+ * returned. Outputs (caller-owned, `mem` space): scores[npairs],
+ * ops_offsets[npairs+1] (filled: pair k owns ops[ops_offsets[k] ..
+ * ops_offsets[k] + |x| + |y|)), ops[ops_capacity] (pair k's columns, first
+ * column first, SAD_COL_* bytes, at the start of its slot), ops_len[npairs]
+ * (columns of pair k). Errors: SAD_EINVAL (a pair id outside 0..n-1, gap
+ * costs > 0 or below -1000, a residue >= alphabet), SAD_ERANGE (ops_capacity
+ * below sum |x| + |y|; ops_offsets is filled), SAD_ENOMEM, SAD_ECUDA. */
+int sad_align_pairs(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* pairs, int32_t npairs,
+                    const int8_t* subst, int32_t gap_open, int32_t gap_extend, int32_t* scores,
+                    int64_t* ops_offsets, uint8_t* ops, int64_t ops_capacity, int32_t* ops_len,
+                    int32_t mem, void* stream);
 
 /* ---- both stages ------------------------------------------------------- */
 

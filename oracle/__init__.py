@@ -11,6 +11,8 @@ Functions follow the paper:
   partition           Section 2.3.2 regular-sampling redistribution
   gotoh               the per-bucket sequential aligner of Section 2.3.3, as
                       global affine-gap (Gotoh) scores
+  align               one optimal alignment (traceback through the same tables)
+  alignment_score     the score of a given alignment, from its columns
   bucket_pair_scores  all pairs u <= v inside every bucket
 
 Parity status: every function here is pinned by tests that do not reuse this
@@ -61,6 +63,10 @@ def _bind(lib):
     lib.orc_partition.argtypes = [i32, P, P, i32, P, P, P]
     lib.orc_gotoh.restype = i64
     lib.orc_gotoh.argtypes = [P, i32, P, i32, P, i32, i32, i32]
+    lib.orc_align.restype = i64
+    lib.orc_align.argtypes = [P, i32, P, i32, P, i32, i32, i32, P, P]
+    lib.orc_alignment_score.restype = ctypes.c_int
+    lib.orc_alignment_score.argtypes = [P, i32, P, i32, P, i32, P, i32, i32, i32, P]
     lib.orc_bucket_pair_scores.restype = ctypes.c_int
     lib.orc_bucket_pair_scores.argtypes = [P, P, i32, P, P, i32, P, i32, i32, i32, i32, P, P]
     return lib
@@ -199,6 +205,30 @@ def gotoh(x, y, subst, gap_open, gap_extend, lib=None) -> int:
     S = _c(subst, np.int8)
     return int(lib.orc_gotoh(_ptr(x), len(x), _ptr(y), len(y), _ptr(S), S.shape[0], gap_open,
                              gap_extend))
+
+
+def align(x, y, subst, gap_open, gap_extend, lib=None):
+    """One optimal alignment: (score, columns) with columns a str over M, X, Y."""
+    lib = lib or _load()
+    x, y = _c(x, np.uint8), _c(y, np.uint8)
+    S = _c(subst, np.int8)
+    buf = ctypes.create_string_buffer(max(1, len(x) + len(y)))
+    n = ctypes.c_int32(0)
+    sc = lib.orc_align(_ptr(x), len(x), _ptr(y), len(y), _ptr(S), S.shape[0], gap_open, gap_extend, buf,
+                       ctypes.byref(n))
+    return int(sc), buf.raw[:n.value].decode()
+
+
+def alignment_score(x, y, columns, subst, gap_open, gap_extend, lib=None):
+    """Score of a given alignment (str or bytes over M, X, Y); None if it is not an alignment of x and y."""
+    lib = lib or _load()
+    x, y = _c(x, np.uint8), _c(y, np.uint8)
+    S = _c(subst, np.int8)
+    cols = columns.encode() if isinstance(columns, str) else bytes(columns)
+    out = ctypes.c_int64(0)
+    rc = lib.orc_alignment_score(_ptr(x), len(x), _ptr(y), len(y), cols, len(cols), _ptr(S), S.shape[0],
+                                 gap_open, gap_extend, ctypes.byref(out))
+    return None if rc != 0 else int(out.value)
 
 
 def bucket_pair_scores(residues, offsets, bucket_offsets, order, subst, gap_open, gap_extend,

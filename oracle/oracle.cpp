@@ -32,6 +32,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -366,16 +367,31 @@ int orc_partition(int32_t n, const int32_t* key_a, const int32_t* key_b, int32_t
     return 0;
 }
 
-/* Global alignment score with affine gaps: a gap run of length g costs
- * go + g*ge (go, ge <= 0); end gaps cost the same as internal ones.
- * Three-state recursion over alignments ending in a match column (M), in x
- * against a gap (X) or in a gap against y (Y); 64-bit arithmetic. */
-int64_t orc_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const int8_t* S,
-                  int32_t alphabet, int32_t go, int32_t ge) {
-    const int64_t W = (int64_t)n + 1;
-    std::vector<int64_t> M((size_t)(m + 1) * W, NEG_INF), X((size_t)(m + 1) * W, NEG_INF),
-        Y((size_t)(m + 1) * W, NEG_INF);
-    auto at = [&](int64_t i, int64_t j) { return i * W + j; };
+}  // extern "C"
+
+namespace {
+
+/* The three score tables of the global affine-gap alignment: M, X and Y hold
+ * the best score of an alignment of x[0..i) with y[0..j) whose last column is
+ * a match column (M), x_i against a gap (X) or a gap against y_j (Y). A gap
+ * run of length g costs go + g*ge (go, ge <= 0); end gaps cost the same as
+ * internal ones; a run of X columns may directly follow a run of Y columns,
+ * each opening its own gap. 64-bit arithmetic; NEG_INF marks no alignment. */
+struct GotohTables {
+    int64_t W;
+    std::vector<int64_t> M, X, Y;
+    int64_t at(int64_t i, int64_t j) const { return i * W + j; }
+};
+
+GotohTables fill_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const int8_t* S,
+                       int32_t alphabet, int32_t go, int32_t ge) {
+    GotohTables t;
+    t.W = (int64_t)n + 1;
+    t.M.assign((size_t)(m + 1) * t.W, NEG_INF);
+    t.X.assign((size_t)(m + 1) * t.W, NEG_INF);
+    t.Y.assign((size_t)(m + 1) * t.W, NEG_INF);
+    std::vector<int64_t>&M = t.M, &X = t.X, &Y = t.Y;
+    auto at = [&](int64_t i, int64_t j) { return t.at(i, j); };
     M[at(0, 0)] = 0;  // the empty alignment
     for (int32_t i = 0; i <= m; i++)
         for (int32_t j = 0; j <= n; j++) {
@@ -399,7 +415,93 @@ int64_t orc_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, cons
                 Y[at(i, j)] = v;
             }
         }
-    return std::max({M[at(m, n)], X[at(m, n)], Y[at(m, n)]});
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+/* Global alignment score with affine gaps (the three tables above). */
+int64_t orc_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const int8_t* S,
+                  int32_t alphabet, int32_t go, int32_t ge) {
+    const GotohTables t = fill_gotoh(x, m, y, n, S, alphabet, go, ge);
+    return std::max({t.M[t.at(m, n)], t.X[t.at(m, n)], t.Y[t.at(m, n)]});
+}
+
+/* One optimal global alignment: columns 'M' (x_i with y_j), 'X' (x_i against a
+ * gap) and 'Y' (a gap against y_j), first column first, written to ops
+ * (capacity m + n); *len receives the column count. Traced back through the
+ * tables from the best state at (m, n), preferring M, then X, then Y among
+ * equal predecessors. Returns the score. */
+int64_t orc_align(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const int8_t* S, int32_t alphabet,
+                  int32_t go, int32_t ge, char* ops, int32_t* len) {
+    const GotohTables t = fill_gotoh(x, m, y, n, S, alphabet, go, ge);
+    auto best_of = [&](int64_t i, int64_t j, bool useM, bool useX, bool useY, int64_t want, int64_t add) {
+        if (useM && t.M[t.at(i, j)] > NEG_INF && t.M[t.at(i, j)] + add == want) return 'M';
+        if (useX && t.X[t.at(i, j)] > NEG_INF && t.X[t.at(i, j)] + add == want) return 'X';
+        if (useY && t.Y[t.at(i, j)] > NEG_INF && t.Y[t.at(i, j)] + add == want) return 'Y';
+        return '?';
+    };
+    const int64_t score = std::max({t.M[t.at(m, n)], t.X[t.at(m, n)], t.Y[t.at(m, n)]});
+    char state = best_of(m, n, true, true, true, score, 0);
+    std::string rev;
+    int64_t i = m, j = n;
+    while (i > 0 || j > 0) {
+        rev.push_back(state);
+        if (state == 'M') {
+            const int64_t v = t.M[t.at(i, j)] - S[x[i - 1] * alphabet + y[j - 1]];
+            state = best_of(i - 1, j - 1, true, true, true, v, 0);
+            i--;
+            j--;
+        } else if (state == 'X') {
+            const int64_t v = t.X[t.at(i, j)];
+            const char ext = best_of(i - 1, j, false, true, false, v, ge);
+            state = ext == 'X' ? 'X' : best_of(i - 1, j, true, false, true, v, go + ge);
+            i--;
+        } else if (state == 'Y') {
+            const int64_t v = t.Y[t.at(i, j)];
+            const char ext = best_of(i, j - 1, false, false, true, v, ge);
+            state = ext == 'Y' ? 'Y' : best_of(i, j - 1, true, true, false, v, go + ge);
+            j--;
+        } else {
+            return NEG_INF;  // cannot happen for a consistent table
+        }
+    }
+    *len = (int32_t)rev.size();
+    for (size_t c = 0; c < rev.size(); c++) ops[c] = rev[rev.size() - 1 - c];
+    return score;
+}
+
+/* Score of a given alignment (columns as in orc_align): the sum of S over the
+ * M columns plus go + g*ge for every maximal run of g X columns and every
+ * maximal run of g Y columns. Returns 0 and *score, or -1 when the columns do
+ * not consume exactly x[0..m) and y[0..n) or hold another letter. */
+int orc_alignment_score(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const char* ops,
+                        int32_t len, const int8_t* S, int32_t alphabet, int32_t go, int32_t ge,
+                        int64_t* score) {
+    int64_t total = 0, i = 0, j = 0;
+    for (int32_t c = 0; c < len; c++) {
+        const char op = ops[c];
+        if (op == 'M') {
+            if (i >= m || j >= n) return -1;
+            total += S[x[i] * alphabet + y[j]];
+            i++;
+            j++;
+        } else if (op == 'X' || op == 'Y') {
+            if (op == 'X' && i >= m) return -1;
+            if (op == 'Y' && j >= n) return -1;
+            if (c == 0 || ops[c - 1] != op) total += go;  // a new run opens
+            total += ge;
+            if (op == 'X') i++;
+            else j++;
+        } else {
+            return -1;
+        }
+    }
+    if (i != m || j != n) return -1;
+    *score = total;
+    return 0;
 }
 
 /* All pairs u <= v inside every bucket. score_offsets: p+1 (filled);

@@ -32,7 +32,8 @@ constexpr int kSortThreads = 1024;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr int kPairThreads = 256;
 constexpr int kRowsMax = 8;       // rows per CTA: one byte each in an 8-byte table value
-constexpr int32_t kColChunk = 128;
+constexpr int32_t kColChunkMin = kPairThreads / 32;  // one column per warp
+constexpr int32_t kColChunkMax = 2048;
 
 // Exclusive block-wide prefix of a per-thread flag; *total receives the sum.
 __device__ __forceinline__ int32_t block_scan_flag(bool f, int32_t* warp_tot, int32_t* total) {
@@ -348,14 +349,14 @@ int pair_shape(sad_ctx* ctx, int64_t keys8, int64_t per_row, int64_t V, int64_t 
     }
     SAD_CHECK(sh->TI > 0, SAD_EINVAL, "a sequence has too many distinct k-mers for the sorted-list hash table");
     sh->smem = (size_t)12 << sh->log2S;
+    // the widest chunk (up to 2048 columns) that still gives 8 CTAs per SM, else
+    // the narrowest (one column per warp)
     const int64_t rb = (nrows + sh->TI - 1) / sh->TI;
     const int64_t want = 8ll * ctx->num_sms;
-    sh->cw = kColChunk;
-    while (sh->cw < 16 * kColChunk) {
-        const int64_t ctas = rb * ((ncols + 2 * sh->cw - 1) / (2 * sh->cw)) / (triangle ? 2 : 1);
-        if (ctas < want) break;
-        sh->cw *= 2;
-    }
+    sh->cw = kColChunkMax;
+    while (sh->cw > kColChunkMin &&
+           rb * ((ncols + sh->cw - 1) / sh->cw) / (triangle ? 2 : 1) < want)
+        sh->cw /= 2;
     return SAD_OK;
 }
 

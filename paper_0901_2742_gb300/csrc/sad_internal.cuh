@@ -78,6 +78,8 @@ enum Slot : int {
     WS_PIPE,           // pipeline intermediates
     WS_GEMM_TILES,     // tile list of the plane GEMM
     WS_GLOBAL,         // block order of the globalized rank
+    WS_TRACE,          // alignment (traceback) call: pairs, offsets, outputs
+    WS_TRACE_DIRS,     // traceback direction words
     WS_NUM_SLOTS
 };
 

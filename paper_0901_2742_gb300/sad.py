@@ -75,6 +75,7 @@ def load():
                                          ctypes.POINTER(RankOut), i32, P]),
         "sad_partition": (ctypes.c_int, [P, i32, P, P, i32, P, P, P, i32, P]),
         "sad_partition_keys64": (ctypes.c_int, [P, i32, P, i32, P, P, P, i32, P]),
+        "sad_align_pairs": (ctypes.c_int, [P, P, P, i32, P, i32, i32, P, P, P, i64, P, i32, P]),
         "sad_partition_noalloc": (ctypes.c_int, [i32, P, P, i32, P, P, P, P]),
         "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
@@ -191,7 +192,7 @@ def _ctx(ctx):
     return None if ctx is None else ctx.handle
 
 
-STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global")
+STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global", "align")
 
 
 def trace_enable(on: bool = True, ctx=None):
@@ -336,6 +337,42 @@ def bucket_pair_scores(residues, offsets, alphabet: int, bucket_offsets, order, 
                                          gap_open, gap_extend, mode, _ptr(so), _ptr(sc), cap, mem,
                                          _stream(stream, mem)))
     return so, sc[:total]
+
+
+def align_pairs(residues, offsets, alphabet: int, pairs, subst, gap_open: int, gap_extend: int, ctx=None,
+                stream=None) -> dict:
+    """sad_align_pairs: dict(scores, ops_offsets, ops, ops_len); pairs is (npairs, 2) sequence ids.
+
+    ``columns(out, k)`` turns pair k's columns into a str over M, X, Y.
+    """
+    mem = _mode(residues, offsets, pairs)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    pr = _as(pairs, np.int32, mem)
+    npairs = pr.shape[0] if pr.ndim > 1 else pr.shape[0] // 2
+    S = _host(subst, np.int8)
+    offs_h = offs.cpu().numpy() if mem == MEM_DEVICE else offs
+    pr_h = pr.cpu().numpy() if mem == MEM_DEVICE else pr
+    lens = np.diff(offs_h)
+    ids = pr_h.reshape(-1)
+    ids = ids[(ids >= 0) & (ids < len(lens))]   # the library reports ids out of range
+    cap = int(lens[ids].sum()) if npairs else 0
+    sc = _empty(max(npairs, 1), np.int32, mem, offs)
+    oo = _empty(npairs + 1, np.int64, mem, offs)
+    ops = _empty(max(cap, 1), np.uint8, mem, offs)
+    ol = _empty(max(npairs, 1), np.int32, mem, offs)
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_align_pairs(_ctx(ctx), ctypes.byref(ss), _ptr(pr), npairs, S.ctypes.data, gap_open,
+                                  gap_extend, _ptr(sc), _ptr(oo), _ptr(ops), cap, _ptr(ol), mem,
+                                  _stream(stream, mem)))
+    return dict(scores=sc[:npairs], ops_offsets=oo, ops=ops, ops_len=ol[:npairs])
+
+
+def columns(out: dict, k: int) -> str:
+    """Columns of pair k of an align_pairs result as a str over M, X, Y."""
+    def h(x):
+        return x.cpu().numpy() if _is_torch(x) else x
+    o, n = int(h(out["ops_offsets"])[k]), int(h(out["ops_len"])[k])
+    return bytes(h(out["ops"])[o:o + n]).decode()
 
 
 def pipeline(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: int, gap_extend: int,

@@ -150,3 +150,52 @@ def test_symmetry_and_self_score(orc):
         y = synth.uniform_residues(rng.randrange(1 << 30), n)
         assert orc.gotoh(x, y, S, -11, -1) == orc.gotoh(y, x, S, -11, -1)
         assert orc.gotoh(x, x, S, -11, -1) == sum(int(S[a, a]) for a in x)
+
+
+# ---- alignments (traceback) -------------------------------------------------------
+
+def test_alignment_scorer_matches_the_enumeration(orc):
+    """The oracle's column scorer agrees with this file's scorer on every alignment of small pairs."""
+    rng = random.Random(11)
+    for _ in range(12):
+        m, n = rng.randint(0, 4), rng.randint(0, 4)
+        x = [rng.randrange(4) for _ in range(m)]
+        y = [rng.randrange(4) for _ in range(n)]
+        S = random_symmetric(rng, 4, -4, 6)
+        go, ge = -rng.randint(0, 6), -rng.randint(0, 3)
+        for cols in all_alignments(m, n):
+            assert orc.alignment_score(x, y, cols, S, go, ge) == score_alignment(cols, x, y, S, go, ge)
+
+
+def test_alignment_scorer_rejects_non_alignments(orc):
+    S = np.eye(4, dtype=np.int8) * 5
+    x, y = [0, 1, 2], [0, 2]
+    assert orc.alignment_score(x, y, "MXM", S, -3, -1) == 5 + (-3 - 1) + 5
+    for bad in ("MM", "MXMY", "MMMX", "MZM", "XXXYY" + "M"):
+        assert orc.alignment_score(x, y, bad, S, -3, -1) is None
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_traceback_is_optimal_and_valid(orc, seed):
+    """The traced alignment consumes both sequences and scores exactly the optimum (brute force for small pairs)."""
+    rng = random.Random(100 + seed)
+    for _ in range(40):
+        m, n = rng.randint(0, 6), rng.randint(0, 6)
+        x = [rng.randrange(5) for _ in range(m)]
+        y = [rng.randrange(5) for _ in range(n)]
+        S = random_symmetric(rng, 5, -4, 8)
+        go, ge = -rng.randint(0, 8), -rng.randint(0, 3)
+        sc, cols = orc.align(x, y, S, go, ge)
+        assert sc == brute_force(x, y, S, go, ge)
+        assert score_alignment(cols, x, y, S, go, ge) == sc
+        assert cols.count("M") + cols.count("X") == m and cols.count("M") + cols.count("Y") == n
+
+
+def test_traceback_long_family_pairs(orc):
+    w = synth.workload(1)
+    res, offs = w.residues, w.offsets
+    for a, b in ((0, 1), (2, 40), (5, 5), (63, 7)):
+        x, y = res[offs[a]:offs[a + 1]], res[offs[b]:offs[b + 1]]
+        sc, cols = orc.align(x, y, w.subst, w.gap_open, w.gap_extend)
+        assert sc == orc.gotoh(x, y, w.subst, w.gap_open, w.gap_extend)
+        assert orc.alignment_score(x, y, cols, w.subst, w.gap_open, w.gap_extend) == sc
