@@ -437,6 +437,7 @@ int64_t orc_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, cons
 int64_t orc_align(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, const int8_t* S, int32_t alphabet,
                   int32_t go, int32_t ge, char* ops, int32_t* len) {
     const GotohTables t = fill_gotoh(x, m, y, n, S, alphabet, go, ge);
+    auto subst = [&](uint8_t a, uint8_t b) { return (int64_t)S[(int64_t)a * alphabet + b]; };
     auto best_of = [&](int64_t i, int64_t j, bool useM, bool useX, bool useY, int64_t want, int64_t add) {
         if (useM && t.M[t.at(i, j)] > NEG_INF && t.M[t.at(i, j)] + add == want) return 'M';
         if (useX && t.X[t.at(i, j)] > NEG_INF && t.X[t.at(i, j)] + add == want) return 'X';
@@ -450,7 +451,7 @@ int64_t orc_align(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n, cons
     while (i > 0 || j > 0) {
         rev.push_back(state);
         if (state == 'M') {
-            const int64_t v = t.M[t.at(i, j)] - S[x[i - 1] * alphabet + y[j - 1]];
+            const int64_t v = t.M[t.at(i, j)] - subst(x[i - 1], y[j - 1]);
             state = best_of(i - 1, j - 1, true, true, true, v, 0);
             i--;
             j--;
