@@ -385,17 +385,63 @@ __device__ void align_pair16(const uint32_t* __restrict__ prof, int32_t m1, int3
     }
 }
 
-// The same alignment with two subject columns per lane step. In step c the
-// lane takes columns j1 = 2c+1 and j2 = 2c+2; sub-step r updates row r to
-// column j1 and row r-1 to column j2 (a skew of one row), so the two column
-// chains F -> H -> H+go+ge are independent and interleave. The instruction
-// count per cell is unchanged; a step hands two (H, F) pairs and two letters
-// to the next lane.
-template <int R>
-__device__ void align_pair16x2(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2,
-                               const uint8_t* __restrict__ y, int32_t n, int32_t nsteps_warp,
-                               const GotohArgs& a, int32_t* __restrict__ bnd, int lane, unsigned gmask,
-                               int32_t* r1, int32_t* r2) {
+// One lane step over C consecutive subject columns j1..j1+C-1 of the lane's R
+// rows (CC <= C of them present): sub-step s moves row s - c to column j1 + c
+// for every chain c, so the C chains F -> H -> H+go+ge are independent and
+// interleave, and every chain finds its left neighbour (chain c - 1, same row)
+// already one sub-step ahead. The instruction count per cell is that of one
+// column; no branch sits inside the unrolled rows.
+template <int R, int CC>
+__device__ __forceinline__ void pair16_columns(const uint32_t* __restrict__ prof, int64_t stride, int64_t chunk,
+                                               uint32_t letters, uint32_t (&H)[R], uint32_t (&Hg)[R],
+                                               uint32_t (&E)[R], const uint32_t* hin, const uint32_t* fin,
+                                               uint32_t hdiag, uint32_t ge2, uint32_t goe2, uint32_t NEG2,
+                                               uint32_t* hout, uint32_t* fout) {
+    uint32_t sc[CC][R];
+#pragma unroll
+    for (int c = 0; c < CC; c++) load_profile32<R>(prof + (int64_t)((letters >> (8 * c)) & 0xffu) * stride + chunk, sc[c]);
+    uint32_t fu[CC], hgu[CC], hd[CC];
+#pragma unroll
+    for (int c = 0; c < CC; c++) {
+        fu[c] = fin[c];
+        hgu[c] = __viaddmax_s16x2(hin[c], goe2, NEG2);
+        hd[c] = c == 0 ? hdiag : hin[c - 1];
+    }
+#pragma unroll
+    for (int s = 0; s < R + CC - 1; s++) {
+#pragma unroll
+        for (int c = CC - 1; c >= 0; c--) {
+            const int r = s - c;
+            if (r < 0 || r >= R) continue;
+            const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
+            const uint32_t f = __viaddmax_s16x2(fu[c], ge2, hgu[c]);
+            const uint32_t t = __viaddmax_s16x2(hd[c], sc[c][r], NEG2);
+            const uint32_t h = __vimax3_s16x2(t, e, f);
+            hd[c] = H[r];
+            H[r] = h;
+            Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
+            E[r] = e;
+            fu[c] = f;
+            hgu[c] = Hg[r];
+            if (r == R - 1) {
+                hout[c] = h;
+                fout[c] = f;
+            }
+        }
+    }
+}
+
+// The alignment of align_pair16 with C subject columns per lane step (one
+// chain per column, see pair16_columns). In step tau lane t takes columns
+// C(tau - t) + 1 .. C(tau - t) + C; the last step of a subject whose length is
+// not a multiple of C takes the remaining columns. A step hands C (H, F) pairs
+// and C letters (one 32-bit word) to the next lane.
+template <int R, int C>
+__device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2,
+                              const uint8_t* __restrict__ y, int32_t n, int32_t nsteps_warp,
+                              const GotohArgs& a, int32_t* __restrict__ bnd, int lane, unsigned gmask,
+                              int32_t* r1, int32_t* r2) {
+    static_assert(C >= 1 && C <= 4, "up to four letters travel in one word");
     const int G = a.G;
     const int32_t go = a.go, ge = a.ge;
     const uint32_t NEG2 = pk2(NEG16, NEG16);
@@ -403,7 +449,7 @@ __device__ void align_pair16x2(const uint32_t* __restrict__ prof, int32_t m1, in
     const int32_t strip_h = G * R;
     const int32_t mrows = max(m1, m2);
     const int32_t strips = (mrows + strip_h - 1) / strip_h;
-    const int32_t npairs = (n + 1) >> 1;
+    const int32_t nchunks = (n + C - 1) / C;
     for (int32_t s = 0; s < strips; s++) {
         const int32_t row0 = s * strip_h + lane * R;
         uint32_t H[R], Hg[R], E[R];
@@ -416,110 +462,77 @@ __device__ void align_pair16x2(const uint32_t* __restrict__ prof, int32_t m1, in
         }
         const int32_t d0 = (row0 == 0) ? 0 : go + row0 * ge;
         uint32_t hdiag = pk2(d0, d0);  // H(row0 - 1, j1 - 1)
-        uint32_t hin1 = 0, fin1 = NEG2, hin2 = 0, fin2 = NEG2, yin = 0, yword = 0;
+        uint32_t hin[C], fin[C], yin = 0;
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            hin[c] = 0;
+            fin[c] = NEG2;
+        }
         const bool last_strip = s == strips - 1;
+        const int64_t chunk = (int64_t)(row0 / R) * rpad<R>();
         for (int32_t tau = 0; tau < nsteps_warp; tau++) {
-            if (lane == 0 && tau < npairs) {
-                // letters y_{2tau+1}, y_{2tau+2} (0-based 2tau, 2tau+1); the padding is zeros
-                if ((tau & 1) == 0) yword = *(const uint32_t*)(y + 2 * tau);
-                yin = (yword >> (16 * (tau & 1))) & 0xffffu;
-                const int32_t j1 = 2 * tau + 1;
-                if (s == 0) {
-                    const int32_t b1 = go + j1 * ge, b2 = b1 + ge;
-                    hin1 = pk2(b1, b1);
-                    hin2 = pk2(b2, b2);
-                    fin1 = NEG2;
-                    fin2 = NEG2;
-                } else {
-                    hin1 = (uint32_t)bnd[2 * j1];
-                    fin1 = (uint32_t)bnd[2 * j1 + 1];
-                    if (j1 < n) {  // column j1 + 1 exists (the buffer holds columns 0..n)
-                        hin2 = (uint32_t)bnd[2 * j1 + 2];
-                        fin2 = (uint32_t)bnd[2 * j1 + 3];
+            if (lane == 0 && tau < nchunks) {
+                // letters y_{C tau + 1 ..}: zero bytes past the subject are padding
+                const uint8_t* yp = y + (int64_t)C * tau;
+                yin = 0;
+#pragma unroll
+                for (int c = 0; c < C; c++) yin |= (uint32_t)yp[c] << (8 * c);
+                const int32_t j1 = C * tau + 1;
+#pragma unroll
+                for (int c = 0; c < C; c++) {
+                    if (s == 0) {
+                        const int32_t b = go + (j1 + c) * ge;
+                        hin[c] = pk2(b, b);
+                        fin[c] = NEG2;
+                    } else if (j1 + c <= n) {  // the buffer holds columns 0..n
+                        hin[c] = (uint32_t)bnd[2 * (j1 + c)];
+                        fin[c] = (uint32_t)bnd[2 * (j1 + c) + 1];
                     }
                 }
             }
-            const int32_t c = tau - lane;
-            const int32_t j1 = 2 * c + 1, j2 = j1 + 1;
-            uint32_t hout1 = hin1, fout1 = fin1, hout2 = hin2, fout2 = fin2;
-            if (c >= 0 && j1 <= n) {
-                const bool two = j2 <= n;
-                const int64_t chunk = (int64_t)(row0 / R) * rpad<R>();
-                uint32_t sc1[R];
-                load_profile32<R>(prof + (int64_t)(yin & 0xffu) * a.prof_stride + chunk, sc1);
-                uint32_t fu1 = fin1, hgu1 = __viaddmax_s16x2(hin1, goe2, NEG2), hd1 = hdiag;
-                if (two) {
-                    // both columns: no branch inside the unrolled rows, so the two
-                    // chains interleave
-                    uint32_t sc2[R];
-                    load_profile32<R>(prof + (int64_t)(yin >> 8) * a.prof_stride + chunk, sc2);
-                    uint32_t fu2 = fin2, hgu2 = __viaddmax_s16x2(hin2, goe2, NEG2), hd2 = hin1;
+            const int32_t cidx = tau - lane;
+            const int32_t j1 = C * cidx + 1;
+            uint32_t hout[C], fout[C];
 #pragma unroll
-                    for (int r = 0; r <= R; r++) {
-                        if (r >= 1) {  // column j2, row r - 1 (its left neighbour is column j1)
-                            const int q = r - 1;
-                            const uint32_t e = __viaddmax_s16x2(E[q], ge2, Hg[q]);
-                            const uint32_t f = __viaddmax_s16x2(fu2, ge2, hgu2);
-                            const uint32_t t = __viaddmax_s16x2(hd2, sc2[q], NEG2);
-                            const uint32_t h = __vimax3_s16x2(t, e, f);
-                            hd2 = H[q];
-                            H[q] = h;
-                            Hg[q] = __viaddmax_s16x2(h, goe2, NEG2);
-                            E[q] = e;
-                            fu2 = f;
-                            hgu2 = Hg[q];
-                        }
-                        if (r < R) {  // column j1, row r
-                            const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
-                            const uint32_t f = __viaddmax_s16x2(fu1, ge2, hgu1);
-                            const uint32_t t = __viaddmax_s16x2(hd1, sc1[r], NEG2);
-                            const uint32_t h = __vimax3_s16x2(t, e, f);
-                            hd1 = H[r];
-                            H[r] = h;
-                            Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
-                            E[r] = e;
-                            fu1 = f;
-                            hgu1 = Hg[r];
-                            if (r == R - 1) {
-                                hout1 = h;
-                                fout1 = f;
-                            }
-                        }
-                    }
-                    hout2 = H[R - 1];
-                    fout2 = fu2;
-                } else {
-                    // the last column of an odd-length subject
-#pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
-                        const uint32_t f = __viaddmax_s16x2(fu1, ge2, hgu1);
-                        const uint32_t t = __viaddmax_s16x2(hd1, sc1[r], NEG2);
-                        const uint32_t h = __vimax3_s16x2(t, e, f);
-                        hd1 = H[r];
-                        H[r] = h;
-                        Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
-                        E[r] = e;
-                        fu1 = f;
-                        hgu1 = Hg[r];
-                    }
-                    hout1 = H[R - 1];
-                    fout1 = fu1;
+            for (int c = 0; c < C; c++) {
+                hout[c] = hin[c];
+                fout[c] = fin[c];
+            }
+            if (cidx >= 0 && j1 <= n) {
+                const int32_t cnt = min(C, n - j1 + 1);
+                if (cnt == C) {
+                    pair16_columns<R, C>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2,
+                                         NEG2, hout, fout);
+                } else if (C > 1 && cnt == 1) {
+                    pair16_columns<R, 1>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2,
+                                         NEG2, hout, fout);
+                } else if (C > 2 && cnt == 2) {
+                    pair16_columns<R, (C > 2 ? 2 : 1)>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag,
+                                                       ge2, goe2, NEG2, hout, fout);
+                } else if (C > 3 && cnt == 3) {
+                    pair16_columns<R, (C > 3 ? 3 : 1)>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag,
+                                                       ge2, goe2, NEG2, hout, fout);
                 }
-                hdiag = hin2;
+                // the last column's value from above is the next step's diagonal
+                // (constant indices keep the arrays in registers)
+#pragma unroll
+                for (int c = 0; c < C; c++)
+                    if (c == cnt - 1) hdiag = hin[c];
                 if (!last_strip && lane == G - 1) {
-                    bnd[2 * j1] = (int32_t)hout1;
-                    bnd[2 * j1 + 1] = (int32_t)fout1;
-                    if (two) {
-                        bnd[2 * j2] = (int32_t)hout2;
-                        bnd[2 * j2 + 1] = (int32_t)fout2;
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        if (c < cnt) {
+                            bnd[2 * (j1 + c)] = (int32_t)hout[c];
+                            bnd[2 * (j1 + c) + 1] = (int32_t)fout[c];
+                        }
                     }
                 }
             }
-            hin1 = __shfl_up_sync(gmask, hout1, 1, G);
-            fin1 = __shfl_up_sync(gmask, fout1, 1, G);
-            hin2 = __shfl_up_sync(gmask, hout2, 1, G);
-            fin2 = __shfl_up_sync(gmask, fout2, 1, G);
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                hin[c] = __shfl_up_sync(gmask, hout[c], 1, G);
+                fin[c] = __shfl_up_sync(gmask, fout[c], 1, G);
+            }
             yin = __shfl_up_sync(gmask, yin, 1, G);
         }
         __syncwarp(gmask);
@@ -610,8 +623,8 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
             if (steps > 0) {
                 const uint8_t* yp = a.res + a.pad_off[have ? ys : x1];
                 const int32_t ny = (have && mrows > 0) ? n : 0;
-                if constexpr (kC == 2)
-                    align_pair16x2<R>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
+                if constexpr (kC > 1)
+                    align_pair16c<R, kC>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
                 else
                     align_pair16<R>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
             }
