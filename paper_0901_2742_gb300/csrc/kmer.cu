@@ -483,6 +483,85 @@ __global__ void k_key_column(int32_t n, const int32_t* __restrict__ ga_ptr,
     }
 }
 
+// Per-sequence tables of the fixed-point terms: nkb = |x_i| - k + 1, q32 =
+// floor(2^32 / nkb), r32 = 2^32 mod nkb, inv = 1/nkb in fp32 (zeros when no
+// k-mer fits), and the block of i (largest b with floor(b n / p) <= i).
+__global__ void k_seq_tables(int32_t n, int32_t k, int32_t p, const int32_t* __restrict__ len,
+                             int32_t* __restrict__ nkb, uint64_t* __restrict__ q32, uint32_t* __restrict__ r32,
+                             float* __restrict__ inv, int32_t* __restrict__ blk) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t nk = len[i] - k + 1;
+    nkb[i] = nk;
+    if (nk >= 1) {
+        q32[i] = (1ull << 32) / (uint64_t)nk;
+        r32[i] = (uint32_t)((1ull << 32) % (uint64_t)nk);
+        inv[i] = 1.0f / (float)nk;
+    } else {
+        q32[i] = 0;
+        r32[i] = 0;
+        inv[i] = 0.0f;
+    }
+    int64_t b = ((int64_t)i * p) / n;
+    while (b + 1 < p && (b + 1) * n / p <= i) b++;
+    while (b > 0 && b * n / p > i) b--;
+    blk[i] = (int32_t)b;
+}
+
+// Prefix offsets (one CTA): exoff of the excess lists (nkb / (T+1) entries per
+// sequence at most) and loff of the sorted k-mer lists (nkb entries). Thread t
+// owns the contiguous segment [t*w, (t+1)*w): it sums its segment, one block
+// scan gives every segment's start, and it writes its segment's offsets.
+__global__ void __launch_bounds__(1024)
+k_seq_offsets(int32_t n, int32_t k, int32_t T, const int32_t* __restrict__ len, int64_t* __restrict__ exoff,
+              int64_t* __restrict__ loff) {
+    __shared__ long long wex[32], wl[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t seg = (n + (int32_t)blockDim.x - 1) / (int32_t)blockDim.x;
+    const int32_t lo = min(n, (int32_t)threadIdx.x * seg), hi = min(n, lo + seg);
+    long long ex = 0, l = 0;
+    for (int32_t i = lo; i < hi; i++) {
+        const int32_t nk = len[i] - k + 1;
+        if (nk > 0) {
+            ex += nk / (T + 1);
+            l += nk;
+        }
+    }
+    // exclusive scan of the segment sums over the block
+    long long iex = ex, il = l;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long a = __shfl_up_sync(0xffffffffu, iex, o), b = __shfl_up_sync(0xffffffffu, il, o);
+        if (lane >= o) {
+            iex += a;
+            il += b;
+        }
+    }
+    if (lane == 31) {
+        wex[w] = iex;
+        wl[w] = il;
+    }
+    __syncthreads();
+    long long bex = 0, bl = 0;
+    for (int q = 0; q < w; q++) {
+        bex += wex[q];
+        bl += wl[q];
+    }
+    long long cex = bex + iex - ex, cl = bl + il - l;  // offsets of my segment's first sequence
+    if (threadIdx.x == 0) {
+        exoff[0] = 0;
+        loff[0] = 0;
+    }
+    for (int32_t i = lo; i < hi; i++) {
+        const int32_t nk = len[i] - k + 1;
+        if (nk > 0) {
+            cex += nk / (T + 1);
+            cl += nk;
+        }
+        exoff[i + 1] = cex;
+        loff[i + 1] = cl;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Globalized rank (Section 2.3.1: every block's sample set goes to all blocks
 // and every sequence is ranked against the s*p samples).
@@ -620,31 +699,15 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         return SAD_OK;
     }
 
-    // per-sequence host tables: nkb, q32, r32, blk, excess-list offsets
-    std::vector<int32_t> nkb(n), blk(n);
-    std::vector<uint64_t> q32(n);
-    std::vector<uint32_t> r32(n);
-    std::vector<float> inv(n);
-    std::vector<int64_t> exoff(n + 1), loff(n + 1);
-    exoff[0] = 0;
-    loff[0] = 0;
+    // per-sequence tables are computed on the device from the lengths; the host
+    // keeps only the totals that size the excess and list workspaces
+    int64_t ex_total = 0, list_total = 0;
     for (int32_t i = 0; i < n; i++) {
-        nkb[i] = S.h_len[i] - k + 1;
-        if (nkb[i] >= 1) {
-            q32[i] = (1ull << 32) / (uint64_t)nkb[i];
-            r32[i] = (uint32_t)((1ull << 32) % (uint64_t)nkb[i]);
-            inv[i] = 1.0f / (float)nkb[i];
-        } else {
-            q32[i] = 0;
-            r32[i] = 0;
-            inv[i] = 0.0f;
+        const int64_t nk = (int64_t)S.h_len[i] - k + 1;
+        if (nk > 0) {
+            ex_total += nk / (T + 1);
+            list_total += nk;
         }
-        exoff[i + 1] = exoff[i] + (nkb[i] > 0 ? nkb[i] / (T + 1) : 0);
-        loff[i + 1] = loff[i] + std::max(nkb[i], 0);
-    }
-    for (int32_t b = 0; b < p; b++) {
-        const int64_t lo = (int64_t)b * n / p, hi = (int64_t)(b + 1) * n / p;
-        for (int64_t i = lo; i < hi; i++) blk[i] = b;
     }
     // device layout of the misc slot
     size_t off = 0;
@@ -658,21 +721,18 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
                  o_loff = carve(8ull * (n + 1)), o_nex = carve(4ull * n), o_nd = carve(4ull * n),
                  o_sT = carve(4ull * n), o_hidx = carve(4ull * n), o_hlist = carve(4ull * n),
                  o_H = carve(16), o_gsum = carve(8ull * p);
-    const size_t host_bytes = o_nex;  // the host-filled prefix
     void* misc = nullptr;
     SAD_RET(workspace(ctx, WS_KMER_MISC, off, stream, &misc));
-    void* pin = nullptr;
-    SAD_RET(pinned(ctx, host_bytes, stream, &pin));
-    SAD_CUDA(cudaStreamSynchronize(stream));
-    char* hp = (char*)pin;
-    memcpy(hp + o_nkb, nkb.data(), 4ull * n);
-    memcpy(hp + o_blk, blk.data(), 4ull * n);
-    memcpy(hp + o_q, q32.data(), 8ull * n);
-    memcpy(hp + o_r, r32.data(), 4ull * n);
-    memcpy(hp + o_inv, inv.data(), 4ull * n);
-    memcpy(hp + o_exoff, exoff.data(), 8ull * (n + 1));
-    memcpy(hp + o_loff, loff.data(), 8ull * (n + 1));
-    SAD_CUDA(cudaMemcpyAsync(misc, pin, host_bytes, cudaMemcpyHostToDevice, stream));
+    {
+        char* d = (char*)misc;
+        TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
+        k_seq_tables<<<(n + 255) / 256, 256, 0, stream>>>(n, k, p, S.len, (int32_t*)(d + o_nkb),
+                                                          (uint64_t*)(d + o_q), (uint32_t*)(d + o_r),
+                                                          (float*)(d + o_inv), (int32_t*)(d + o_blk));
+        SAD_LAUNCHED();
+        k_seq_offsets<<<1, 1024, 0, stream>>>(n, k, T, S.len, (int64_t*)(d + o_exoff), (int64_t*)(d + o_loff));
+        SAD_LAUNCHED();
+    }
     char* dm = (char*)misc;
     SeqTables tab;
     tab.nkb = (const int32_t*)(dm + o_nkb);
@@ -693,7 +753,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     // counts (+ planes), or the sorted (code, count) lists
     void* c8 = nullptr;
     const int64_t nrows = round_up(n, 128);
-    SAD_RET(workspace(ctx, WS_COUNTS, sparse ? (size_t)(8 * std::max<int64_t>(loff[n], 1)) : (size_t)(nrows * Vs),
+    SAD_RET(workspace(ctx, WS_COUNTS, sparse ? (size_t)(8 * std::max<int64_t>(list_total, 1)) : (size_t)(nrows * Vs),
                       stream, &c8));
     SparseLists L{(const uint2*)c8, (const int64_t*)(dm + o_loff), (const int32_t*)(dm + o_nd)};
     uint8_t* planes = nullptr;
@@ -707,7 +767,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
                                      (size_t)((nrows - n) * (int64_t)cap * Vs), stream));
     }
     void* exb = nullptr;
-    const int64_t excap = exoff[n] > 0 ? exoff[n] : 1;
+    const int64_t excap = ex_total > 0 ? ex_total : 1;
     SAD_RET(workspace(ctx, WS_EXCESS, (size_t)(8 * excap), stream, &exb));
     int32_t* ex_tau = (int32_t*)exb;
     int32_t* ex_val = ex_tau + excap;

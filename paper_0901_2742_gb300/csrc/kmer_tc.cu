@@ -141,12 +141,15 @@ __device__ __forceinline__ uint64_t transpose_reduce32(uint64_t (&x)[32]) {
 }
 
 // Per-column table entry of one tile, staged in shared memory by the epilogue
-// warps; all lanes read the same entry (broadcast), two 16-byte loads.
+// warps; all lanes read the same entry (broadcast), one 16-byte load. With
+// b = nk of the sequence: 2^32 = q b + r, and rf = r / b in fp32. For b = 1
+// the pair (q, r) = (2^32 - 1, 1) keeps the same formula exact; for b <= 0 (no
+// k-mer fits, so every numerator of the row is 0) q = r = rf = 0.
 struct __align__(16) ColRec {
     int32_t nkb;
-    uint32_t q32;  // floor(2^32 / nkb) for nkb >= 2 (nkb = 1 is handled apart)
+    uint32_t q32;
     uint32_t r32;
-    float inv;
+    float rf;
 };
 
 // Less frequently needed per-column fields: block (local D) and excess index.
@@ -155,21 +158,88 @@ struct __align__(8) ColAux {
     int32_t hidx;
 };
 
-// floor(a 2^32 / b), b = min(nk_i, nk_j) < 2^16, from 32-bit per-sequence tables
-// (see fixed_term_fast); b = 1 gives a << 32, b <= 0 gives 0.
-__device__ __forceinline__ uint64_t fixed_term32(uint32_t a, int32_t nki, uint32_t qi, uint32_t ri, float invi,
-                                                 const ColRec& c) {
-    const bool take_i = nki <= c.nkb;
-    const int32_t b = take_i ? nki : c.nkb;
-    const uint32_t q = take_i ? qi : c.q32;
-    const uint32_t r = take_i ? ri : c.r32;
-    const float inv = take_i ? invi : c.inv;
+__device__ __forceinline__ ColRec col_rec(const SeqTables& tab, int32_t j, int32_t n) {
+    ColRec r{0, 0u, 0u, 0.f};
+    if (j < n) {
+        const int32_t nk = tab.nkb[j];
+        r.nkb = nk;
+        if (nk >= 2) {
+            r.q32 = (uint32_t)tab.q32[j];  // < 2^31
+            r.r32 = tab.r32[j];
+            r.rf = (float)r.r32 * tab.inv[j];
+        } else if (nk == 1) {
+            r.q32 = 0xffffffffu;
+            r.r32 = 1u;
+            r.rf = 1.0f;
+        }
+    }
+    return r;
+}
+
+constexpr float kTwo23 = 8388608.0f;     // 2^23: a float in [2^23, 2^24) has unit spacing
+constexpr uint32_t kTwo23Bits = 0x4B000000u;
+
+// floor(a 2^32 / b) for b = min(nk_i, nk_j) < 2^16 and 0 <= a <= b (af = a as
+// a float): a 2^32 / b = a q + a r / b, and floor(a r / b) < 2^16 is estimated
+// as a * rf rounded to the nearest integer (the estimate is off by far less
+// than one half), then corrected by one comparison each way. The rounding and
+// the float-to-integer move are one fused multiply-add with 2^23 and one
+// integer subtraction, exact below 2^23, so no conversion instruction is used.
+__device__ __forceinline__ uint64_t fixed_term_tc(uint32_t a, float af, const ColRec& ri, const ColRec& c) {
+    const bool take_i = ri.nkb <= c.nkb;
+    const int32_t b = max(take_i ? ri.nkb : c.nkb, 1);
+    const uint32_t q = take_i ? ri.q32 : c.q32;
+    const uint32_t r = take_i ? ri.r32 : c.r32;
+    const float rf = take_i ? ri.rf : c.rf;
     const uint32_t x = a * r;
-    uint32_t qq = __float2uint_rz(__uint2float_rn(x) * inv);
+    uint32_t qq = __float_as_uint(fmaf(af, rf, kTwo23)) - kTwo23Bits;
     const int32_t rem = (int32_t)(x - qq * (uint32_t)b);  // |rem| < 2b < 2^17
     qq = rem < 0 ? qq - 1 : (rem >= b ? qq + 1 : qq);
-    const uint64_t t = (uint64_t)a * q + qq;
-    return b <= 0 ? 0ull : (b == 1 ? ((uint64_t)a << 32) : t);
+    return (uint64_t)a * q + qq;
+}
+
+// One 32-column chunk of the accumulator for this thread's row i: the exact
+// numerators and their fixed-point terms; *sum collects the row sum, cw[u] the
+// value that column u contributes to the column reduction. kFull: every pair
+// of the tile is valid and off the diagonal (i < j < n). kLoc: only pairs of
+// the same block count (the local D sum); tiles without such pairs never run
+// this pass, so the all-pairs pass keeps a single 32-entry array live.
+template <bool kFull, bool kLoc>
+__device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], int col0, int32_t i, int32_t j0, int32_t n,
+                                          bool oki, const ColRec& rowr, int32_t bli, int32_t hxi,
+                                          const ColRec* __restrict__ ct, const ColAux* __restrict__ cx,
+                                          const SeqTables& tab, int32_t* __restrict__ A, uint64_t& sum,
+                                          uint64_t (&cw)[32]) {
+#pragma unroll
+    for (int u = 0; u < 32; u++) {
+        const int col = col0 + u;
+        const int32_t j = j0 + col;
+        const ColRec c = ct[col];
+        float af = __uint_as_float(v[u]);  // an integer below 2^16, exact in fp32
+        uint32_t av = __float_as_uint(af + kTwo23) - kTwo23Bits;
+        if (hxi >= 0) {
+            const int32_t hj = cx[col].hidx;
+            if (hj >= 0) {
+                av += (uint32_t)tab.R[(int64_t)hxi * tab.H + hj];
+                af = __uint_as_float(av | kTwo23Bits) - kTwo23;
+            }
+        }
+        uint64_t tv = fixed_term_tc(av, af, rowr, c);
+        bool off_diag = true;
+        if (!kFull) {
+            const bool use = oki && j < n && i <= j;
+            tv = use ? tv : 0;
+            off_diag = i != j;  // the diagonal counts once, for its own row
+        }
+        if (kLoc) {
+            tv = bli == cx[col].blk ? tv : 0;
+        } else if (A && (kFull || (oki && j < n && i <= j))) {
+            A[(int64_t)i * n + j] = (int32_t)av;
+            if (i != j) A[(int64_t)j * n + i] = (int32_t)av;
+        }
+        sum += tv;
+        cw[u] = off_diag ? tv : 0;
+    }
 }
 
 constexpr int kEpiWarps = 8;                       // two per TMEM lane quadrant
@@ -330,24 +400,12 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (epi_stop) break;
             for (int c = et; c < BN; c += 256) {
                 const int32_t j = j0 + c;
-                ColRec r;
-                ColAux x;
+                ct[c] = col_rec(tab, j, n);
+                ColAux x{-1, -1};
                 if (j < n) {
-                    r.nkb = tab.nkb[j];
-                    r.q32 = (uint32_t)tab.q32[j];  // < 2^31 for nkb >= 2
-                    r.r32 = tab.r32[j];
-                    r.inv = tab.inv[j];
                     x.blk = tab.blk[j];
                     x.hidx = tab.hidx[j];
-                } else {
-                    r.nkb = 0;
-                    r.q32 = 0;
-                    r.r32 = 0;
-                    r.inv = 0.f;
-                    x.blk = -1;
-                    x.hidx = -1;
                 }
-                ct[c] = r;
                 cx[c] = x;
             }
             if (et == 0) {
@@ -365,46 +423,36 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const bool valid = ok_wait && !aborted();
             const int32_t i = i0 + 32 * q + lane;
             const bool oki = valid && i < n;
-            const int32_t nki = oki ? tab.nkb[i] : 0;
-            const uint32_t qi = oki ? (uint32_t)tab.q32[i] : 0;
-            const uint32_t ri = oki ? tab.r32[i] : 0;
-            const float invi = oki ? tab.inv[i] : 0.f;
+            const ColRec rowr = col_rec(tab, oki ? i : n, n);
             const int32_t bli = oki ? tab.blk[i] : -2;
             const int32_t hxi = oki ? tab.hidx[i] : -1;
+            // every pair valid and off the diagonal: the tile lies right of the
+            // diagonal and inside n (uniform over the CTA)
+            const bool full = i0 + kTM <= j0 && j0 + BN <= n;
             uint64_t rs_c = 0, rs_l = 0;
 #pragma unroll 1
             for (int cc0 = 0; cc0 < kChunks; cc0++) {
                 const int c = h * kChunks + cc0;
                 uint32_t v[32];
                 tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
-                uint64_t cc[32], cl[32];
-#pragma unroll
-                for (int u = 0; u < 32; u++) {
-                    const int col = 32 * c + u;
-                    const int32_t j = j0 + col;
-                    const ColRec r = ct[col];
-                    const bool use = oki && j < n && i <= j;
-                    uint32_t av = (uint32_t)__uint_as_float(v[u]);
-                    if (hxi >= 0) {
-                        const int32_t hj = cx[col].hidx;
-                        if (hj >= 0) av += (uint32_t)tab.R[(int64_t)hxi * tab.H + hj];
-                    }
-                    uint64_t tv = fixed_term32(av, nki, qi, ri, invi, r);
-                    tv = use ? tv : 0;
-                    const uint64_t tl = (any_loc && bli == cx[col].blk) ? tv : 0;
-                    if (A && use) {
-                        A[(int64_t)i * n + j] = (int32_t)av;
-                        if (i != j) A[(int64_t)j * n + i] = (int32_t)av;
-                    }
-                    rs_c += tv;
-                    rs_l += tl;
-                    const bool off_diag = i != j;  // the diagonal counts once, for its own row
-                    cc[u] = off_diag ? tv : 0;
-                    cl[u] = off_diag ? tl : 0;
-                }
+                uint64_t cw[32];
+                if (full)
+                    epi_chunk<true, false>(v, 32 * c, i, j0, n, oki, rowr, bli, hxi, ct, cx, tab, A, rs_c, cw);
+                else
+                    epi_chunk<false, false>(v, 32 * c, i, j0, n, oki, rowr, bli, hxi, ct, cx, tab, A, rs_c, cw);
                 // lane l now sums column 32c + l over this warp's 32 rows
-                colw_c[q][32 * c + lane] = transpose_reduce32(cc);
-                colw_l[q][32 * c + lane] = any_loc ? transpose_reduce32(cl) : 0ull;
+                colw_c[q][32 * c + lane] = transpose_reduce32(cw);
+                if (any_loc) {
+                    // the local sums: a second pass over the same accumulator columns
+                    tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
+                    if (full)
+                        epi_chunk<true, true>(v, 32 * c, i, j0, n, oki, rowr, bli, hxi, ct, cx, tab, A, rs_l, cw);
+                    else
+                        epi_chunk<false, true>(v, 32 * c, i, j0, n, oki, rowr, bli, hxi, ct, cx, tab, A, rs_l, cw);
+                    colw_l[q][32 * c + lane] = transpose_reduce32(cw);
+                } else {
+                    colw_l[q][32 * c + lane] = 0ull;
+                }
             }
             // the accumulator is read: hand it back to the MMA warp
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
