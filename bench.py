@@ -40,6 +40,33 @@ SM_MAX_MHZ = 2070.0
 INT_OPS_PER_CLK_SM = 64   # measured: IADD3, VIADDMNMX, VIMNMX3 (32-bit and 16x2) each 64/clk/SM
 
 
+def plane_gemm_flops(n, k, kmer_alphabet, cap, num_sms=SMS):
+    """Tensor-core work of one all-pairs launch on the threshold planes: 2 K flops
+    per pair of every 128 x BN tile the kernel computes (the upper-triangle tiles;
+    BN = 256 when there are at least as many such tiles as SMs, else 128), with
+    K = cap * (kmer_alphabet^k rounded up to 64)."""
+    if cap <= 0 or n == 0:
+        return 0.0
+    V = kmer_alphabet ** k
+    K = cap * (-(-V // 64) * 64)
+    nti = -(-n // 128)
+
+    def tiles(bn):
+        ntj = -(-n // bn)
+        return sum(1 for ti in range(nti) for tj in range(ntj) if bn * tj + bn - 1 >= 128 * ti)
+
+    bn = 256 if tiles(256) >= num_sms else 128
+    return 2.0 * K * 128 * bn * tiles(bn)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
 def workload_cells(lengths, bucket_offsets, order):
     L = np.asarray(lengths, dtype=np.int64)
     bo, od = np.asarray(bucket_offsets), np.asarray(order)
@@ -352,6 +379,23 @@ def main():
     achieved = ops_per_cell * cells / (sc_ms / args.steps * 1e-3) / 1e12
     peak = SMS * INT_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
 
+    # the k-mer all-pairs launch against the tensor-core peak (fp8: 2 x the measured bf16 burst)
+    kmer_roofline = None
+    flops = plane_gemm_flops(n, w.k, w.kmer_alphabet, w.cap)
+    ap_ms = trace["allpairs"][0] / max(trace["allpairs"][1], 1)
+    peaks = measured_peaks()
+    if flops > 0 and ap_ms > 0:
+        bf16 = peaks["bf16_tflops"] if peaks else 1900.0
+        peak_fp8 = 2.0 * bf16
+        ach = flops / (ap_ms * 1e-3) / 1e12
+        kmer_roofline = {"bound": "tensor", "achieved": ach, "peak": peak_fp8, "unit": "TFLOP/s (fp8 e4m3)",
+                         "frac": ach / peak_fp8, "traffic": None,
+                         "kernel": "k_plane_gemm2 (threshold-plane GEMM, tcgen05 kind::f8f6f4, fused D sums)",
+                         "kernel_ms": ap_ms, "flops_per_launch": flops,
+                         "peak_basis": ("2 x measured bf16 dense burst " + ("(MEASURED_PEAKS.json, of measured)"
+                                        if peaks else "(fallback 1.9 PFLOP/s, of fallback)")),
+                         "pairs_per_s": n * (n + 1) / 2 / (ap_ms * 1e-3)}
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -425,6 +469,7 @@ def main():
                      "peak_gcups": peak * 1e12 / ops_per_cell / 1e9,
                      "peak_basis": f"{SMS} SMs x {INT_OPS_PER_CLK_SM} int ops/clk x {SM_MAX_MHZ:.0f} MHz; "
                                    f"{ops_per_cell:g} instructions per cell"},
+        "kmer_roofline": kmer_roofline,
         "gpu_launches": int(launches),
         "wall_s": wall,
         "clocks": clocks,

@@ -32,6 +32,7 @@ namespace sad {
 namespace {
 
 constexpr int32_t NEG = -(1 << 30);
+constexpr int32_t kChunkSubjects = 64;  // subjects per packed work item (at most)
 
 // everything a Gotoh kernel needs besides its work items
 struct GotohArgs {
@@ -431,6 +432,26 @@ __device__ __forceinline__ void pair16_columns(const uint32_t* __restrict__ prof
     }
 }
 
+// pair16_columns for the cnt <= C columns present (the last chunk of a subject).
+template <int R, int C>
+__device__ __forceinline__ void pair16_chunk(int32_t cnt, const uint32_t* __restrict__ prof, int64_t stride,
+                                             int64_t chunk, uint32_t letters, uint32_t (&H)[R], uint32_t (&Hg)[R],
+                                             uint32_t (&E)[R], const uint32_t* hin, const uint32_t* fin,
+                                             uint32_t hdiag, uint32_t ge2, uint32_t goe2, uint32_t NEG2,
+                                             uint32_t* hout, uint32_t* fout) {
+    if (cnt == C) {
+        pair16_columns<R, C>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2, hout, fout);
+    } else if (C > 1 && cnt == 1) {
+        pair16_columns<R, 1>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2, hout, fout);
+    } else if (C > 2 && cnt == 2) {
+        pair16_columns<R, (C > 2 ? 2 : 1)>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
+                                           hout, fout);
+    } else if (C > 3 && cnt == 3) {
+        pair16_columns<R, (C > 3 ? 3 : 1)>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
+                                           hout, fout);
+    }
+}
+
 // The alignment of align_pair16 with C subject columns per lane step (one
 // chain per column, see pair16_columns). In step tau lane t takes columns
 // C(tau - t) + 1 .. C(tau - t) + C; the last step of a subject whose length is
@@ -500,19 +521,8 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
             }
             if (cidx >= 0 && j1 <= n) {
                 const int32_t cnt = min(C, n - j1 + 1);
-                if (cnt == C) {
-                    pair16_columns<R, C>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2,
-                                         NEG2, hout, fout);
-                } else if (C > 1 && cnt == 1) {
-                    pair16_columns<R, 1>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2,
-                                         NEG2, hout, fout);
-                } else if (C > 2 && cnt == 2) {
-                    pair16_columns<R, (C > 2 ? 2 : 1)>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag,
-                                                       ge2, goe2, NEG2, hout, fout);
-                } else if (C > 3 && cnt == 3) {
-                    pair16_columns<R, (C > 3 ? 3 : 1)>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag,
-                                                       ge2, goe2, NEG2, hout, fout);
-                }
+                pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
+                                   hout, fout);
                 // the last column's value from above is the next step's diagonal
                 // (constant indices keep the arrays in registers)
 #pragma unroll
@@ -553,6 +563,153 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
     }
 }
 
+// The query pair against every subject of one group (bucket positions vfirst,
+// vfirst + vstep, ... below vend, in length order) in a single wavefront: the
+// subjects' columns follow each other in chunks of up to C columns that never
+// span two subjects, and every lane walks the same chunk sequence one step
+// behind the lane above, so the wavefront fills and drains once per group
+// instead of once per subject. A lane resets its rows to column 0 when it
+// enters a subject; the lane that holds a query's last row writes that query's
+// score when it finishes the subject's last column. Only for query pairs within
+// one strip (1 <= max(m1, m2) <= G R); pairs with an empty query or subject are
+// scored beforehand by lane 0.
+// The group's non-empty subjects go to shared memory first (slots g, g + NG,
+// ... of subj_pos / subj_off), so that moving to the next subject inside the
+// wavefront loop is an index step and one shared load.
+template <int R, int C>
+__device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2, int32_t u1, int32_t u2,
+                              int32_t b, int32_t boff, int32_t nb, int32_t vfirst, int32_t vend, int32_t vstep,
+                              int2* __restrict__ subj_pos, long long* __restrict__ subj_off, const GotohArgs& a,
+                              int lane, unsigned gmask) {
+    const int G = a.G;
+    const int32_t go = a.go, ge = a.ge;
+    const uint32_t NEG2 = pk2(NEG16, NEG16);
+    const uint32_t ge2 = pk2(ge, ge), goe2 = pk2(go + ge, go + ge);
+    int32_t* scores = a.scores + a.score_off[b];
+    auto subject = [&](int32_t v, int32_t* uv, int32_t* ys) {
+        *uv = a.srt[boff + v];
+        *ys = a.order[boff + *uv];
+        return a.len[*ys];
+    };
+    // empty queries or subjects are scored here; the rest are listed in order
+    int32_t nchunks = 0, nsubj = 0;
+    for (int32_t v = vfirst; v < vend; v += vstep) {
+        int32_t uv, ys;
+        const int32_t n = subject(v, &uv, &ys);
+        nchunks += (n + C - 1) / C;
+        if (n > 0) {
+            if (lane == 0) {
+                subj_pos[nsubj * vstep] = make_int2(uv, n);
+                subj_off[nsubj * vstep] = a.pad_off[ys];
+            }
+            nsubj++;
+        }
+        if (lane == 0) {
+            const int32_t mq[2] = {m1, m2}, uq[2] = {u1, u2};
+#pragma unroll
+            for (int q = 0; q < 2; q++) {
+                if (uq[q] < 0 || (mq[q] > 0 && n > 0)) continue;
+                const int32_t sc = (mq[q] == 0 && n == 0) ? 0 : go + (mq[q] + n) * ge;
+                scores[tri_pos(min(uq[q], uv), max(uq[q], uv), nb)] = sc;
+            }
+        }
+    }
+    __syncwarp(gmask);
+    if (max(m1, m2) == 0) return;  // every score was written above (uniform over the CTA)
+    const int32_t steps = __reduce_max_sync(0xffffffffu, nchunks > 0 ? nchunks + G - 1 : 0);
+    if (steps == 0) return;
+    // this lane's cursor: subject ordinal k, its length, CSR position, residues, next column
+    int32_t ck = -1, cn = 0, cuv = 0, cj = 1;
+    const uint8_t* cy = nullptr;
+    auto advance = [&]() {
+        ck++;
+        if (ck < nsubj) {
+            const int2 e = subj_pos[ck * vstep];
+            cuv = e.x;
+            cn = e.y;
+            cy = a.res + subj_off[ck * vstep];
+        }
+        cj = 1;
+    };
+    advance();
+    const int32_t row0 = lane * R;
+    const int64_t chunk = (int64_t)lane * rpad<R>();
+    const int own1 = m1 >= 1 ? (m1 - 1) / R : -1, sel1 = m1 >= 1 ? (m1 - 1) % R : 0;
+    const int own2 = (u2 >= 0 && m2 >= 1) ? (m2 - 1) / R : -1, sel2 = m2 >= 1 ? (m2 - 1) % R : 0;
+    uint32_t H[R], Hg[R], E[R];
+    uint32_t hdiag = 0;
+    uint32_t hin[C], fin[C], yin = 0;
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        hin[c] = 0;
+        fin[c] = NEG2;
+    }
+    for (int32_t tau = 0; tau < steps; tau++) {
+        const bool live = tau >= lane && ck < nsubj;
+        if (lane == 0 && live) {
+            yin = 0;
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                yin |= (uint32_t)cy[cj - 1 + c] << (8 * c);  // bytes past the subject are zero padding
+                const int32_t bnd0 = go + (cj + c) * ge;
+                hin[c] = pk2(bnd0, bnd0);
+                fin[c] = NEG2;
+            }
+        }
+        uint32_t hout[C], fout[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            hout[c] = hin[c];
+            fout[c] = fin[c];
+        }
+        if (live) {
+            if (cj == 1) {  // entering a subject: column 0 of my rows
+                // recomputed here on purpose: hoisting these 2R loop-invariant values
+                // out of the loop would hold them in registers for the whole stream
+                int32_t base;
+                asm volatile("mov.b32 %0, %1;" : "=r"(base) : "r"(go + row0 * ge));
+                const uint32_t ge1 = pk2(ge, ge);
+                uint32_t h = pk2(base, base);
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    h = __viaddmax_s16x2(h, ge1, NEG2);  // go + (row0 + r + 1) ge
+                    H[r] = h;
+                    Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
+                    E[r] = NEG2;
+                }
+                hdiag = row0 == 0 ? 0u : pk2(base, base);
+            }
+            const int32_t cnt = min(C, cn - cj + 1);
+            pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
+                               hout, fout);
+#pragma unroll
+            for (int c = 0; c < C; c++)
+                if (c == cnt - 1) hdiag = hin[c];
+            if (cj + cnt - 1 == cn) {  // the subject's last column
+                if (lane == own1 || lane == own2) {
+                    uint32_t v1 = 0, v2 = 0;
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        v1 = (r == sel1) ? H[r] : v1;
+                        v2 = (r == sel2) ? H[r] : v2;
+                    }
+                    if (lane == own1) scores[tri_pos(min(u1, cuv), max(u1, cuv), nb)] = lo16(v1);
+                    if (lane == own2) scores[tri_pos(min(u2, cuv), max(u2, cuv), nb)] = hi16(v2);
+                }
+                advance();
+            } else {
+                cj += cnt;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            hin[c] = __shfl_up_sync(gmask, hout[c], 1, G);
+            fin[c] = __shfl_up_sync(gmask, fout[c], 1, G);
+        }
+        yin = __shfl_up_sync(gmask, yin, 1, G);
+    }
+}
+
 // Columns per lane step of the packed kernel for R rows per lane.
 template <int R>
 __host__ __device__ constexpr int pair_cols() {
@@ -561,12 +718,18 @@ __host__ __device__ constexpr int pair_cols() {
 
 // Work item (bucket, query pair qp, subjects [v0, v1)): queries are the
 // members at length-order positions 2qp and 2qp+1 of the bucket.
-template <int R>
+// kStream: every query pair of the launch lies within one strip, and each
+// group streams its subjects through one wavefront (stream_pair16); otherwise
+// one wavefront per subject, in strips (the two forms are separate kernels: in
+// one body their register needs add up).
+template <int R, bool kStream>
 __global__ void __launch_bounds__(128, (R <= 20) ? 4 : ((R <= 24) ? 3 : 2))
 k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __restrict__ head,
                GotohArgs a) {
     extern __shared__ __align__(16) uint32_t prof32[];
     __shared__ int32_t item_sh;
+    __shared__ int2 subj_pos[kChunkSubjects];       // streamed subjects: (CSR position, length)
+    __shared__ long long subj_off[kChunkSubjects];  // and their padded residue offsets
     const int G = a.G;
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G;
@@ -605,6 +768,13 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
         }
         __syncthreads();
         const int32_t mrows = max(m1, m2);
+        if constexpr (kStream) {
+            // one wavefront over all of the group's subjects (1 <= mrows <= G R is
+            // guaranteed by the host; mrows = 0 scores every pair in the pre-pass)
+            stream_pair16<R, pair_cols<R>()>(prof32, m1, m2, u1, u2, b, boff, nb, it.v0 + g, it.v1, NG,
+                                             subj_pos + g, subj_off + g, a, lane, gmask);
+            continue;
+        }
         const int32_t nsub = it.v1 - it.v0;
         const int32_t rounds = (nsub + NG - 1) / NG;
         for (int32_t rd = 0; rd < rounds; rd++) {
@@ -646,14 +816,14 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
     }
 }
 
-KernelFn pair16_kernel_for(int R) {
+KernelFn pair16_kernel_for(int R, bool stream) {
     switch (R) {
-        case 8: return k_gotoh_pair16<8>;
-        case 12: return k_gotoh_pair16<12>;
-        case 16: return k_gotoh_pair16<16>;
-        case 20: return k_gotoh_pair16<20>;
-        case 24: return k_gotoh_pair16<24>;
-        case 32: return k_gotoh_pair16<32>;
+        case 8: return stream ? k_gotoh_pair16<8, true> : k_gotoh_pair16<8, false>;
+        case 12: return stream ? k_gotoh_pair16<12, true> : k_gotoh_pair16<12, false>;
+        case 16: return stream ? k_gotoh_pair16<16, true> : k_gotoh_pair16<16, false>;
+        case 20: return stream ? k_gotoh_pair16<20, true> : k_gotoh_pair16<20, false>;
+        case 24: return stream ? k_gotoh_pair16<24, true> : k_gotoh_pair16<24, false>;
+        case 32: return stream ? k_gotoh_pair16<32, true> : k_gotoh_pair16<32, false>;
         default: return nullptr;
     }
 }
@@ -737,7 +907,6 @@ constexpr int kPackedR[] = {8, 12, 16, 20, 24, 32};
 constexpr int kPackedG[] = {8, 16, 32};
 constexpr int kNumR = 6, kNumG = 3, kNumVariants = kNumR * kNumG;
 constexpr int kPackedThreads = 128;
-constexpr int32_t kChunkSubjects = 64;
 
 // Every value of the packed DP must stay inside (NEG16, 2^15): scores are at
 // most max(s, 0) * min(m, n) and at least the all-gap path 2 go + (i + j) ge
@@ -901,6 +1070,7 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         size_t smem = 0;
         int64_t scratch_off = 0;
         bool strips = false;
+        bool stream = false;
         int32_t prof_stride = 0;
     } shp[kNumVariants];
     const int64_t stride = 2 * ((int64_t)S.max_len + 1 + 4);
@@ -914,13 +1084,18 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         shp[v].smem = (size_t)S.alphabet * shp[v].prof_stride * 4;
         SAD_CHECK(shp[v].smem <= ctx->smem_optin, SAD_EINVAL,
                   "packed query profile of %zu bytes exceeds shared memory", shp[v].smem);
-        KernelFn fn = pair16_kernel_for(R);
+        // every query pair within one strip and 32 lanes per subject: the streaming
+        // kernel (its single fill and drain saves most where one wavefront per
+        // subject costs 31 idle steps; with 8 or 16 lanes per subject the per-step
+        // bookkeeping of the stream measured as large as the fill it saves)
+        shp[v].strips = rows_var[v] > strip_h;
+        shp[v].stream = !shp[v].strips && G == 32;
+        KernelFn fn = pair16_kernel_for(R, shp[v].stream);
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
         int occ = 0;
         SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPackedThreads, shp[v].smem));
         occ = std::max(occ, 1);
         shp[v].grid = std::min<int64_t>(nv, (int64_t)ctx->num_sms * occ);
-        shp[v].strips = rows_var[v] > strip_h;
         if (shp[v].strips) {
             shp[v].scratch_off = scratch_ints;
             scratch_ints += (int64_t)shp[v].grid * (kPackedThreads / G) * stride;
@@ -960,7 +1135,7 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         L.args.G = G;
         L.args.prof_stride = shp[v].prof_stride;
         L.args.scratch = shp[v].strips ? scratch + shp[v].scratch_off : nullptr;
-        L.fn = pair16_kernel_for(R);
+        L.fn = pair16_kernel_for(R, shp[v].stream);
         L.grid = shp[v].grid;
         L.block = kPackedThreads;
         L.smem = shp[v].smem;

@@ -15,9 +15,10 @@
 // streams 128-byte k-blocks of the row panels with TMA (128B swizzle) into a
 // ring of shared-memory stages; one thread of warp 1 issues
 // tcgen05.mma.kind::f8f6f4 (M = 128, N = BN, K = 32 per instruction) into one
-// of two TMEM accumulators and releases stages with tcgen05.commit; warps 2-9
-// read the other accumulator with tcgen05.ld and reduce the fixed-point D
-// terms while the next tile's MMAs run. Every wait is bounded in time; on
+// of two TMEM accumulators and releases stages with tcgen05.commit; the
+// epilogue warps (kEpiParts per TMEM lane quadrant) read the other accumulator
+// with tcgen05.ld and reduce the fixed-point D terms while the next tile's
+// MMAs run. Every wait is bounded in time; on
 // expiry the kernel sets a status bit, waits (bounded) for its own copies,
 // frees its tensor memory and returns.
 #include <cuda.h>
@@ -242,14 +243,16 @@ __device__ __forceinline__ void epi_chunk(const uint32_t (&v)[32], int col0, int
     }
 }
 
-constexpr int kEpiWarps = 8;                       // two per TMEM lane quadrant
+constexpr int kEpiParts = 3;                        // epilogue warps per TMEM lane quadrant
+constexpr int kEpiWarps = 4 * kEpiParts;
+constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kGemmThreads = (2 + kEpiWarps) * 32;  // producer, MMA issuer, epilogue
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 template <int BN>
 __host__ __device__ constexpr int kStagesFor() {
@@ -274,9 +277,9 @@ __device__ __forceinline__ void mma_f8n(uint32_t d_tmem, uint64_t a, uint64_t b,
 // Persistent all-pairs plane GEMM. Warp 0 streams the k-blocks of every tile
 // of this CTA with TMA; warp 1 (one thread) issues the MMAs into one of two
 // TMEM accumulators (BN columns each) and hands finished accumulators to the
-// epilogue; warps 2-9 read an accumulator (warp w owns rows 32(w%4)..+31 and
-// one half of the columns), release it and reduce the fixed-point D terms
-// while the next tile's MMAs run. A tile covers rows i0..i0+127 and columns j0..j0+BN-1; the pair (i, j)
+// epilogue; the epilogue warps read an accumulator (warp w owns rows
+// 32(w%4)..+31 and every kEpiParts-th 32-column chunk), release it and reduce
+// the fixed-point D terms while the next tile's MMAs run. A tile covers rows i0..i0+127 and columns j0..j0+BN-1; the pair (i, j)
 // is taken when i <= j (i < j: both D sums, i = j: its own), so every
 // unordered pair is counted exactly once whatever the tile shape.
 template <int BN>
@@ -383,13 +386,13 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         __syncwarp();
     } else {
-        // epilogue warps 2..9: TMEM lane quadrant q = warp % 4 (rows 32q..32q+31),
-        // column half h; the two warps of a quadrant split the tile's columns
+        // epilogue warps: TMEM lane quadrant q = warp % 4 (rows 32q..32q+31) and
+        // part h; the kEpiParts warps of a quadrant split the tile's chunks
         const int ew = warp - 2;
         const int q = warp & 3;
-        const int h = ew >> 2;
-        const int et = threadIdx.x - 64;  // 0..255
-        constexpr int kChunks = BN / 64;  // 32-column chunks per warp
+        const int h = ew >> 2;            // part: chunks h, h + kEpiParts, ...
+        const int et = threadIdx.x - 64;  // 0 .. kEpiThreads - 1
+        constexpr int kChunks = BN / 32;  // 32-column chunks of a tile
         int32_t lt = 0;
         for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x, lt++) {
             const int a = lt & 1;
@@ -398,7 +401,7 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (et == 0) epi_stop = aborted() ? 1 : 0;
             epi_barrier();  // also: the previous tile's tables and column sums are no longer read
             if (epi_stop) break;
-            for (int c = et; c < BN; c += 256) {
+            for (int c = et; c < BN; c += kEpiThreads) {
                 const int32_t j = j0 + c;
                 ct[c] = col_rec(tab, j, n);
                 ColAux x{-1, -1};
@@ -431,8 +434,7 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const bool full = i0 + kTM <= j0 && j0 + BN <= n;
             uint64_t rs_c = 0, rs_l = 0;
 #pragma unroll 1
-            for (int cc0 = 0; cc0 < kChunks; cc0++) {
-                const int c = h * kChunks + cc0;
+            for (int c = h; c < kChunks; c += kEpiParts) {
                 uint32_t v[32];
                 tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
                 uint64_t cw[32];
@@ -464,7 +466,7 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             epi_barrier();
             if (valid)
-                for (int c = et; c < BN; c += 256) {
+                for (int c = et; c < BN; c += kEpiThreads) {
                     const int32_t j = j0 + c;
                     if (j < n) {
                         const unsigned long long sc = colw_c[0][c] + colw_c[1][c] + colw_c[2][c] + colw_c[3][c];
