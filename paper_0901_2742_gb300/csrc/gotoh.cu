@@ -176,6 +176,7 @@ k_gotoh_items(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __r
               GotohArgs a) {
     extern __shared__ __align__(16) int8_t prof[];
     __shared__ int32_t item_sh;
+    __shared__ int32_t next_sub;  // next subject of the item
     const int G = a.G;
     const int NG = blockDim.x / G;
     const int g = threadIdx.x / G;
@@ -205,13 +206,21 @@ k_gotoh_items(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __r
             const int32_t c = t / mp, i = t - c * mp;
             prof[t] = i < m ? a.subst[c * a.alphabet + x[i]] : (int8_t)0;
         }
+        if (threadIdx.x == 0) next_sub = 0;
         __syncthreads();
         int32_t* bnd = a.scratch + ((int64_t)blockIdx.x * NG + g) * a.scratch_stride;
+        // warps take the item's subjects from a shared counter, longest first (the
+        // subjects are in ascending length order), so that no warp waits at the
+        // next item's barrier for more than one subject of another
         const int32_t nsub = it.v1 - it.v0;
-        const int32_t rounds = (nsub + NG - 1) / NG;
-        for (int32_t rd = 0; rd < rounds; rd++) {
-            const int32_t v = it.v0 + rd * NG + g;
-            const bool have = v < it.v1;
+        const int gpw = 32 / G, gw = g % gpw;  // groups per warp, my group's index in it
+        for (;;) {
+            int32_t base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(&next_sub, gpw);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= nsub) break;  // uniform in the warp
+            const int32_t v = it.v1 - 1 - (base + gw);
+            const bool have = v >= it.v0;
             int32_t uv = 0, ys = 0, n = 0;
             if (have) {
                 uv = a.srt[boff + v];
@@ -728,6 +737,7 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
                GotohArgs a) {
     extern __shared__ __align__(16) uint32_t prof32[];
     __shared__ int32_t item_sh;
+    __shared__ int32_t next_sub;                    // next subject of the item (per-subject form)
     __shared__ int2 subj_pos[kChunkSubjects];       // streamed subjects: (CSR position, length)
     __shared__ long long subj_off[kChunkSubjects];  // and their padded residue offsets
     const int G = a.G;
@@ -766,6 +776,7 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
             const int32_t hi = (row && i < m2) ? a.subst[c * a.alphabet + q2[i]] : 0;
             prof32[t] = pk2(lo, hi);
         }
+        if (threadIdx.x == 0) next_sub = 0;
         __syncthreads();
         const int32_t mrows = max(m1, m2);
         if constexpr (kStream) {
@@ -775,11 +786,18 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
                                              subj_pos + g, subj_off + g, a, lane, gmask);
             continue;
         }
+        // warps take the item's subjects from a shared counter, longest first (the
+        // subjects are in ascending length order), so that no warp waits at the
+        // next item's barrier for more than one subject of another
         const int32_t nsub = it.v1 - it.v0;
-        const int32_t rounds = (nsub + NG - 1) / NG;
-        for (int32_t rd = 0; rd < rounds; rd++) {
-            const int32_t v = it.v0 + rd * NG + g;
-            const bool have = v < it.v1;
+        const int gpw = 32 / G, gw = g % gpw;  // groups per warp, my group's index in it
+        for (;;) {
+            int32_t base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(&next_sub, gpw);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= nsub) break;  // uniform in the warp
+            const int32_t v = it.v1 - 1 - (base + gw);
+            const bool have = v >= it.v0;
             int32_t uv = 0, ys = 0, n = 0;
             if (have) {
                 uv = a.srt[boff + v];
