@@ -51,6 +51,7 @@ struct GotohArgs {
     int32_t go, ge;
     int32_t prof_stride;       // bytes per profile row (>= padded query length)
     int32_t G;                 // lanes per group
+    int32_t bias;              // packed form: stored DP value = true value + bias
 };
 
 __device__ __forceinline__ int64_t tri_pos(int64_t u, int64_t v, int64_t nb) {
@@ -265,18 +266,26 @@ KernelFn kernel_for(int R) {
 // ---------------------------------------------------------------------------
 // Packed form: two queries of similar length share every instruction. Each
 // 32-bit register holds the same DP cell of both problems (x1 in the low
-// halfword, x2 in the high halfword) and every cell operation is one 16x2
-// DPX instruction; an add is __viaddmax_s16x2(a, b, NEG2), exact while every
-// value stays above NEG16 (the host proves |values| fit before choosing this
-// form). Per row and column: 5 instructions for 2 cells.
-constexpr int32_t NEG16 = -20000;
-
+// halfword, x2 in the high halfword). Every DP value is stored with a bias B
+// (stored = true + B) chosen by the host so that each stored H, E, F lies in
+// [0, 32767] and each addend keeps it there. Then a plain 32-bit add of a
+// packed addend word a_hi * 2^16 + a_lo adds both halves exactly (a borrow
+// from a negative low addend is cancelled by the carry of the low sum, and no
+// half leaves [0, 65535]), and the compiler can spread those adds over the
+// integer and FMA pipes, while the maxima are 16x2 DPX instructions. The
+// sentinel for -inf is stored 0: every real stored E or F candidate is >= 0.
+// Per row and column: 3 DPX instructions and 2 adds for 2 cells.
 __device__ __forceinline__ uint32_t pk2(int32_t lo, int32_t hi) {
     return ((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16);
 }
 
-__device__ __forceinline__ int32_t lo16(uint32_t v) { return (int32_t)(int16_t)(v & 0xffffu); }
-__device__ __forceinline__ int32_t hi16(uint32_t v) { return (int32_t)(int16_t)(v >> 16); }
+// the 32-bit addend that adds lo to the low and hi to the high halfword
+__host__ __device__ __forceinline__ uint32_t addend2(int32_t lo, int32_t hi) {
+    return (uint32_t)(hi * 65536 + lo);
+}
+
+__device__ __forceinline__ int32_t lo16(uint32_t v) { return (int32_t)(v & 0xffffu); }
+__device__ __forceinline__ int32_t hi16(uint32_t v) { return (int32_t)(v >> 16); }
 
 // Words per lane chunk of the packed profile: R rows padded so that a chunk is
 // an odd number of 16-byte units; the 8 lanes of one 128-bit load phase then
@@ -300,112 +309,19 @@ __device__ __forceinline__ void load_profile32(const uint32_t* p, uint32_t (&s)[
     }
 }
 
-// One group aligns the query pair (packed profile in smem, lengths m1, m2)
-// against subject y of length n; writes the two scores to r1, r2 (valid for
-// m1 >= 1 and m2 >= 1 respectively).
-template <int R>
-__device__ void align_pair16(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2,
-                             const uint8_t* __restrict__ y, int32_t n, int32_t nsteps_warp,
-                             const GotohArgs& a, int32_t* __restrict__ bnd, int lane, unsigned gmask,
-                             int32_t* r1, int32_t* r2) {
-    const int G = a.G;
-    const int32_t go = a.go, ge = a.ge;
-    const uint32_t NEG2 = pk2(NEG16, NEG16);
-    const uint32_t ge2 = pk2(ge, ge), goe2 = pk2(go + ge, go + ge);
-    const int32_t strip_h = G * R;
-    const int32_t mrows = max(m1, m2);
-    const int32_t strips = (mrows + strip_h - 1) / strip_h;
-    for (int32_t s = 0; s < strips; s++) {
-        const int32_t row0 = s * strip_h + lane * R;
-        uint32_t H[R], Hg[R], E[R];
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int32_t b0 = go + (row0 + r + 1) * ge;
-            H[r] = pk2(b0, b0);
-            Hg[r] = __viaddmax_s16x2(H[r], goe2, NEG2);
-            E[r] = NEG2;
-        }
-        const int32_t d0 = (row0 == 0) ? 0 : go + row0 * ge;
-        uint32_t hdiag = pk2(d0, d0);
-        uint32_t hin = 0, fin = NEG2, yin = 0, yword = 0;
-        const bool last_strip = s == strips - 1;
-        for (int32_t tau = 0; tau < nsteps_warp; tau++) {
-            const int32_t j = tau - lane + 1;
-            if (lane == 0 && tau < n) {
-                if ((tau & 3) == 0) yword = *(const uint32_t*)(y + tau);
-                yin = (yword >> (8 * (tau & 3))) & 0xffu;
-                if (s == 0) {
-                    const int32_t b0 = go + (tau + 1) * ge;
-                    hin = pk2(b0, b0);
-                    fin = NEG2;
-                } else {
-                    hin = (uint32_t)bnd[2 * (tau + 1)];
-                    fin = (uint32_t)bnd[2 * (tau + 1) + 1];
-                }
-            }
-            uint32_t hout = hin, fout = fin;
-            if (j >= 1 && j <= n) {
-                uint32_t sc[R];
-                load_profile32<R>(prof + (int64_t)yin * a.prof_stride + (int64_t)(row0 / R) * rpad<R>(),
-                                  sc);
-                uint32_t fu = fin;
-                uint32_t hgu = __viaddmax_s16x2(hin, goe2, NEG2);
-                uint32_t hd = hdiag;
-#pragma unroll
-                for (int r = 0; r < R; r++) {
-                    const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
-                    const uint32_t f = __viaddmax_s16x2(fu, ge2, hgu);
-                    const uint32_t t = __viaddmax_s16x2(hd, sc[r], NEG2);
-                    const uint32_t h = __vimax3_s16x2(t, e, f);
-                    hd = H[r];
-                    H[r] = h;
-                    Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
-                    E[r] = e;
-                    fu = f;
-                    hgu = Hg[r];
-                }
-                hdiag = hin;
-                hout = H[R - 1];
-                fout = fu;
-                if (!last_strip && lane == G - 1) {
-                    bnd[2 * j] = (int32_t)hout;
-                    bnd[2 * j + 1] = (int32_t)fout;
-                }
-            }
-            hin = __shfl_up_sync(gmask, hout, 1, G);
-            fin = __shfl_up_sync(gmask, fout, 1, G);
-            yin = __shfl_up_sync(gmask, yin, 1, G);
-        }
-        __syncwarp(gmask);
-        // a query whose last row lies in this strip has its score now
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-            const int32_t mq = q == 0 ? m1 : m2;
-            if (mq >= 1 && (mq - 1) / strip_h == s) {
-                const int32_t rr = (mq - 1) - s * strip_h;
-                const int owner = rr / R, rsel = rr % R;
-                uint32_t v = 0;
-#pragma unroll
-                for (int r = 0; r < R; r++) v = (r == rsel) ? H[r] : v;
-                v = __shfl_sync(gmask, v, owner, G);
-                if (q == 0) *r1 = lo16(v);
-                else *r2 = hi16(v);
-            }
-        }
-    }
-}
-
 // One lane step over C consecutive subject columns j1..j1+C-1 of the lane's R
 // rows (CC <= C of them present): sub-step s moves row s - c to column j1 + c
 // for every chain c, so the C chains F -> H -> H+go+ge are independent and
 // interleave, and every chain finds its left neighbour (chain c - 1, same row)
 // already one sub-step ahead. The instruction count per cell is that of one
-// column; no branch sits inside the unrolled rows.
+// column; no branch sits inside the unrolled rows. Values are biased (see the
+// packed-form note): t = H(i-1,j-1) + s and H + go + ge are plain 32-bit adds
+// (goe_w = addend2(go + ge, go + ge)); ge2 = pk2(ge, ge) feeds the DPX add-max.
 template <int R, int CC>
 __device__ __forceinline__ void pair16_columns(const uint32_t* __restrict__ prof, int64_t stride, int64_t chunk,
                                                uint32_t letters, uint32_t (&H)[R], uint32_t (&Hg)[R],
                                                uint32_t (&E)[R], const uint32_t* hin, const uint32_t* fin,
-                                               uint32_t hdiag, uint32_t ge2, uint32_t goe2, uint32_t NEG2,
+                                               uint32_t hdiag, uint32_t ge2, uint32_t goe_w,
                                                uint32_t* hout, uint32_t* fout) {
     uint32_t sc[CC][R];
 #pragma unroll
@@ -414,7 +330,7 @@ __device__ __forceinline__ void pair16_columns(const uint32_t* __restrict__ prof
 #pragma unroll
     for (int c = 0; c < CC; c++) {
         fu[c] = fin[c];
-        hgu[c] = __viaddmax_s16x2(hin[c], goe2, NEG2);
+        hgu[c] = hin[c] + goe_w;
         hd[c] = c == 0 ? hdiag : hin[c - 1];
     }
 #pragma unroll
@@ -425,11 +341,10 @@ __device__ __forceinline__ void pair16_columns(const uint32_t* __restrict__ prof
             if (r < 0 || r >= R) continue;
             const uint32_t e = __viaddmax_s16x2(E[r], ge2, Hg[r]);
             const uint32_t f = __viaddmax_s16x2(fu[c], ge2, hgu[c]);
-            const uint32_t t = __viaddmax_s16x2(hd[c], sc[c][r], NEG2);
-            const uint32_t h = __vimax3_s16x2(t, e, f);
+            const uint32_t h = __vimax3_s16x2(hd[c] + sc[c][r], e, f);
             hd[c] = H[r];
             H[r] = h;
-            Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
+            Hg[r] = h + goe_w;
             E[r] = e;
             fu[c] = f;
             hgu[c] = Hg[r];
@@ -446,23 +361,25 @@ template <int R, int C>
 __device__ __forceinline__ void pair16_chunk(int32_t cnt, const uint32_t* __restrict__ prof, int64_t stride,
                                              int64_t chunk, uint32_t letters, uint32_t (&H)[R], uint32_t (&Hg)[R],
                                              uint32_t (&E)[R], const uint32_t* hin, const uint32_t* fin,
-                                             uint32_t hdiag, uint32_t ge2, uint32_t goe2, uint32_t NEG2,
+                                             uint32_t hdiag, uint32_t ge2, uint32_t goe_w,
                                              uint32_t* hout, uint32_t* fout) {
     if (cnt == C) {
-        pair16_columns<R, C>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2, hout, fout);
+        pair16_columns<R, C>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe_w, hout, fout);
     } else if (C > 1 && cnt == 1) {
-        pair16_columns<R, 1>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2, hout, fout);
+        pair16_columns<R, 1>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe_w, hout, fout);
     } else if (C > 2 && cnt == 2) {
-        pair16_columns<R, (C > 2 ? 2 : 1)>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
+        pair16_columns<R, (C > 2 ? 2 : 1)>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe_w,
                                            hout, fout);
     } else if (C > 3 && cnt == 3) {
-        pair16_columns<R, (C > 3 ? 3 : 1)>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
+        pair16_columns<R, (C > 3 ? 3 : 1)>(prof, stride, chunk, letters, H, Hg, E, hin, fin, hdiag, ge2, goe_w,
                                            hout, fout);
     }
 }
 
-// The alignment of align_pair16 with C subject columns per lane step (one
-// chain per column, see pair16_columns). In step tau lane t takes columns
+// One group aligns the query pair (packed profile in smem, lengths m1, m2)
+// against subject y of length n, with C subject columns per lane step (one
+// chain per column, see pair16_columns), in strips of G R rows; writes the two
+// scores to r1, r2 (valid for m1 >= 1 and m2 >= 1). In step tau lane t takes columns
 // C(tau - t) + 1 .. C(tau - t) + C; the last step of a subject whose length is
 // not a multiple of C takes the remaining columns. A step hands C (H, F) pairs
 // and C letters (one 32-bit word) to the next lane.
@@ -474,8 +391,8 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
     static_assert(C >= 1 && C <= 4, "up to four letters travel in one word");
     const int G = a.G;
     const int32_t go = a.go, ge = a.ge;
-    const uint32_t NEG2 = pk2(NEG16, NEG16);
-    const uint32_t ge2 = pk2(ge, ge), goe2 = pk2(go + ge, go + ge);
+    const int32_t B = a.bias;  // stored = true + B
+    const uint32_t ge2 = pk2(ge, ge), goe_w = addend2(go + ge, go + ge);
     const int32_t strip_h = G * R;
     const int32_t mrows = max(m1, m2);
     const int32_t strips = (mrows + strip_h - 1) / strip_h;
@@ -485,18 +402,18 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
         uint32_t H[R], Hg[R], E[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int32_t b0 = go + (row0 + r + 1) * ge;
+            const int32_t b0 = go + (row0 + r + 1) * ge + B;
             H[r] = pk2(b0, b0);
-            Hg[r] = __viaddmax_s16x2(H[r], goe2, NEG2);
-            E[r] = NEG2;
+            Hg[r] = H[r] + goe_w;
+            E[r] = 0u;
         }
-        const int32_t d0 = (row0 == 0) ? 0 : go + row0 * ge;
+        const int32_t d0 = ((row0 == 0) ? 0 : go + row0 * ge) + B;
         uint32_t hdiag = pk2(d0, d0);  // H(row0 - 1, j1 - 1)
         uint32_t hin[C], fin[C], yin = 0;
 #pragma unroll
         for (int c = 0; c < C; c++) {
-            hin[c] = 0;
-            fin[c] = NEG2;
+            hin[c] = 0u;
+            fin[c] = 0u;
         }
         const bool last_strip = s == strips - 1;
         const int64_t chunk = (int64_t)(row0 / R) * rpad<R>();
@@ -511,9 +428,9 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
 #pragma unroll
                 for (int c = 0; c < C; c++) {
                     if (s == 0) {
-                        const int32_t b = go + (j1 + c) * ge;
+                        const int32_t b = go + (j1 + c) * ge + B;
                         hin[c] = pk2(b, b);
-                        fin[c] = NEG2;
+                        fin[c] = 0u;
                     } else if (j1 + c <= n) {  // the buffer holds columns 0..n
                         hin[c] = (uint32_t)bnd[2 * (j1 + c)];
                         fin[c] = (uint32_t)bnd[2 * (j1 + c) + 1];
@@ -530,8 +447,8 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
             }
             if (cidx >= 0 && j1 <= n) {
                 const int32_t cnt = min(C, n - j1 + 1);
-                pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
-                                   hout, fout);
+                pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe_w, hout,
+                                   fout);
                 // the last column's value from above is the next step's diagonal
                 // (constant indices keep the arrays in registers)
 #pragma unroll
@@ -565,8 +482,8 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
 #pragma unroll
                 for (int r = 0; r < R; r++) v = (r == rsel) ? H[r] : v;
                 v = __shfl_sync(gmask, v, owner, G);
-                if (q == 0) *r1 = lo16(v);
-                else *r2 = hi16(v);
+                if (q == 0) *r1 = lo16(v) - B;
+                else *r2 = hi16(v) - B;
             }
         }
     }
@@ -592,8 +509,8 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
                               int lane, unsigned gmask) {
     const int G = a.G;
     const int32_t go = a.go, ge = a.ge;
-    const uint32_t NEG2 = pk2(NEG16, NEG16);
-    const uint32_t ge2 = pk2(ge, ge), goe2 = pk2(go + ge, go + ge);
+    const int32_t B = a.bias;  // stored = true + B
+    const uint32_t ge2 = pk2(ge, ge), goe_w = addend2(go + ge, go + ge);
     int32_t* scores = a.scores + a.score_off[b];
     auto subject = [&](int32_t v, int32_t* uv, int32_t* ys) {
         *uv = a.srt[boff + v];
@@ -650,8 +567,8 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
     uint32_t hin[C], fin[C], yin = 0;
 #pragma unroll
     for (int c = 0; c < C; c++) {
-        hin[c] = 0;
-        fin[c] = NEG2;
+        hin[c] = 0u;
+        fin[c] = 0u;
     }
     for (int32_t tau = 0; tau < steps; tau++) {
         const bool live = tau >= lane && ck < nsubj;
@@ -660,9 +577,9 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
 #pragma unroll
             for (int c = 0; c < C; c++) {
                 yin |= (uint32_t)cy[cj - 1 + c] << (8 * c);  // bytes past the subject are zero padding
-                const int32_t bnd0 = go + (cj + c) * ge;
+                const int32_t bnd0 = go + (cj + c) * ge + B;
                 hin[c] = pk2(bnd0, bnd0);
-                fin[c] = NEG2;
+                fin[c] = 0u;
             }
         }
         uint32_t hout[C], fout[C];
@@ -676,21 +593,21 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
                 // recomputed here on purpose: hoisting these 2R loop-invariant values
                 // out of the loop would hold them in registers for the whole stream
                 int32_t base;
-                asm volatile("mov.b32 %0, %1;" : "=r"(base) : "r"(go + row0 * ge));
-                const uint32_t ge1 = pk2(ge, ge);
+                asm volatile("mov.b32 %0, %1;" : "=r"(base) : "r"(go + row0 * ge + B));
+                const uint32_t ge_w = addend2(ge, ge);
                 uint32_t h = pk2(base, base);
 #pragma unroll
                 for (int r = 0; r < R; r++) {
-                    h = __viaddmax_s16x2(h, ge1, NEG2);  // go + (row0 + r + 1) ge
+                    h = h + ge_w;  // go + (row0 + r + 1) ge
                     H[r] = h;
-                    Hg[r] = __viaddmax_s16x2(h, goe2, NEG2);
-                    E[r] = NEG2;
+                    Hg[r] = h + goe_w;
+                    E[r] = 0u;
                 }
-                hdiag = row0 == 0 ? 0u : pk2(base, base);
+                hdiag = row0 == 0 ? pk2(B, B) : pk2(base, base);
             }
             const int32_t cnt = min(C, cn - cj + 1);
-            pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe2, NEG2,
-                               hout, fout);
+            pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe_w, hout,
+                               fout);
 #pragma unroll
             for (int c = 0; c < C; c++)
                 if (c == cnt - 1) hdiag = hin[c];
@@ -702,8 +619,8 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
                         v1 = (r == sel1) ? H[r] : v1;
                         v2 = (r == sel2) ? H[r] : v2;
                     }
-                    if (lane == own1) scores[tri_pos(min(u1, cuv), max(u1, cuv), nb)] = lo16(v1);
-                    if (lane == own2) scores[tri_pos(min(u2, cuv), max(u2, cuv), nb)] = hi16(v2);
+                    if (lane == own1) scores[tri_pos(min(u1, cuv), max(u1, cuv), nb)] = lo16(v1) - B;
+                    if (lane == own2) scores[tri_pos(min(u2, cuv), max(u2, cuv), nb)] = hi16(v2) - B;
                 }
                 advance();
             } else {
@@ -774,7 +691,7 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
             const bool row = off < R;
             const int32_t lo = (row && i < m1) ? a.subst[c * a.alphabet + q1[i]] : 0;
             const int32_t hi = (row && i < m2) ? a.subst[c * a.alphabet + q2[i]] : 0;
-            prof32[t] = pk2(lo, hi);
+            prof32[t] = addend2(lo, hi);
         }
         if (threadIdx.x == 0) next_sub = 0;
         __syncthreads();
@@ -811,10 +728,7 @@ k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __
             if (steps > 0) {
                 const uint8_t* yp = a.res + a.pad_off[have ? ys : x1];
                 const int32_t ny = (have && mrows > 0) ? n : 0;
-                if constexpr (kC > 1)
-                    align_pair16c<R, kC>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
-                else
-                    align_pair16<R>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
+                align_pair16c<R, kC>(prof32, m1, m2, yp, ny, steps, a, bnd, lane, gmask, &s1, &s2);
             }
             if (have && lane == 0) {
                 const int32_t mq[2] = {m1, m2};
@@ -926,11 +840,14 @@ constexpr int kPackedG[] = {8, 16, 32};
 constexpr int kNumR = 6, kNumG = 3, kNumVariants = kNumR * kNumG;
 constexpr int kPackedThreads = 128;
 
-// Every value of the packed DP must stay inside (NEG16, 2^15): scores are at
-// most max(s, 0) * min(m, n) and at least the all-gap path 2 go + (i + j) ge
-// (minus one gap opening and the most negative substitution for E, F and the
-// diagonal sum), with i up to the padded strip rows.
-bool fits_packed16(const DevSeqs& S, const int8_t* subst, int32_t go, int32_t ge) {
+// Bias of the packed form (stored = true + bias), or false when none fits.
+// Over the padded strip rows i <= L + 1024 and columns j <= L (L = longest
+// sequence) every true H, E, F value v satisfies
+//   2 go + (i + j) ge <= v <= max(s, 0) L
+// (the all-gap path is one alignment; each column gains at most max(s, 0)).
+// The stored values must stay in [0, 32767] with room for every addend:
+//   bias + vmin + min(smin, go + ge, 0) >= 0,  bias + vmax + max(smax, 0) <= 32767.
+bool packed16_bias(const DevSeqs& S, const int8_t* subst, int32_t go, int32_t ge, int32_t* bias) {
     int32_t smax = 0, smin = 0;
     for (int32_t t = 0; t < S.alphabet * S.alphabet; t++) {
         smax = std::max<int32_t>(smax, subst[t]);
@@ -938,9 +855,13 @@ bool fits_packed16(const DevSeqs& S, const int8_t* subst, int32_t go, int32_t ge
     }
     const int64_t L = S.max_len;
     const int64_t rows = L + 1024;  // padding of the widest strip
-    const int64_t hi = (int64_t)smax * L;
-    const int64_t lo = 3ll * -go + (int64_t)-ge * (rows + L + 2) - smin;
-    return hi < 32000 && lo < -(int64_t)NEG16 - 1000 && -ge < 4000 && -go < 4000;
+    const int64_t vmax = (int64_t)smax * L;
+    const int64_t vmin = 2ll * go + (int64_t)ge * (rows + L);
+    const int64_t lo = -vmin - std::min<int64_t>(std::min<int64_t>(smin, go + ge), 0);
+    const int64_t hi = 32767 - vmax - smax;
+    if (lo > hi) return false;
+    *bias = (int32_t)lo;
+    return true;
 }
 
 int rpad_rt(int R) { return ((R / 4) % 2 == 0) ? R + 4 : R; }
@@ -1143,6 +1064,7 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         a.go = base.go;
         a.ge = base.ge;
         a.scratch_stride = stride;
+        a.bias = base.bias;
     };
     for (int v = 0; v < kNumVariants; v++) {
         if (shp[v].grid == 0) continue;
@@ -1342,7 +1264,7 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
             first += nb;
         }
     } else {
-        if (fits_packed16(S, h_subst, go, ge)) {
+        if (packed16_bias(S, h_subst, go, ge, &L.bias)) {
             SAD_RET(launch_packed(ctx, S, h_bo, h_order, srt, L, stream));
             return SAD_OK;
         }
@@ -1425,7 +1347,8 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
     cudaStream_t stream = (cudaStream_t)stream_ptr;
     DevSeqs S;
     SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
-    SAD_CHECK(fits_packed16(S, subst, gap_open, gap_extend), SAD_EINVAL,
+    int32_t bias = 0;  // the score calls below derive it again
+    SAD_CHECK(packed16_bias(S, subst, gap_open, gap_extend, &bias), SAD_EINVAL,
               "these sequences and costs need the 32-bit kernel; there is nothing to tune");
     const int32_t n = S.n;
     const int32_t* dbo = bucket_offsets;

@@ -25,6 +25,7 @@ struct GotohLaunch {
     int32_t* scores = nullptr;
     const int8_t* subst = nullptr;
     int32_t go = 0, ge = 0;
+    int32_t bias = 0;  // packed form: stored DP value = true value + bias
     int R = 16, G = 32;
     int32_t max_m = 0;
     const GotohItem* items = nullptr;
