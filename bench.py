@@ -92,6 +92,32 @@ def aggregate_ranks(ms_step: float, units: float, dist=None, device=None):
     return float(t.item()), float(u.item()), dist.get_world_size()
 
 
+def device_gaps(spans):
+    """Device idle time inside the traced part of each step, from the tracer's
+    timeline: a step's intervals start with its 'prepare' stage; the gap after a
+    stage is the time from its end to the start of the next traced interval of
+    the same step (host work and synchronisation between launches)."""
+    steps, cur = [], []
+    for sp in spans:
+        if sp[0] == "prepare" and cur:
+            steps.append(cur)
+            cur = []
+        cur.append(sp)
+    if cur:
+        steps.append(cur)
+    if not steps:
+        return None
+    gap_after, busy, span = {}, 0.0, 0.0
+    for st in steps:
+        busy += sum(b - a for _, a, b in st)
+        span += st[-1][2] - st[0][1]
+        for (s0, _, b0), (_, a1, _) in zip(st, st[1:]):
+            gap_after[s0] = gap_after.get(s0, 0.0) + (a1 - b0)
+    k = len(steps)
+    return {"traced_span_ms": span / k, "busy_ms": busy / k, "idle_ms": (span - busy) / k,
+            "gap_after_ms": {s: g / k for s, g in gap_after.items()}}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -363,6 +389,7 @@ def main():
     wall = time.perf_counter() - t0
     launches = sad.launch_count() - l0
     trace = sad.trace_read()
+    timeline = device_gaps(sad.trace_timeline())
     sad.trace_enable(False)
     clocks = clock_sampler_stop(sampler, sf, clock_path, local)
     if dist:
@@ -459,6 +486,7 @@ def main():
                    "autotune_s": round(t_tune, 3) if tuning else None},
         "kmer_pairs_per_s": n * (n + 1) / 2 / (kmer_ms * 1e-3) if kmer_ms > 0 else None,
         "stage_ms": {k: v[0] / args.steps for k, v in trace.items()},
+        "device_timeline": timeline,
         "pairs_scored": pairs_scored, "cells": cells,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
                      "frac": achieved / peak, "traffic": None,

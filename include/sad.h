@@ -193,6 +193,14 @@ int sad_trace_enable(sad_ctx* ctx, int32_t on);
  * milliseconds (ms[s]) and the number of traced intervals (counts[s]) for
  * s < nstages, and clear them. */
 int sad_trace_read(sad_ctx* ctx, double* ms, int32_t* counts, int32_t nstages);
+/* The intervals that the last sad_trace_read consumed, in start order: for
+ * entry t its stage (stage[t]) and its device start and end (t0_ms[t],
+ * t1_ms[t]) in milliseconds after the start of the first of them. Gaps between
+ * consecutive intervals of one call are device idle time (host work between
+ * launches, host synchronisation). Writes min(n, max_entries) entries and sets
+ * *n_entries = n. Host arrays, caller-owned. */
+int sad_trace_timeline(sad_ctx* ctx, int32_t* stage, double* t0_ms, double* t1_ms, int32_t max_entries,
+                       int32_t* n_entries);
 /* Number of kernels this library has launched in this process. */
 uint64_t sad_launch_count(void);
 

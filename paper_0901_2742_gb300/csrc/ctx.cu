@@ -1,6 +1,7 @@
 // Context, workspaces, error reporting and sequence staging for libsad.
 #include <cstdarg>
 #include <atomic>
+#include <algorithm>
 #include <cstring>
 
 #include "sad_internal.cuh"
@@ -46,6 +47,7 @@ TraceScope::TraceScope(sad_ctx* ctx, int stage, cudaStream_t stream)
     end_ = take_event(ctx_);
     if (!b || !end_) return;
     cudaEventRecord(b, stream_);
+    if (!ctx_->trace_origin) ctx_->trace_origin = b;
     ctx_->trace[stage_].pending.push_back({b, end_});
 }
 
@@ -296,19 +298,34 @@ int trace_reset(sad_ctx* ctx, bool on) {
         st.ms = 0;
         st.count = 0;
     }
+    ctx->trace_origin = nullptr;
+    ctx->timeline.clear();
     ctx->trace_on = on;
     return SAD_OK;
 }
 
 int trace_collect(sad_ctx* ctx, double* ms, int32_t* counts, int32_t nstages) {
+    // every interval's times first (the origin is one of the begin events), then
+    // the events go back to the pool
+    ctx->timeline.clear();
     for (int s = 0; s < SAD_NUM_STAGES; s++) {
         auto& st = ctx->trace[s];
         for (auto& pr : st.pending) {
             SAD_CUDA(cudaEventSynchronize(pr.second));
-            float t = 0;
+            float t = 0, a = 0, b = 0;
             SAD_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+            SAD_CUDA(cudaEventElapsedTime(&a, ctx->trace_origin, pr.first));
+            SAD_CUDA(cudaEventElapsedTime(&b, ctx->trace_origin, pr.second));
+            ctx->timeline.push_back(TraceSpan{s, a, b});
             st.ms += t;
             st.count++;
+        }
+    }
+    std::stable_sort(ctx->timeline.begin(), ctx->timeline.end(),
+                     [](const TraceSpan& x, const TraceSpan& y) { return x.t0 < y.t0; });
+    for (int s = 0; s < SAD_NUM_STAGES; s++) {
+        auto& st = ctx->trace[s];
+        for (auto& pr : st.pending) {
             ctx->event_pool.push_back(pr.first);
             ctx->event_pool.push_back(pr.second);
         }
@@ -320,6 +337,7 @@ int trace_collect(sad_ctx* ctx, double* ms, int32_t* counts, int32_t nstages) {
         st.ms = 0;
         st.count = 0;
     }
+    ctx->trace_origin = nullptr;
     for (int s = SAD_NUM_STAGES; s < nstages; s++) {
         ms[s] = 0;
         counts[s] = 0;
@@ -392,6 +410,26 @@ int sad_trace_read(sad_ctx* ctx_in, double* ms, int32_t* counts, int32_t nstages
     SAD_RET(sad::resolve_ctx(ctx_in, &ctx));
     std::lock_guard<std::mutex> lock(ctx->mu);
     return sad::trace_collect(ctx, ms, counts, nstages);
+}
+
+int sad_trace_timeline(sad_ctx* ctx_in, int32_t* stage, double* t0_ms, double* t1_ms, int32_t max_entries,
+                       int32_t* n_entries) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(n_entries != nullptr, SAD_EINVAL, "n_entries is NULL");
+    SAD_CHECK(max_entries >= 0 && (max_entries == 0 || (stage && t0_ms && t1_ms)), SAD_EINVAL,
+              "an output pointer is NULL");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    const int32_t n = (int32_t)ctx->timeline.size();
+    for (int32_t t = 0; t < n && t < max_entries; t++) {
+        stage[t] = ctx->timeline[t].stage;
+        t0_ms[t] = ctx->timeline[t].t0;
+        t1_ms[t] = ctx->timeline[t].t1;
+    }
+    *n_entries = n;
+    return SAD_OK;
 }
 
 const char* sad_version(void) { return "sad-gb300 0.1 (sm_103a)"; }

@@ -636,10 +636,17 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
     }
 }
 
-// Columns per lane step of the packed kernel for R rows per lane.
+// Columns per lane step of the packed kernel for R rows per lane (a build
+// option: SAD_PAIR_COLS_SMALL for R <= 20, SAD_PAIR_COLS_LARGE above).
+#ifndef SAD_PAIR_COLS_SMALL
+#define SAD_PAIR_COLS_SMALL 2
+#endif
+#ifndef SAD_PAIR_COLS_LARGE
+#define SAD_PAIR_COLS_LARGE 2
+#endif
 template <int R>
 __host__ __device__ constexpr int pair_cols() {
-    return 2;
+    return R <= 20 ? SAD_PAIR_COLS_SMALL : SAD_PAIR_COLS_LARGE;
 }
 
 // Work item (bucket, query pair qp, subjects [v0, v1)): queries are the
@@ -770,13 +777,15 @@ void plan_buckets(const std::vector<int32_t>& h_bo, const std::vector<int32_t>& 
                   std::vector<int64_t>* score_off) {
     srt->assign(h_order.size(), 0);
     score_off->assign((size_t)p + 1, 0);
+    std::vector<uint64_t> key;
     for (int32_t b = 0; b < p; b++) {
         const int32_t lo = h_bo[b], nb = h_bo[b + 1] - h_bo[b];
+        // (length, local position) packed in one integer: ascending length, ties by position
+        key.resize((size_t)nb);
+        for (int32_t u = 0; u < nb; u++) key[u] = ((uint64_t)(uint32_t)h_len[h_order[lo + u]] << 32) | (uint32_t)u;
+        std::sort(key.begin(), key.end());
         int32_t* s = srt->data() + lo;
-        std::iota(s, s + nb, 0);
-        std::stable_sort(s, s + nb, [&](int32_t u, int32_t v) {
-            return h_len[h_order[lo + u]] < h_len[h_order[lo + v]];
-        });
+        for (int32_t u = 0; u < nb; u++) s[u] = (int32_t)(key[u] & 0xffffffffu);
         (*score_off)[b + 1] = (*score_off)[b] + (int64_t)nb * (nb + 1) / 2;
     }
 }
@@ -903,9 +912,19 @@ struct PackedLaunch {
     GotohArgs args;
 };
 
-int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_bo,
-                  const std::vector<int32_t>& h_order, const std::vector<int32_t>& srt,
-                  const GotohLaunch& base, cudaStream_t stream) {
+// Host plan of the packed score stage: work items grouped by kernel variant
+// (longest first inside a variant), then the single-query items of queries too
+// long for any packed profile.
+struct PackedPlan {
+    std::vector<GotohItem> all;
+    int32_t first[kNumVariants + 1];
+    int32_t rows_var[kNumVariants];
+    int32_t first_single = 0;
+    int32_t singles_rows = 0;
+};
+
+void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_bo,
+                 const std::vector<int32_t>& h_order, const std::vector<int32_t>& srt, PackedPlan* plan) {
     const int32_t p = (int32_t)h_bo.size() - 1;
     auto len_at = [&](int32_t b, int32_t pos) { return S.h_len[h_order[h_bo[b] + srt[h_bo[b] + pos]]]; };
     std::vector<GotohItem> by_var[kNumVariants];
@@ -913,17 +932,18 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
     int32_t rows_var[kNumVariants] = {0};
     std::vector<GotohItem> singles;  // single-query items for the 32-bit kernel
     int32_t singles_rows = 0;
+    std::vector<int64_t> pre;  // prefix sums of the bucket's lengths in length order
     for (int32_t b = 0; b < p; b++) {
         const int32_t nb = h_bo[b + 1] - h_bo[b];
+        pre.assign((size_t)nb + 1, 0);
+        for (int32_t v = 0; v < nb; v++) pre[v + 1] = pre[v] + len_at(b, v);
         for (int32_t qp = 0; 2 * qp < nb; qp++) {
             const int32_t m1 = len_at(b, 2 * qp);
             const int32_t m2 = (2 * qp + 1 < nb) ? len_at(b, 2 * qp + 1) : 0;
             const int32_t rows = std::max(m1, m2);
             for (int32_t v0 = 2 * qp; v0 < nb; v0 += kChunkSubjects) {
                 const int32_t v1 = std::min(nb, v0 + kChunkSubjects);
-                double nsum = 0;
-                for (int32_t v = v0; v < v1; v++) nsum += len_at(b, v);
-                const double navg = nsum / (v1 - v0);
+                const double navg = (double)(pre[v1] - pre[v0]) / (v1 - v0);
                 // the packed profile of the pair must fit in shared memory
                 auto fits = [&](int v) {
                     const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
@@ -979,30 +999,57 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
     // longest first inside every variant
     std::vector<GotohItem> all;
     int32_t first[kNumVariants + 1];
+    std::vector<std::pair<double, int32_t>> ord;
     for (int v = 0; v < kNumVariants; v++) {
         first[v] = (int32_t)all.size();
-        std::vector<int32_t> idx(by_var[v].size());
-        std::iota(idx.begin(), idx.end(), 0);
-        std::stable_sort(idx.begin(), idx.end(),
-                         [&](int32_t x, int32_t y) { return cost_var[v][x] > cost_var[v][y]; });
-        for (int32_t t : idx) all.push_back(by_var[v][t]);
+        ord.resize(by_var[v].size());
+        for (size_t t = 0; t < ord.size(); t++) ord[t] = {-cost_var[v][t], (int32_t)t};
+        std::sort(ord.begin(), ord.end());  // largest cost first, ties in plan order
+        for (const auto& e : ord) all.push_back(by_var[v][e.second]);
     }
     first[kNumVariants] = (int32_t)all.size();
-    const int32_t first_single = (int32_t)all.size();
+    plan->first_single = (int32_t)all.size();
     for (const GotohItem& it : singles) all.push_back(it);
-    const size_t items_bytes = sizeof(GotohItem) * (all.size() + 1);
-    const size_t heads_off = (size_t)round_up((int64_t)items_bytes, 256);
+    plan->singles_rows = singles_rows;
+    for (int v = 0; v <= kNumVariants; v++) plan->first[v] = first[v];
+    for (int v = 0; v < kNumVariants; v++) plan->rows_var[v] = rows_var[v];
+    plan->all.swap(all);
+}
+
+// Blocks of `fn` resident per SM at `threads` threads and `smem` dynamic shared
+// memory bytes (cached: the answer depends only on these and the device).
+int occupancy(sad_ctx* ctx, const void* fn, int threads, size_t smem, int* occ) {
+    struct Key {
+        int dev;
+        const void* fn;
+        int threads;
+        size_t smem;
+    };
+    static std::mutex mu;
+    static std::vector<std::pair<Key, int>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : cache)
+        if (e.first.dev == ctx->device && e.first.fn == fn && e.first.threads == threads && e.first.smem == smem) {
+            *occ = e.second;
+            return SAD_OK;
+        }
+    int o = 0;
+    SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, threads, smem));
+    cache.push_back({Key{ctx->device, fn, threads, smem}, o});
+    *occ = o;
+    return SAD_OK;
+}
+
+// Launch a packed plan whose items are on the device (d_items, in plan order)
+// with kNumVariants + 1 queue heads at d_heads (zeroed here, on the stream).
+int launch_packed(sad_ctx* ctx, const DevSeqs& S, const PackedPlan& plan, const GotohItem* d_items,
+                  int32_t* d_heads, const GotohLaunch& base, cudaStream_t stream) {
+    const int32_t* first = plan.first;
+    const int32_t* rows_var = plan.rows_var;
+    const int32_t first_single = plan.first_single;
+    const int32_t singles_rows = plan.singles_rows;
+    const size_t n_singles = plan.all.size() - (size_t)first_single;
     const size_t heads_bytes = 4 * (kNumVariants + 1);
-    void* dplan = nullptr;
-    SAD_RET(workspace(ctx, WS_SCORE_ITEMS, heads_off + heads_bytes + 256, stream, &dplan));
-    void* pin = nullptr;
-    SAD_RET(pinned(ctx, heads_off + heads_bytes, stream, &pin));
-    SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may feed an earlier copy
-    memcpy(pin, all.data(), sizeof(GotohItem) * all.size());
-    memset((char*)pin + heads_off, 0, heads_bytes);
-    SAD_CUDA(cudaMemcpyAsync(dplan, pin, heads_off + heads_bytes, cudaMemcpyHostToDevice, stream));
-    const GotohItem* d_items = (const GotohItem*)dplan;
-    int32_t* d_heads = (int32_t*)((char*)dplan + heads_off);
     // launch shapes and strip-boundary scratch
     struct Shape {
         int grid = 0;
@@ -1032,7 +1079,7 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         KernelFn fn = pair16_kernel_for(R, shp[v].stream);
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
         int occ = 0;
-        SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kPackedThreads, shp[v].smem));
+        SAD_RET(occupancy(ctx, (const void*)fn, kPackedThreads, shp[v].smem, &occ));
         occ = std::max(occ, 1);
         shp[v].grid = std::min<int64_t>(nv, (int64_t)ctx->num_sms * occ);
         if (shp[v].strips) {
@@ -1084,7 +1131,7 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
         L.head = d_heads + v;
         recs.push_back(L);
     }
-    if (!singles.empty()) {
+    if (n_singles > 0) {
         // queries too long for a packed profile: 32-bit kernel, int8 profile, G = 32, R = 32
         constexpr int R1 = 32, G1 = 32, T1 = 128;
         PackedLaunch L;
@@ -1098,15 +1145,15 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_
                   L.smem);
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)L.fn));
         int occ = 0;
-        SAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, L.fn, T1, L.smem));
-        L.grid = (int)std::min<int64_t>((int64_t)singles.size(), (int64_t)ctx->num_sms * std::max(occ, 1));
+        SAD_RET(occupancy(ctx, (const void*)L.fn, T1, L.smem, &occ));
+        L.grid = (int)std::min<int64_t>((int64_t)n_singles, (int64_t)ctx->num_sms * std::max(occ, 1));
         void* sp = nullptr;
         SAD_RET(workspace(ctx, WS_SCORE_SCRATCH_LONG, sizeof(int32_t) * (size_t)L.grid * (T1 / G1) * stride,
                           stream, &sp));
         L.args.scratch = (int32_t*)sp;
         L.block = T1;
         L.items = d_items + first_single;
-        L.n_items = (int32_t)singles.size();
+        L.n_items = (int32_t)n_singles;
         L.head = d_heads + kNumVariants;
         recs.push_back(L);
     }
@@ -1193,18 +1240,45 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
     std::vector<int64_t> score_off;
     plan_buckets(h_bo, h_order, S.h_len, p, &srt, &score_off);
     *total_out = score_off[p];
-    // device plan: srt, score_off, subst, items
-    std::vector<GotohItem> items;
-    int32_t max_m = 0;
-    for (int32_t b = 0; b < p; b++) {
-        const int32_t lo = h_bo[b], nb = h_bo[b + 1] - lo;
-        for (int32_t q = 0; q < nb; q++) {
-            items.push_back(GotohItem{b, q, q, nb});
-            max_m = std::max(max_m, S.h_len[h_order[lo + srt[lo + q]]]);
-        }
-    }
     SAD_CHECK(mode == SAD_SCORES_PER_BUCKET || mode == SAD_SCORES_PERSISTENT, SAD_EINVAL,
               "unknown scores mode %d", mode);
+    // work items: the packed plan, or one item per query row (longest first for
+    // the persistent 32-bit kernel)
+    int32_t bias = 0;
+    const bool packed = mode == SAD_SCORES_PERSISTENT && packed16_bias(S, h_subst, go, ge, &bias);
+    PackedPlan pplan;
+    std::vector<GotohItem> items;
+    int32_t max_m = 0;
+    if (packed) {
+        plan_packed(ctx, S, h_bo, h_order, srt, &pplan);
+    } else {
+        for (int32_t b = 0; b < p; b++) {
+            const int32_t lo = h_bo[b], nb = h_bo[b + 1] - lo;
+            for (int32_t q = 0; q < nb; q++) {
+                items.push_back(GotohItem{b, q, q, nb});
+                max_m = std::max(max_m, S.h_len[h_order[lo + srt[lo + q]]]);
+            }
+        }
+        if (mode == SAD_SCORES_PERSISTENT) {
+            std::vector<int64_t> cost(items.size());
+            std::vector<int32_t> idx(items.size());
+            for (size_t t = 0; t < items.size(); t++) {
+                const GotohItem& it = items[t];
+                const int32_t lo = h_bo[it.bucket];
+                const int64_t mq = S.h_len[h_order[lo + srt[lo + it.q]]];
+                int64_t c = 0;
+                for (int32_t v = it.v0; v < it.v1; v++) c += mq * S.h_len[h_order[lo + srt[lo + v]]];
+                cost[t] = c;
+                idx[t] = (int32_t)t;
+            }
+            std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+            std::vector<GotohItem> sorted(items.size());
+            for (size_t t = 0; t < items.size(); t++) sorted[t] = items[idx[t]];
+            items.swap(sorted);
+        }
+    }
+    const std::vector<GotohItem>& its = packed ? pplan.all : items;
+    // one staging copy: srt, score_off, subst, items, queue heads
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         size_t o = off;
@@ -1212,18 +1286,18 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
         return o;
     };
     const size_t o_srt = carve(4ull * (n + 1)), o_so = carve(8ull * (p + 1)),
-                 o_sub = carve((size_t)S.alphabet * S.alphabet), o_items = carve(sizeof(GotohItem) * (items.size() + 1)),
-                 o_head = carve(16);
+                 o_sub = carve((size_t)S.alphabet * S.alphabet), o_items = carve(sizeof(GotohItem) * (its.size() + 1)),
+                 o_head = carve(4 * (kNumVariants + 1));
     void* plan = nullptr;
     SAD_RET(workspace(ctx, WS_SCORE_PLAN, off, stream, &plan));
     void* pin = nullptr;
-    SAD_RET(pinned(ctx, off, stream, &pin));
+    SAD_RET(pinned(ctx, off, stream, &pin));  // earlier copies from it are done: the stream was synchronised above
     char* hp = (char*)pin;
     memcpy(hp + o_srt, srt.data(), 4ull * n);
     memcpy(hp + o_so, score_off.data(), 8ull * (p + 1));
     memcpy(hp + o_sub, h_subst, (size_t)S.alphabet * S.alphabet);
-    memcpy(hp + o_items, items.data(), sizeof(GotohItem) * items.size());
-    memset(hp + o_head, 0, 16);
+    if (!its.empty()) memcpy(hp + o_items, its.data(), sizeof(GotohItem) * its.size());
+    memset(hp + o_head, 0, 4 * (kNumVariants + 1));
     char* dp = (char*)plan;
     SAD_CUDA(cudaMemcpyAsync(dp, hp, off, cudaMemcpyHostToDevice, stream));
     if (d_score_off_out)
@@ -1243,7 +1317,10 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
     L.subst = (const int8_t*)(dp + o_sub);
     L.go = go;
     L.ge = ge;
+    L.bias = bias;
     const GotohItem* d_items = (const GotohItem*)(dp + o_items);
+    int32_t* d_heads = (int32_t*)(dp + o_head);
+    if (packed) return launch_packed(ctx, S, pplan, d_items, d_heads, L, stream);
     if (mode == SAD_SCORES_PER_BUCKET) {
         // one launch per bucket, R from the bucket's median member length
         int64_t first = 0;
@@ -1263,44 +1340,21 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
             SAD_RET(gotoh_launch(ctx, S, L, stream));
             first += nb;
         }
-    } else {
-        if (packed16_bias(S, h_subst, go, ge, &L.bias)) {
-            SAD_RET(launch_packed(ctx, S, h_bo, h_order, srt, L, stream));
-            return SAD_OK;
-        }
-        // persistent: one launch over every bucket's rows, longest first
-        std::vector<int64_t> cost(items.size());
-        std::vector<int32_t> idx(items.size());
-        for (size_t t = 0; t < items.size(); t++) {
-            const GotohItem& it = items[t];
-            const int32_t lo = h_bo[it.bucket];
-            const int64_t mq = S.h_len[h_order[lo + srt[lo + it.q]]];
-            int64_t c = 0;
-            for (int32_t v = it.v0; v < it.v1; v++) c += mq * S.h_len[h_order[lo + srt[lo + v]]];
-            cost[t] = c;
-            idx[t] = (int32_t)t;
-        }
-        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
-        std::vector<GotohItem> sorted(items.size());
-        for (size_t t = 0; t < items.size(); t++) sorted[t] = items[idx[t]];
-        memcpy(hp + o_items, sorted.data(), sizeof(GotohItem) * sorted.size());
-        SAD_CUDA(cudaMemcpyAsync(dp + o_items, hp + o_items, sizeof(GotohItem) * sorted.size(),
-                                 cudaMemcpyHostToDevice, stream));
-        std::vector<int32_t> all_len;
-        for (int32_t i = 0; i < n; i++) all_len.push_back(S.h_len[i]);
-        std::sort(all_len.begin(), all_len.end());
-        const int32_t med = n ? all_len[n / 2] : 1;
-        L.R = pick_R(med);
-        L.G = 32;
-        L.max_m = max_m;
-        L.items = d_items;
-        L.n_items = (int32_t)items.size();
-        L.head = (int32_t*)(dp + o_head);
-        L.persistent = true;
-        L.persistent_grid = ctx->num_sms * 4;
-        SAD_RET(gotoh_launch(ctx, S, L, stream));
+        return SAD_OK;
     }
-    return SAD_OK;
+    // persistent 32-bit: one launch over every bucket's rows, longest first
+    std::vector<int32_t> all_len(S.h_len.begin(), S.h_len.begin() + n);
+    std::sort(all_len.begin(), all_len.end());
+    const int32_t med = n ? all_len[n / 2] : 1;
+    L.R = pick_R(med);
+    L.G = 32;
+    L.max_m = max_m;
+    L.items = d_items;
+    L.n_items = (int32_t)items.size();
+    L.head = d_heads;
+    L.persistent = true;
+    L.persistent_grid = ctx->num_sms * 4;
+    return gotoh_launch(ctx, S, L, stream);
 }
 
 }  // namespace sad

@@ -109,6 +109,13 @@ struct TraceStage {
     int32_t count = 0;
 };
 
+// One traced interval: stage and its start and end in ms after the first
+// traced interval's start.
+struct TraceSpan {
+    int32_t stage;
+    double t0, t1;
+};
+
 }  // namespace sad
 
 struct sad_ctx {
@@ -131,6 +138,8 @@ struct sad_ctx {
     cudaEvent_t ev_join[8] = {};
     bool trace_on = false;
     sad::TraceStage trace[SAD_NUM_STAGES];
+    cudaEvent_t trace_origin = nullptr;      // begin event of the first interval since the last read
+    std::vector<sad::TraceSpan> timeline;    // intervals of the last read, by start time
     std::vector<cudaEvent_t> event_pool;
 };
 

@@ -86,6 +86,8 @@ def load():
         "sad_scores_get_variants": (ctypes.c_int, [P, P, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_trace_enable": (ctypes.c_int, [P, i32]),
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
+        "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
         "sad_pipeline": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), ctypes.POINTER(KmerParams), P, i32,
                                         i32, i32, ctypes.POINTER(RankOut), P, P, P, P, i64, i32, P]),
@@ -206,6 +208,20 @@ def trace_read(ctx=None) -> dict:
     cnt = (ctypes.c_int32 * len(STAGES))()
     _check(load().sad_trace_read(_ctx(ctx), ms, cnt, len(STAGES)))
     return {name: (ms[i], cnt[i]) for i, name in enumerate(STAGES)}
+
+
+def trace_timeline(ctx=None) -> list:
+    """[(stage, start ms, end ms)] of the intervals the last trace_read consumed,
+    in start order, relative to the first one's start."""
+    lib = load()
+    n = ctypes.c_int32(0)
+    _check(lib.sad_trace_timeline(_ctx(ctx), None, None, None, 0, ctypes.byref(n)))
+    m = n.value
+    st = (ctypes.c_int32 * max(m, 1))()
+    t0 = (ctypes.c_double * max(m, 1))()
+    t1 = (ctypes.c_double * max(m, 1))()
+    _check(lib.sad_trace_timeline(_ctx(ctx), st, t0, t1, m, ctypes.byref(n)))
+    return [(STAGES[st[i]], t0[i], t1[i]) for i in range(min(m, n.value))]
 
 
 def set_score_variants(table, ctx=None):
