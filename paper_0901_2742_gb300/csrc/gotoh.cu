@@ -21,6 +21,7 @@
 // is handed to the next strip through a per-group boundary buffer in global
 // memory. Per cell: two add-max (DPX), one add, one 3-way max (DPX), one add.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <numeric>
 
@@ -655,8 +656,12 @@ __host__ __device__ constexpr int pair_cols() {
 // group streams its subjects through one wavefront (stream_pair16); otherwise
 // one wavefront per subject, in strips (the two forms are separate kernels: in
 // one body their register needs add up).
+// Occupancy: 4 CTAs (16 warps) per SM up to R = 20 rows per lane, 3 above
+// (the R = 32 body fits 167 registers without spilling; at 2 CTAs per SM the
+// two interleaved column chains per lane left the DPX pipe waiting on
+// dependencies: N = 2000 scores 2.68 -> 2.57 ms with 3).
 template <int R, bool kStream>
-__global__ void __launch_bounds__(128, (R <= 20) ? 4 : ((R <= 24) ? 3 : 2))
+__global__ void __launch_bounds__(128, (R <= 20) ? 4 : 3)
 k_gotoh_pair16(const GotohItem* __restrict__ items, int32_t n_items, int32_t* __restrict__ head,
                GotohArgs a) {
     extern __shared__ __align__(16) uint32_t prof32[];
@@ -775,18 +780,40 @@ KernelFn pair16_kernel_for(int R, bool stream) {
 void plan_buckets(const std::vector<int32_t>& h_bo, const std::vector<int32_t>& h_order,
                   const std::vector<int32_t>& h_len, int32_t p, std::vector<int32_t>* srt,
                   std::vector<int64_t>* score_off) {
-    srt->assign(h_order.size(), 0);
+    const int32_t n = (int32_t)h_order.size();
+    srt->assign((size_t)n, 0);
     score_off->assign((size_t)p + 1, 0);
-    std::vector<uint64_t> key;
     for (int32_t b = 0; b < p; b++) {
-        const int32_t lo = h_bo[b], nb = h_bo[b + 1] - h_bo[b];
-        // (length, local position) packed in one integer: ascending length, ties by position
-        key.resize((size_t)nb);
-        for (int32_t u = 0; u < nb; u++) key[u] = ((uint64_t)(uint32_t)h_len[h_order[lo + u]] << 32) | (uint32_t)u;
-        std::sort(key.begin(), key.end());
-        int32_t* s = srt->data() + lo;
-        for (int32_t u = 0; u < nb; u++) s[u] = (int32_t)(key[u] & 0xffffffffu);
-        (*score_off)[b + 1] = (*score_off)[b] + (int64_t)nb * (nb + 1) / 2;
+        const int64_t nb = h_bo[b + 1] - h_bo[b];
+        (*score_off)[b + 1] = (*score_off)[b] + nb * (nb + 1) / 2;
+    }
+    int32_t maxlen = 0;
+    for (int32_t t = 0; t < n; t++) maxlen = std::max(maxlen, h_len[h_order[t]]);
+    if ((int64_t)maxlen > 4ll * n + 4096) {
+        // sparse length range: sort (length, position) keys per bucket
+        std::vector<uint64_t> key;
+        for (int32_t b = 0; b < p; b++) {
+            const int32_t lo = h_bo[b], nb = h_bo[b + 1] - h_bo[b];
+            key.resize((size_t)nb);
+            for (int32_t u = 0; u < nb; u++) key[u] = ((uint64_t)(uint32_t)h_len[h_order[lo + u]] << 32) | (uint32_t)u;
+            std::sort(key.begin(), key.end());
+            for (int32_t u = 0; u < nb; u++) (*srt)[lo + u] = (int32_t)(key[u] & 0xffffffffu);
+        }
+        return;
+    }
+    // two stable counting passes over the CSR positions: by length, then by
+    // bucket; inside a bucket that is ascending length, ties by local position
+    std::vector<int32_t> cnt((size_t)maxlen + 2, 0), by_len((size_t)n), bucket_of((size_t)n), next((size_t)p);
+    for (int32_t t = 0; t < n; t++) cnt[h_len[h_order[t]] + 1]++;
+    for (int32_t l = 0; l <= maxlen; l++) cnt[l + 1] += cnt[l];
+    for (int32_t t = 0; t < n; t++) by_len[cnt[h_len[h_order[t]]]++] = t;
+    for (int32_t b = 0; b < p; b++) {
+        next[b] = h_bo[b];
+        for (int32_t t = h_bo[b]; t < h_bo[b + 1]; t++) bucket_of[t] = b;
+    }
+    for (int32_t t : by_len) {
+        const int32_t b = bucket_of[t];
+        (*srt)[next[b]++] = t - h_bo[b];
     }
 }
 
@@ -999,13 +1026,25 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
     // longest first inside every variant
     std::vector<GotohItem> all;
     int32_t first[kNumVariants + 1];
-    std::vector<std::pair<double, int32_t>> ord;
+    // one counting pass per variant over 32 cost classes per octave, largest
+    // first, plan order inside a class (about 2 % resolution is enough to
+    // leave the shortest items for the end of the queue)
+    constexpr int kClasses = 32 * 64;
+    std::vector<int32_t> ccnt(kClasses + 1);
+    std::vector<int32_t> cls;
     for (int v = 0; v < kNumVariants; v++) {
         first[v] = (int32_t)all.size();
-        ord.resize(by_var[v].size());
-        for (size_t t = 0; t < ord.size(); t++) ord[t] = {-cost_var[v][t], (int32_t)t};
-        std::sort(ord.begin(), ord.end());  // largest cost first, ties in plan order
-        for (const auto& e : ord) all.push_back(by_var[v][e.second]);
+        const size_t nv = by_var[v].size();
+        cls.resize(nv);
+        std::fill(ccnt.begin(), ccnt.end(), 0);
+        for (size_t t = 0; t < nv; t++) {
+            const int c = (int)std::min<double>(kClasses - 1, std::max(0.0, 32.0 * std::log2(1.0 + cost_var[v][t])));
+            cls[t] = kClasses - 1 - c;  // descending cost
+            ccnt[cls[t] + 1]++;
+        }
+        for (int c = 0; c < kClasses; c++) ccnt[c + 1] += ccnt[c];
+        all.resize(first[v] + nv);
+        for (size_t t = 0; t < nv; t++) all[first[v] + ccnt[cls[t]]++] = by_var[v][t];
     }
     first[kNumVariants] = (int32_t)all.size();
     plan->first_single = (int32_t)all.size();
