@@ -34,10 +34,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gotoh GCUPS + k-mer sim pairs/s (exact vs oracle); N=2000,L≈316 wall time"
-OPS_PER_CELL = 5          # add-max, add-max, add, max3, add (32-bit DP)
+# DPX instructions per DP cell: add-max (E), add-max (F), 3-way max (H); the two
+# adds per cell are plain integer adds that also issue to the FMA pipe. The
+# packed kernels do one row of two problems per 16x2 instruction: 1.5 per cell.
+DPX_PER_CELL = 3
 SMS = 152
 SM_MAX_MHZ = 2070.0
-INT_OPS_PER_CLK_SM = 64   # measured: IADD3, VIADDMNMX, VIMNMX3 (32-bit and 16x2) each 64/clk/SM
+DPX_OPS_PER_CLK_SM = 64   # measured: VIADDMNMX and VIMNMX3 (32-bit and 16x2) each 64 lanes/clk/SM
+# DRAM bytes (read + write) of the packed score launches of one step of this
+# benchmark, summed from one ncu capture; reported while the score kernels'
+# source is the one that was measured (sha256 of csrc/gotoh.cu), else null.
+SCORE_TRAFFIC = {"bytes_per_step": 2253670,
+                 "gotoh_sha256": "9286463b967f0f7ef706c2a955eb2e301f228d17e3728e24a45156155d4b5822",
+                 "profile": "profiles/gotoh_pair16_n2000.md"}
 
 
 def plane_gemm_flops(n, k, kmer_alphabet, cap, num_sms=SMS):
@@ -57,6 +66,16 @@ def plane_gemm_flops(n, k, kmer_alphabet, cap, num_sms=SMS):
 
     bn = 256 if tiles(256) >= num_sms else 128
     return 2.0 * K * 128 * bn * tiles(bn)
+
+
+def score_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_0901_2742_gb300", "csrc", "gotoh.cu")
+    with open(path, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    if SCORE_TRAFFIC["bytes_per_step"] is None or h != SCORE_TRAFFIC["gotoh_sha256"]:
+        return None
+    return SCORE_TRAFFIC["bytes_per_step"]
 
 
 def measured_peaks():
@@ -313,6 +332,8 @@ def main():
                     help="0: uint8 CUDA-core k-mer path; >0 tensor-core planes; -1 sorted k-mer lists")
     ap.add_argument("--mode", type=int, default=1, help="0: per-bucket launches, 1: persistent")
     ap.add_argument("--no-tune", action="store_true", help="skip the per-length-bin variant autotuner")
+    ap.add_argument("--variants", default=None,
+                    help="fixed score-variant table instead of the autotuner: rows:R:G,... (rows ascending)")
     ap.add_argument("--global-samples", type=int, default=0,
                     help="s > 0: partition by the globalized rank against s samples per block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,7 +373,11 @@ def main():
     cells = workload_cells(w.lengths(), bo, od)
     pairs_scored = int(sum((bo[b + 1] - bo[b]) * (bo[b + 1] - bo[b] + 1) // 2 for b in range(p)))
     tuning = None
-    if args.mode == 1 and not args.no_tune:
+    t_tune = 0.0
+    if args.mode == 1 and args.variants:
+        tuning = [tuple(int(x) for x in v.split(":")) for v in args.variants.split(",")]
+        sad.set_score_variants(tuning)
+    elif args.mode == 1 and not args.no_tune:
         # pick the packed-kernel variant per query-length bin on this layout (outside the timed region)
         t_tune = time.perf_counter()
         tuning = sad.autotune_scores(res_d, offs_d, w.alphabet, out_d["bucket_offsets"],
@@ -402,9 +427,9 @@ def main():
     sc_ms, sc_n = trace["scores_packed"] if packed else trace["scores"]
     score_ms = sc_ms / max(sc_n, 1)
     score_launches_per_step = sc_n / args.steps
-    ops_per_cell = OPS_PER_CELL / 2 if packed else OPS_PER_CELL   # 16x2: one instruction, two cells
+    ops_per_cell = DPX_PER_CELL / 2 if packed else DPX_PER_CELL   # 16x2: one instruction, two cells
     achieved = ops_per_cell * cells / (sc_ms / args.steps * 1e-3) / 1e12
-    peak = SMS * INT_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = SMS * DPX_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
 
     # the k-mer all-pairs launch against the tensor-core peak (fp8: 2 x the measured bf16 burst)
     kmer_roofline = None
@@ -483,20 +508,22 @@ def main():
                    "parallelism": f"replicas x{ws}", "l2": "flushed between timed steps (256 MiB write)",
                    "score_variants": ([{"rows_le": u, "R": r, "G": g} for u, r, g in tuning]
                                       if tuning else "cost model"),
-                   "autotune_s": round(t_tune, 3) if tuning else None},
+                   "autotune_s": round(t_tune, 3) if tuning and not args.variants else None},
         "kmer_pairs_per_s": n * (n + 1) / 2 / (kmer_ms * 1e-3) if kmer_ms > 0 else None,
         "stage_ms": {k: v[0] / args.steps for k, v in trace.items()},
         "device_timeline": timeline,
         "pairs_scored": pairs_scored, "cells": cells,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32)",
-                     "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (DPX pipe)",
+                     "frac": achieved / peak, "traffic": (score_traffic() if packed else None),
                      "kernel": ("k_gotoh_pair16 (alignment scores, two problems per 16x2 lane)" if packed
                                 else "k_gotoh_items (alignment scores, 32-bit DP)"),
                      "kernel_ms": score_ms, "launches_per_step": score_launches_per_step,
                      "gcups": cells / (sc_ms / args.steps * 1e-3) / 1e9,
                      "peak_gcups": peak * 1e12 / ops_per_cell / 1e9,
-                     "peak_basis": f"{SMS} SMs x {INT_OPS_PER_CLK_SM} int ops/clk x {SM_MAX_MHZ:.0f} MHz; "
-                                   f"{ops_per_cell:g} instructions per cell"},
+                     "peak_basis": f"{SMS} SMs x {DPX_OPS_PER_CLK_SM} DPX lanes/clk x {SM_MAX_MHZ:.0f} MHz; "
+                                   f"{ops_per_cell:g} DPX instructions per cell (the adds issue to the FMA pipe too)",
+                     "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the score launches "
+                                      "of one step (" + SCORE_TRAFFIC["profile"] + ")"},
         "kmer_roofline": kmer_roofline,
         "gpu_launches": int(launches),
         "wall_s": wall,
