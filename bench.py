@@ -49,25 +49,6 @@ SCORE_TRAFFIC = {"bytes_per_step": 2253670,
                  "profile": "profiles/gotoh_pair16_n2000.md"}
 
 
-def plane_gemm_flops(n, k, kmer_alphabet, cap, num_sms=SMS):
-    """Tensor-core work of one all-pairs launch on the threshold planes: 2 K flops
-    per pair of every 128 x BN tile the kernel computes (the upper-triangle tiles;
-    BN = 256 when there are at least as many such tiles as SMs, else 128), with
-    K = cap * (kmer_alphabet^k rounded up to 64)."""
-    if cap <= 0 or n == 0:
-        return 0.0
-    V = kmer_alphabet ** k
-    K = cap * (-(-V // 64) * 64)
-    nti = -(-n // 128)
-
-    def tiles(bn):
-        ntj = -(-n // bn)
-        return sum(1 for ti in range(nti) for tj in range(ntj) if bn * tj + bn - 1 >= 128 * ti)
-
-    bn = 256 if tiles(256) >= num_sms else 128
-    return 2.0 * K * 128 * bn * tiles(bn)
-
-
 def score_traffic():
     import hashlib
     path = os.path.join(ROOT, "paper_0901_2742_gb300", "csrc", "gotoh.cu")
@@ -431,9 +412,10 @@ def main():
     achieved = ops_per_cell * cells / (sc_ms / args.steps * 1e-3) / 1e12
     peak = SMS * DPX_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
 
-    # the k-mer all-pairs launch against the tensor-core peak (fp8: 2 x the measured bf16 burst)
+    # the k-mer all-pairs launch against the tensor-core peak (fp8: 2 x the measured bf16 burst),
+    # counting the MMAs it issued (zero k-blocks of a panel are skipped)
     kmer_roofline = None
-    flops = plane_gemm_flops(n, w.k, w.kmer_alphabet, w.cap)
+    flops, dense_flops = (sad.kmer_gemm_work() if w.cap > 0 else (0, 0))
     ap_ms = trace["allpairs"][0] / max(trace["allpairs"][1], 1)
     peaks = measured_peaks()
     if flops > 0 and ap_ms > 0:
@@ -443,7 +425,8 @@ def main():
         kmer_roofline = {"bound": "tensor", "achieved": ach, "peak": peak_fp8, "unit": "TFLOP/s (fp8 e4m3)",
                          "frac": ach / peak_fp8, "traffic": None,
                          "kernel": "k_plane_gemm2 (threshold-plane GEMM, tcgen05 kind::f8f6f4, fused D sums)",
-                         "kernel_ms": ap_ms, "flops_per_launch": flops,
+                         "kernel_ms": ap_ms, "flops_per_launch": flops, "dense_flops_per_launch": dense_flops,
+                         "kblocks_run_frac": flops / dense_flops if dense_flops else None,
                          "peak_basis": ("2 x measured bf16 dense burst " + ("(MEASURED_PEAKS.json, of measured)"
                                         if peaks else "(fallback 1.9 PFLOP/s, of fallback)")),
                          "pairs_per_s": n * (n + 1) / 2 / (ap_ms * 1e-3)}

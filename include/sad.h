@@ -204,6 +204,14 @@ int sad_trace_timeline(sad_ctx* ctx, int32_t* stage, double* t0_ms, double* t1_m
 /* Number of kernels this library has launched in this process. */
 uint64_t sad_launch_count(void);
 
+/* Tensor-core work of the last threshold-plane GEMM that ctx ran (cap > 0):
+ * *mma_flops = 2 x 128 x 128 x (k-blocks x tile width) of the MMAs issued, and
+ * *dense_flops the same over every k-block of every tile. A tile skips the
+ * 128-byte k-blocks that are zero in all rows of its row or of its column
+ * panel (the planes of counts >= 3 are mostly zero); they add nothing, so the
+ * result is the same. Synchronises the device; host outputs. */
+int sad_kmer_gemm_work(sad_ctx* ctx, int64_t* mma_flops, int64_t* dense_flops);
+
 /* ---- stage 1: k-mer rank ----------------------------------------------- */
 
 /* All-pairs k-mer similarity and the rank keys (Section 2 equations r_ij,

@@ -21,20 +21,26 @@ constexpr int kCountThreads = 256;
 //   planes[i][(t-1)Vs + tau] = e4m3(1.0) if count >= t, t = 1..cap  (optional)
 //   sT[i]             = sum_tau min(count, T)
 //   excess list of i  = (tau, count - T) for count > T, ascending tau
+//   kbits[i / 128]   |= the nonzero 128-byte k-blocks of the plane row (optional)
 // T is the residual threshold: cap on the plane path, 255 on the uint8 path.
+constexpr int kMaxKBlockWords = (8 * SAD_MAX_KMER_SPACE / 128 + 31) / 32 + 1;
+
 __global__ void __launch_bounds__(kCountThreads)
 k_count(const uint8_t* __restrict__ res, const int64_t* __restrict__ pad_off,
         const int32_t* __restrict__ len, int32_t k, int32_t A2, int32_t Vs, ClassMap cm,
         int32_t T, int32_t cap, uint8_t* __restrict__ C8, uint8_t* __restrict__ planes,
         const int64_t* __restrict__ ex_off, int32_t* __restrict__ ex_tau,
-        int32_t* __restrict__ ex_val, int32_t* __restrict__ nex, uint32_t* __restrict__ sT) {
+        int32_t* __restrict__ ex_val, int32_t* __restrict__ nex, uint32_t* __restrict__ sT,
+        uint32_t* __restrict__ kbits, int32_t kbwords) {
     extern __shared__ uint32_t cnt[];  // Vs counters
     __shared__ int32_t warp_tot[kCountThreads / 32];
     __shared__ uint32_t red[kCountThreads / 32];
+    __shared__ uint32_t kbm[kMaxKBlockWords];  // this row's nonzero k-blocks
     const int32_t i = blockIdx.x;
     const int32_t L = len[i];
     const uint8_t* x = res + pad_off[i];
     for (int32_t t = threadIdx.x; t < Vs; t += blockDim.x) cnt[t] = 0;
+    for (int32_t t = threadIdx.x; t < kbwords; t += blockDim.x) kbm[t] = 0;
     __syncthreads();
     const int32_t nk = L - k + 1;
     for (int32_t pos = threadIdx.x; pos < nk; pos += blockDim.x) {
@@ -60,6 +66,10 @@ k_count(const uint8_t* __restrict__ res, const int64_t* __restrict__ pad_off,
                 const uint32_t w = (c0 >= tt ? 0x38u : 0u) | (c1 >= tt ? 0x3800u : 0u) |
                                    (c2 >= tt ? 0x380000u : 0u) | (c3 >= tt ? 0x38000000u : 0u);
                 *(uint32_t*)(prow + (int64_t)(t - 1) * Vs + t4) = w;
+                if (kbits && w) {
+                    const int32_t kb = ((t - 1) * Vs + t4) >> 7;
+                    atomicOr(&kbm[kb >> 5], 1u << (kb & 31));
+                }
             }
         }
     }
@@ -73,6 +83,9 @@ k_count(const uint8_t* __restrict__ res, const int64_t* __restrict__ pad_off,
         for (int q = 0; q < kCountThreads / 32; q++) s += red[q];
         sT[i] = s;
     }
+    if (kbits)
+        for (int32_t t = threadIdx.x; t < kbwords; t += blockDim.x)
+            if (kbm[t]) atomicOr(&kbits[(int64_t)(i >> 7) * kbwords + t], kbm[t]);
     if (!any_heavy) {
         if (threadIdx.x == 0) nex[i] = 0;
         return;
@@ -757,10 +770,20 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
                       stream, &c8));
     SparseLists L{(const uint2*)c8, (const int64_t*)(dm + o_loff), (const int32_t*)(dm + o_nd)};
     uint8_t* planes = nullptr;
+    KBlockMap kbm{nullptr, 0, 0};
+    uint32_t* kbm_bits = nullptr;
     if (cap > 0) {
         void* pl = nullptr;
         SAD_RET(workspace(ctx, WS_PLANES, (size_t)(nrows * (int64_t)cap * Vs), stream, &pl));
         planes = (uint8_t*)pl;
+        // nonzero k-blocks per 128-row panel, for the tensor-core tiles to skip zero ones
+        kbm.npanels = (int32_t)(nrows / 128);
+        kbm.kbwords = (int32_t)((((int64_t)cap * Vs + 127) / 128 + 31) / 32);
+        void* kb = nullptr;
+        SAD_RET(workspace(ctx, WS_KBLOCKS, 4ull * kbm.npanels * kbm.kbwords, stream, &kb));
+        kbm_bits = (uint32_t*)kb;
+        kbm.bits = kbm_bits;
+        SAD_CUDA(cudaMemsetAsync(kb, 0, 4ull * kbm.npanels * kbm.kbwords, stream));
         // padding rows beyond n stay zero for the tensor-core tiles
         if (nrows > n)
             SAD_CUDA(cudaMemsetAsync(planes + (int64_t)n * cap * Vs, 0,
@@ -784,7 +807,8 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
             SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_count));
         k_count<<<n, kCountThreads, smem, stream>>>(S.res, S.pad_off, S.len, k, A2, Vs, cm, T, cap,
                                                    (uint8_t*)c8, planes, (const int64_t*)(dm + o_exoff),
-                                                   ex_tau, ex_val, d_nex, d_sT);
+                                                   ex_tau, ex_val, d_nex, d_sT, kbm.bits ? kbm_bits : nullptr,
+                                                   kbm.kbwords);
         SAD_LAUNCHED();
     }
     k_heavy_index<<<1, 1024, 0, stream>>>(n, d_nex, d_hidx, d_hlist, d_H);
@@ -822,7 +846,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     if (sparse) {
         SAD_RET(sparse_allpairs(ctx, n, L, tab, nd_host.data(), V, out.dloc, out.dcen, out.A, stream));
     } else if (cap > 0) {
-        SAD_RET(allpairs_planes(ctx, n, cap * Vs, planes, tab, out.dloc, out.dcen, out.A, stream));
+        SAD_RET(allpairs_planes(ctx, n, cap * Vs, planes, kbm, tab, out.dloc, out.dcen, out.A, stream));
     } else {
         const int32_t ntiles = (int32_t)((n + kTile - 1) / kTile);
         const int64_t ntri = (int64_t)ntiles * (ntiles + 1) / 2;

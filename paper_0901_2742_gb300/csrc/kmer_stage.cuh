@@ -35,12 +35,26 @@ bool uses_sparse_path(const sad_kmer_params* kp);
 int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
                      const KmerOutDev& out, cudaStream_t stream);
 
+// Bitmap of the nonzero 128-byte k-blocks of every 128-row panel of the
+// threshold planes: bit kb of word kb / 32 of panel q, kbwords words per panel.
+struct KBlockMap {
+    const uint32_t* bits;
+    int32_t kbwords;
+    int32_t npanels;
+};
+
 // All-pairs similarity from e4m3 threshold planes (n rows of K bytes, rows
 // padded to a multiple of 128 with zeros) on the tensor cores, with the same
-// fixed-point epilogue as the CUDA-core path.
-int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes,
+// fixed-point epilogue as the CUDA-core path. With a k-block map, a tile skips
+// the k-blocks that are zero in its row or column panel (exact: they add 0).
+int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, const KBlockMap& kbm,
                     const SeqTables& tab, uint64_t* dloc, uint64_t* dcen, int32_t* A,
                     cudaStream_t stream);
+
+// Tensor-core work of the last plane GEMM of ctx: flops of the MMAs issued
+// (k-blocks run) and of every k-block of every tile (host values, read after
+// the launch completed; synchronises the device).
+int plane_gemm_work(sad_ctx* ctx, int64_t* mma_flops, int64_t* dense_flops);
 
 // ---- sorted-list (sparse) k-mer path ----------------------------------------
 // Per sequence i: lists[loff[i] + u], u < nd[i], holds (k-mer code, exact count)

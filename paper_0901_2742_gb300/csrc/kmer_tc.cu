@@ -282,14 +282,32 @@ __device__ __forceinline__ void mma_f8n(uint32_t d_tmem, uint64_t a, uint64_t b,
 // the fixed-point D terms while the next tile's MMAs run. A tile covers rows i0..i0+127 and columns j0..j0+BN-1; the pair (i, j)
 // is taken when i <= j (i < j: both D sums, i = j: its own), so every
 // unordered pair is counted exactly once whatever the tile shape.
+//
+// Zero k-blocks: a k-block adds nothing to a tile when its 128-byte slab is
+// zero in every row of the tile's row panel or of its column panel (kbm); the
+// producer and the MMA thread both skip such k-blocks by the same test, so they
+// stay in step. k-block 0 always runs (it initialises the accumulator). The
+// MMA thread adds the k-blocks it ran (x BN) to *work.
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int32_t n,
-              int32_t kblocks, const int2* __restrict__ tiles, int32_t ntiles, SeqTables tab,
+              int32_t kblocks, const int2* __restrict__ tiles, int32_t ntiles, SeqTables tab, KBlockMap kbm,
               uint64_t* __restrict__ dloc, uint64_t* __restrict__ dcen, int32_t* __restrict__ A,
-              uint32_t* __restrict__ status) {
+              unsigned long long* __restrict__ work, uint32_t* __restrict__ status) {
     constexpr int S = kStagesFor<BN>();
     constexpr uint32_t kA = kTM * kKB, kB = BN * kKB;
+    // the nonzero k-blocks of a tile: its row panel's and its column panels' bits, ANDed
+    auto tile_bits = [&](int32_t i0, int32_t j0, int32_t w) -> uint32_t {
+        if (!kbm.bits) return 0xffffffffu;
+        const uint32_t fa = kbm.bits[(int64_t)(i0 >> 7) * kbm.kbwords + w];
+        uint32_t fb = 0;
+#pragma unroll
+        for (int q = 0; q < BN / kTM; q++) {
+            const int32_t panel = (j0 >> 7) + q;
+            if (panel < kbm.npanels) fb |= kbm.bits[(int64_t)panel * kbm.kbwords + w];
+        }
+        return fa & fb;
+    };
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[S];
     __shared__ __align__(8) uint64_t empty[S];
@@ -336,7 +354,10 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             uint32_t g = 0;  // k-blocks issued so far
             for (int32_t t = blockIdx.x; t < ntiles && !aborted(); t += gridDim.x) {
                 const int32_t i0 = tiles[t].x * kTM, j0 = tiles[t].y * BN;
+                uint32_t bits = 0;
                 for (int32_t kb = 0; kb < kblocks; kb++) {
+                    if ((kb & 31) == 0) bits = tile_bits(i0, j0, kb >> 5);
+                    if (kb > 0 && !((bits >> (kb & 31)) & 1u)) continue;  // zero in a panel: adds nothing
                     const int s = (int)(g % S);
                     if (g >= (uint32_t)S && !mbar_wait(smem_u32(&empty[s]), ((g / S) + 1) & 1, status)) {
                         give_up();
@@ -368,9 +389,15 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t acc = tmem + (uint32_t)(a * BN);
-                for (int32_t kb = 0; kb < kblocks; kb++, g++) {
+                const int32_t i0 = tiles[t].x * kTM, j0 = tiles[t].y * BN;
+                uint32_t bits = 0, ran = 0;
+                for (int32_t kb = 0; kb < kblocks; kb++) {
+                    if ((kb & 31) == 0) bits = tile_bits(i0, j0, kb >> 5);
+                    if (kb > 0 && !((bits >> (kb & 31)) & 1u)) continue;  // the producer skips it too
                     const int s = (int)(g % S);
-                    if (!mbar_wait(smem_u32(&full[s]), (g / S) & 1, status)) {
+                    g++;
+                    ran++;
+                    if (!mbar_wait(smem_u32(&full[s]), ((g - 1) / S) & 1, status)) {
                         give_up();
                         break;
                     }
@@ -382,6 +409,7 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     mma_commit(smem_u32(&empty[s]));
                 }
                 mma_commit(smem_u32(&tfull[a]));
+                if (work) atomicAdd(work, (unsigned long long)ran * BN);
             }
         }
         __syncwarp();
@@ -504,8 +532,8 @@ int get_encoder() {
 
 }  // namespace
 
-int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, const SeqTables& tab,
-                    uint64_t* dloc, uint64_t* dcen, int32_t* A, cudaStream_t stream) {
+int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, const KBlockMap& kbm,
+                    const SeqTables& tab, uint64_t* dloc, uint64_t* dcen, int32_t* A, cudaStream_t stream) {
     if (n == 0) return SAD_OK;
     SAD_CHECK(K % 16 == 0, SAD_EINVAL, "plane row length %d is not a multiple of 16 bytes", K);
     SAD_RET(get_encoder());
@@ -527,8 +555,13 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
         for (int32_t tj = 0; tj < ntj; tj++)
             for (int32_t ti = ib; ti < std::min(nti, ib + 8); ti++)
                 if ((int64_t)BN * tj + BN - 1 >= (int64_t)kTM * ti) tiles.push_back(make_int2(ti, tj));
+    // tile list, then (256-byte aligned) the work counter of this launch
+    const size_t work_off = (size_t)round_up((int64_t)(sizeof(int2) * tiles.size()), 256);
     void* dt = nullptr;
-    SAD_RET(workspace(ctx, WS_GEMM_TILES, sizeof(int2) * tiles.size(), stream, &dt));
+    SAD_RET(workspace(ctx, WS_GEMM_TILES, work_off + 16, stream, &dt));
+    unsigned long long* work = (unsigned long long*)((char*)dt + work_off);
+    SAD_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream));
+    ctx->gemm_work = work;
     void* pin = nullptr;
     SAD_RET(pinned(ctx, sizeof(int2) * tiles.size(), stream, &pin));
     SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may feed an earlier copy
@@ -550,20 +583,40 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
     SAD_CHECK(cr == CUDA_SUCCESS, SAD_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     const int32_t kblocks = (K + kKB - 1) / kKB;
     const int32_t ntiles = (int32_t)tiles.size();
+    ctx->gemm_dense_units = (int64_t)ntiles * kblocks * BN;  // k-blocks x BN of every tile
     const int grid = std::min<int32_t>(ntiles, ctx->num_sms);
     if (BN == 256) {
         const size_t smem = (size_t)kStagesFor<256>() * (kTM + 256) * kKB + 1024;
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<256>));
         k_plane_gemm2<256><<<grid, kGemmThreads, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
-                                                        dloc, dcen, A, ctx->d_status);
+                                                        kbm, dloc, dcen, A, work, ctx->d_status);
     } else {
         const size_t smem = (size_t)kStagesFor<128>() * (kTM + 128) * kKB + 1024;
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<128>));
         k_plane_gemm2<128><<<grid, kGemmThreads, smem, stream>>>(tmA, tmB, n, kblocks, (const int2*)dt, ntiles, tab,
-                                                        dloc, dcen, A, ctx->d_status);
+                                                        kbm, dloc, dcen, A, work, ctx->d_status);
     }
     SAD_LAUNCHED();
     return SAD_OK;
 }
 
+int plane_gemm_work(sad_ctx* ctx, int64_t* mma_flops, int64_t* dense_flops) {
+    unsigned long long units = 0;
+    if (ctx->gemm_work) SAD_CUDA(cudaMemcpy(&units, ctx->gemm_work, sizeof(units), cudaMemcpyDeviceToHost));
+    // one k-block of one tile column: 2 x 128 rows x 128 bytes of K
+    *mma_flops = (int64_t)units * 2 * kTM * kKB;
+    *dense_flops = ctx->gemm_dense_units * 2 * kTM * kKB;
+    return SAD_OK;
+}
+
 }  // namespace sad
+
+extern "C" int sad_kmer_gemm_work(sad_ctx* ctx_in, int64_t* mma_flops, int64_t* dense_flops) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mma_flops && dense_flops, SAD_EINVAL, "an output pointer is NULL");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    return plane_gemm_work(ctx, mma_flops, dense_flops);
+}

@@ -80,6 +80,7 @@ enum Slot : int {
     WS_GLOBAL,         // block order of the globalized rank
     WS_TRACE,          // alignment (traceback) call: pairs, offsets, outputs
     WS_TRACE_DIRS,     // traceback direction words
+    WS_KBLOCKS,        // per 128-row panel of the planes: bitmap of nonzero 128-byte k-blocks
     WS_NUM_SLOTS
 };
 
@@ -141,6 +142,8 @@ struct sad_ctx {
     cudaEvent_t trace_origin = nullptr;      // begin event of the first interval since the last read
     std::vector<sad::TraceSpan> timeline;    // intervals of the last read, by start time
     std::vector<cudaEvent_t> event_pool;
+    unsigned long long* gemm_work = nullptr;  // device: k-blocks x BN the last plane GEMM ran
+    int64_t gemm_dense_units = 0;             // k-blocks x BN of all its tiles
 };
 
 namespace sad {

@@ -86,6 +86,7 @@ def load():
         "sad_scores_get_variants": (ctypes.c_int, [P, P, P, P, i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_trace_enable": (ctypes.c_int, [P, i32]),
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
+        "sad_kmer_gemm_work": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -222,6 +223,14 @@ def trace_timeline(ctx=None) -> list:
     t1 = (ctypes.c_double * max(m, 1))()
     _check(lib.sad_trace_timeline(_ctx(ctx), st, t0, t1, m, ctypes.byref(n)))
     return [(STAGES[st[i]], t0[i], t1[i]) for i in range(min(m, n.value))]
+
+
+def kmer_gemm_work(ctx=None) -> tuple:
+    """(flops of the MMAs the last threshold-plane GEMM issued, flops of all
+    its tiles' k-blocks): zero k-blocks of a panel are skipped."""
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().sad_kmer_gemm_work(_ctx(ctx), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def set_score_variants(table, ctx=None):

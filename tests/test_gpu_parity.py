@@ -261,13 +261,38 @@ def test_planes_caps_and_residuals(sad, cap):
 
 
 def test_planes_paper_scale(sad):
-    """N = 2000, cap 4, K = 4 x 8000: ragged last tile row, 136 tiles."""
+    """N = 2000, cap 4, K = 4 x 8000: ragged last tile row, 136 tiles. Most
+    k-blocks of the count >= 3 and >= 4 planes are zero in a panel and are
+    skipped; the result is the oracle's all the same."""
     w = synth.workload(3)
     want = oracle_all(w, "cfg2")
     r, pt, so, sc = run_gpu(sad, w, 1)
     assert_rank_equal(r, want[0])
     np.testing.assert_array_equal(pt["order"], want[1]["order"])
     np.testing.assert_array_equal(sc, want[3])
+    mma, dense = sad.kmer_gemm_work()
+    assert dense == 136 * 250 * 2 * 128 * 128 * 128
+    assert 0 < mma < dense
+
+
+def test_planes_skip_only_zero_kblocks(sad):
+    """Counts up to 6 in a few rows of different panels, 1 elsewhere: the
+    k-blocks of the high planes are nonzero in some panels only, so some tiles
+    run them and some skip them; every D sum and key stays the oracle's."""
+    rng = np.random.default_rng(77)
+    seqs = []
+    for i in range(300):
+        L = int(rng.integers(40, 200))
+        s = list(rng.integers(0, 20, L))
+        if i % 97 == 5:  # a repeat: one 3-mer many times
+            s[:18] = [3, 7, 11] * 6
+        seqs.append(s)
+    res, offs = synth.pack(seqs)
+    want = oracle.kmer_rank(res, offs, 20, 3, 4, want_A=True)
+    got = sad.kmer_rank(res, offs, 20, 3, 4, cap=4, want_A=True)
+    assert_rank_equal(got, want)
+    mma, dense = sad.kmer_gemm_work()
+    assert 0 < mma < dense
 
 
 def test_planes_compressed_alphabet(sad):
