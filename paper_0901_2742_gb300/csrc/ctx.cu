@@ -262,7 +262,9 @@ int prepare_seqs(sad_ctx* ctx, const sad_seqset* s, int32_t mem, cudaStream_t st
     int32_t* d_len = (int32_t*)(d_pad + n + 1);
     void* pin = nullptr;
     SAD_RET(pinned(ctx, meta_bytes, stream, &pin));
-    SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may still feed a previous copy
+    // the pinned area may still feed a previous copy (with device offsets the
+    // stream was synchronised just above, reading them)
+    if (mem == SAD_MEM_HOST) SAD_CUDA(cudaStreamSynchronize(stream));
     memcpy(pin, pad.data(), sizeof(int64_t) * (n + 1));
     memcpy((char*)pin + sizeof(int64_t) * (n + 1), out->h_len.data(), sizeof(int32_t) * n);
     SAD_CUDA(cudaMemcpyAsync(meta, pin, sizeof(int64_t) * (n + 1) + sizeof(int32_t) * n,

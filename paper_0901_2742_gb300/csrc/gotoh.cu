@@ -909,13 +909,6 @@ int variant_index(int R, int G) {
     return -1;
 }
 
-// Cost estimate (instruction slots) of one subject of length n for a query
-// pair of `rows` rows under variant (R, G).
-double packed_cost(int32_t rows, double n, int R, int G) {
-    const int32_t strip_h = R * G;
-    const int32_t strips = (rows + strip_h - 1) / strip_h;
-    return (double)strips * G * (n + G + 1) * (5.0 * R + 16.0) + strips * G * 40.0;
-}
 
 int ensure_aux_streams(sad_ctx* ctx) {
     if (ctx->aux_ready) return SAD_OK;
@@ -954,60 +947,90 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
                  const std::vector<int32_t>& h_order, const std::vector<int32_t>& srt, PackedPlan* plan) {
     const int32_t p = (int32_t)h_bo.size() - 1;
     auto len_at = [&](int32_t b, int32_t pos) { return S.h_len[h_order[h_bo[b] + srt[h_bo[b] + pos]]]; };
-    std::vector<GotohItem> by_var[kNumVariants];
-    std::vector<double> cost_var[kNumVariants];
+    // per variant: strip height and the most strips whose profile fits in shared memory
+    int32_t vsh[kNumVariants], vmax_strips[kNumVariants];
+    for (int v = 0; v < kNumVariants; v++) {
+        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+        vsh[v] = R * G;
+        vmax_strips[v] = (int32_t)(ctx->smem_optin / ((size_t)S.alphabet * 4 * G * rpad_rt(R)));
+    }
+    const ScoreTuning& tu = ctx->tuning;
+    const int fv = tu.filter ? variant_index(tu.force_R, tu.force_G) : -1;
+    // per-thread scratch kept across calls (no allocation once warm)
+    thread_local std::vector<GotohItem> by_var[kNumVariants];
+    thread_local std::vector<double> cost_var[kNumVariants];
+    for (int v = 0; v < kNumVariants; v++) {
+        by_var[v].clear();
+        cost_var[v].clear();
+    }
     int32_t rows_var[kNumVariants] = {0};
     std::vector<GotohItem> singles;  // single-query items for the 32-bit kernel
     int32_t singles_rows = 0;
-    std::vector<int64_t> pre;  // prefix sums of the bucket's lengths in length order
+    // the table's variant per bin (or -1)
+    int bin_v[ScoreTuning::kMaxBins];
+    for (int t = 0; t < tu.nbins; t++) bin_v[t] = variant_index(tu.R[t], tu.G[t]);
+    // per variant for a pair of `rows` rows: whether its profile fits, and the
+    // estimated instruction slots of one subject of length n, ca n + cb =
+    // strips G ((n + G + 1)(5 R + 16) + 40): every strip runs n + G + 1 steps on
+    // G lanes of 5R + 16 instructions, plus a fixed cost per strip and lane
+    auto variant_cost = [&](int v, int32_t rows1, double* ca, double* cb) {
+        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+        const int32_t strips = (rows1 + vsh[v] - 1) / vsh[v];
+        const double k = (double)strips * G;
+        *ca = k * (5.0 * R + 16.0);
+        *cb = k * ((G + 1) * (5.0 * R + 16.0) + 40.0);
+        return strips <= vmax_strips[v];
+    };
+    thread_local std::vector<int32_t> lens;  // the bucket's lengths in length order
+    thread_local std::vector<int64_t> pre;   // and their prefix sums
     for (int32_t b = 0; b < p; b++) {
         const int32_t nb = h_bo[b + 1] - h_bo[b];
+        lens.resize((size_t)nb);
         pre.assign((size_t)nb + 1, 0);
-        for (int32_t v = 0; v < nb; v++) pre[v + 1] = pre[v] + len_at(b, v);
+        for (int32_t v = 0; v < nb; v++) {
+            lens[v] = len_at(b, v);
+            pre[v + 1] = pre[v] + lens[v];
+        }
         for (int32_t qp = 0; 2 * qp < nb; qp++) {
-            const int32_t m1 = len_at(b, 2 * qp);
-            const int32_t m2 = (2 * qp + 1 < nb) ? len_at(b, 2 * qp + 1) : 0;
+            const int32_t m1 = lens[2 * qp];
+            const int32_t m2 = (2 * qp + 1 < nb) ? lens[2 * qp + 1] : 0;
             const int32_t rows = std::max(m1, m2);
+            const int32_t rows1 = std::max(rows, 1);
+            if (tu.filter && (rows <= tu.lo || rows > tu.hi)) continue;  // autotuning: one length bin
+            // the variant of this pair: the forced one (autotuning), the table's, or
+            // per chunk the cost model's (every variant's cost, computed only then)
+            int fixed_v = -1;
+            double fa = 0, fb = 0;
+            if (tu.filter) {
+                if (fv < 0 || !variant_cost(fv, rows1, &fa, &fb)) {
+                    ctx->tuning.skipped = true;  // this variant cannot serve the whole bin
+                    continue;
+                }
+                fixed_v = fv;
+            } else {
+                int tv = -1;
+                for (int t = 0; t < tu.nbins && tv < 0; t++)
+                    if (rows <= tu.upper[t]) tv = bin_v[t];
+                if (tv >= 0 && variant_cost(tv, rows1, &fa, &fb)) fixed_v = tv;
+            }
+            bool fit[kNumVariants];
+            double ca[kNumVariants], cb[kNumVariants];
+            if (fixed_v < 0)
+                for (int v = 0; v < kNumVariants; v++) fit[v] = variant_cost(v, rows1, &ca[v], &cb[v]);
             for (int32_t v0 = 2 * qp; v0 < nb; v0 += kChunkSubjects) {
                 const int32_t v1 = std::min(nb, v0 + kChunkSubjects);
                 const double navg = (double)(pre[v1] - pre[v0]) / (v1 - v0);
-                // the packed profile of the pair must fit in shared memory
-                auto fits = [&](int v) {
-                    const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
-                    const int64_t words = round_up(std::max(rows, 1), (int64_t)R * G) / R * rpad_rt(R);
-                    return (size_t)S.alphabet * words * 4 <= ctx->smem_optin;
-                };
-                int best = -1;
-                double bc = 1e300;
-                const ScoreTuning& tu = ctx->tuning;
-                if (tu.filter) {
-                    // autotuning: one length bin, one forced variant, nothing else
-                    const int fv = variant_index(tu.force_R, tu.force_G);
-                    if (rows <= tu.lo || rows > tu.hi) continue;
-                    if (fv < 0 || !fits(fv)) {
-                        ctx->tuning.skipped = true;  // this variant cannot serve the whole bin
-                        continue;
-                    }
-                    by_var[fv].push_back(GotohItem{b, qp, v0, v1});
-                    cost_var[fv].push_back(packed_cost(std::max(rows, 1), navg, tu.force_R, tu.force_G) * (v1 - v0));
-                    rows_var[fv] = std::max(rows_var[fv], rows);
-                    continue;
-                }
-                for (int t = 0; t < tu.nbins && best < 0; t++)
-                    if (rows <= tu.upper[t]) best = variant_index(tu.R[t], tu.G[t]);
-                if (best >= 0 && fits(best)) {
-                    bc = packed_cost(std::max(rows, 1), navg, kPackedR[best / kNumG], kPackedG[best % kNumG]);
-                } else {
-                    best = -1;
-                    for (int ri = 0; ri < kNumR; ri++)
-                        for (int gi = 0; gi < kNumG; gi++) {
-                            if (!fits(ri * kNumG + gi)) continue;
-                            const double c = packed_cost(std::max(rows, 1), navg, kPackedR[ri], kPackedG[gi]);
-                            if (c < bc) {
-                                bc = c;
-                                best = ri * kNumG + gi;
-                            }
+                int best = fixed_v;
+                double bc = best >= 0 ? fa * navg + fb : 1e300;
+                if (best < 0) {
+                    for (int v = 0; v < kNumVariants; v++) {
+                        if (!fit[v]) continue;
+                        const double c = ca[v] * navg + cb[v];
+                        if (c < bc) {
+                            bc = c;
+                            best = v;
                         }
+                    }
                 }
                 if (best < 0) {
                     // too long for any packed profile: both queries go to the 32-bit kernel
@@ -1023,28 +1046,35 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
             }
         }
     }
-    // longest first inside every variant
+    // longest first inside every variant: one counting pass over 32 cost classes
+    // per octave (exponent and top five mantissa bits of the cost), largest first,
+    // plan order inside a class (about 3 % resolution is enough to leave the
+    // shortest items for the end of the queue)
     std::vector<GotohItem> all;
+    all.reserve(plan->all.capacity());
     int32_t first[kNumVariants + 1];
-    // one counting pass per variant over 32 cost classes per octave, largest
-    // first, plan order inside a class (about 2 % resolution is enough to
-    // leave the shortest items for the end of the queue)
-    constexpr int kClasses = 32 * 64;
-    std::vector<int32_t> ccnt(kClasses + 1);
-    std::vector<int32_t> cls;
+    thread_local std::vector<int32_t> ccnt;
+    thread_local std::vector<int32_t> cls;
     for (int v = 0; v < kNumVariants; v++) {
         first[v] = (int32_t)all.size();
         const size_t nv = by_var[v].size();
+        if (nv == 0) continue;
         cls.resize(nv);
-        std::fill(ccnt.begin(), ccnt.end(), 0);
+        int32_t cmin = INT32_MAX, cmax = -1;
         for (size_t t = 0; t < nv; t++) {
-            const int c = (int)std::min<double>(kClasses - 1, std::max(0.0, 32.0 * std::log2(1.0 + cost_var[v][t])));
-            cls[t] = kClasses - 1 - c;  // descending cost
-            ccnt[cls[t] + 1]++;
+            uint64_t bits;
+            const double x = 1.0 + cost_var[v][t];
+            memcpy(&bits, &x, sizeof(bits));
+            const int32_t c = (int32_t)(bits >> 47);  // 11 exponent bits, 5 mantissa bits
+            cls[t] = c;
+            cmin = std::min(cmin, c);
+            cmax = std::max(cmax, c);
         }
-        for (int c = 0; c < kClasses; c++) ccnt[c + 1] += ccnt[c];
+        ccnt.assign((size_t)(cmax - cmin) + 2, 0);
+        for (size_t t = 0; t < nv; t++) ccnt[(size_t)(cmax - cls[t]) + 1]++;  // descending cost
+        for (int32_t c = 0; c <= cmax - cmin; c++) ccnt[c + 1] += ccnt[c];
         all.resize(first[v] + nv);
-        for (size_t t = 0; t < nv; t++) all[first[v] + ccnt[cls[t]]++] = by_var[v][t];
+        for (size_t t = 0; t < nv; t++) all[first[v] + ccnt[cmax - cls[t]]++] = by_var[v][t];
     }
     first[kNumVariants] = (int32_t)all.size();
     plan->first_single = (int32_t)all.size();

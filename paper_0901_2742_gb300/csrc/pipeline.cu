@@ -66,6 +66,24 @@ extern "C" int sad_pipeline(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_k
         d.G = (uint64_t*)(c + o_G);
         d.samples = (int32_t*)(c + o_smp);
     }
+    // device outputs: the stages write the caller's arrays directly (nothing to copy at the end)
+    const bool direct = mem == SAD_MEM_DEVICE;
+    if (direct) {
+        dbo = bucket_offsets;
+        if (n) dord = order;
+        dso = score_offsets;
+        if (rank) {
+            // (arrays of n entries only for n > 0: the stage writes one element of an empty set)
+            if (rank->dloc && n) d.dloc = (uint64_t*)rank->dloc;
+            if (rank->dcen && n) d.dcen = (uint64_t*)rank->dcen;
+            if (rank->la) d.la = rank->la;
+            if (rank->ga) d.ga = rank->ga;
+            if (rank->key_a && n) d.key_a = rank->key_a;
+            if (rank->key_b && n) d.key_b = rank->key_b;
+            if (gs > 0 && rank->G && n) d.G = (uint64_t*)rank->G;
+            if (gs > 0 && rank->sample_idx) d.samples = rank->sample_idx;
+        }
+    }
     SAD_RET(kmer_rank_device(ctx, S, params, d, stream));
     if (gs > 0)
         SAD_RET(partition_keys64_device(ctx, n, d.G, p, dbo, dord, nullptr, stream));
@@ -92,16 +110,18 @@ extern "C" int sad_pipeline(sad_ctx* ctx_in, const sad_seqset* seqs, const sad_k
     const int rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend, mode, dso,
                                         dsc, scores_capacity, &total, stream);
     const cudaMemcpyKind k = mem == SAD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    SAD_CUDA(cudaMemcpyAsync(score_offsets, dso, 8ull * (p + 1), k, stream));
-    SAD_CUDA(cudaMemcpyAsync(bucket_offsets, dbo, 4ull * (p + 1), k, stream));
-    if (n) SAD_CUDA(cudaMemcpyAsync(order, dord, 4ull * n, k, stream));
+    if (!direct) {
+        SAD_CUDA(cudaMemcpyAsync(score_offsets, dso, 8ull * (p + 1), k, stream));
+        SAD_CUDA(cudaMemcpyAsync(bucket_offsets, dbo, 4ull * (p + 1), k, stream));
+        if (n) SAD_CUDA(cudaMemcpyAsync(order, dord, 4ull * n, k, stream));
+    }
     if (rc != SAD_OK) {
         cudaStreamSynchronize(stream);
         return rc;
     }
     if (mem == SAD_MEM_HOST && total > 0)
         SAD_CUDA(cudaMemcpyAsync(scores, dsc, 4ull * total, k, stream));
-    if (rank) {
+    if (rank && !direct) {
         if (rank->dloc) SAD_CUDA(cudaMemcpyAsync(rank->dloc, d.dloc, 8ull * n, k, stream));
         if (rank->dcen) SAD_CUDA(cudaMemcpyAsync(rank->dcen, d.dcen, 8ull * n, k, stream));
         if (rank->la) SAD_CUDA(cudaMemcpyAsync(rank->la, d.la, 4ull * p, k, stream));
