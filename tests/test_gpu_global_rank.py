@@ -123,8 +123,10 @@ def test_partition_keys64_extreme_keys(sad):
         np.testing.assert_array_equal(got["order"], want["order"])
 
 
-def test_pipeline_globalized_matches_oracle(sad):
-    """The pipeline with global_samples partitions by G and scores those buckets."""
+@pytest.mark.parametrize("mem", ["host", "device"])
+def test_pipeline_globalized_matches_oracle(sad, mem):
+    """The pipeline with global_samples partitions by G and scores those buckets
+    (with device arrays the stages write G and the sample slots in place)."""
     w = synth.workload(2)
     s = w.p - 1
     r = oracle.kmer_rank(w.residues, w.offsets, w.alphabet, w.k, w.p, want_A=False)
@@ -132,8 +134,13 @@ def test_pipeline_globalized_matches_oracle(sad):
     pt = oracle.partition_keys64(G, w.p)
     so, sc = oracle.bucket_pair_scores(w.residues, w.offsets, pt["bucket_offsets"], pt["order"], w.subst,
                                        w.gap_open, w.gap_extend)
-    o = sad.pipeline(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend, mode=1,
+    res, offs = w.residues, w.offsets
+    if mem == "device":
+        import torch
+        res, offs = torch.from_numpy(res).cuda(), torch.from_numpy(offs).cuda()
+    o = sad.pipeline(res, offs, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend, mode=1,
                      global_samples=s)
+    o = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in o.items()}
     np.testing.assert_array_equal(o["G"][:w.n], G)
     np.testing.assert_array_equal(o["sample_idx"], smp)
     np.testing.assert_array_equal(o["bucket_offsets"], pt["bucket_offsets"])
