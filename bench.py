@@ -41,6 +41,9 @@ DPX_PER_CELL = 3
 SMS = 152
 SM_MAX_MHZ = 2070.0
 DPX_OPS_PER_CLK_SM = 64   # measured: VIADDMNMX and VIMNMX3 (32-bit and 16x2) each 64 lanes/clk/SM
+# measured ceiling of the packed row mix itself (3 DPX + 2 adds per row of two
+# cells, independent chains, every SM busy): 18.7 rows/clk/SM on this GPU
+MIX_ROWS_PER_CLK_SM = 18.7
 # DRAM bytes (read + write) of the packed score launches of one step of this
 # benchmark, summed from one ncu capture; reported while the score kernels'
 # source is the one that was measured (sha256 of the device code of
@@ -508,6 +511,9 @@ def main():
                      "kernel_ms": score_ms, "launches_per_step": score_launches_per_step,
                      "gcups": cells / (sc_ms / args.steps * 1e-3) / 1e9,
                      "peak_gcups": peak * 1e12 / ops_per_cell / 1e9,
+                     "mix_peak_gcups": (2 * MIX_ROWS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e9) if packed else None,
+                     "frac_of_mix_peak": ((cells / (sc_ms / args.steps * 1e-3)) /
+                                          (2 * MIX_ROWS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6)) if packed else None,
                      "peak_basis": f"{SMS} SMs x {DPX_OPS_PER_CLK_SM} DPX lanes/clk x {SM_MAX_MHZ:.0f} MHz; "
                                    f"{ops_per_cell:g} DPX instructions per cell (the adds issue to the FMA pipe too)",
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the score launches "
