@@ -14,6 +14,8 @@ Functions follow the paper:
   align               one optimal alignment (traceback through the same tables)
   alignment_score     the score of a given alignment, from its columns
   bucket_pair_scores  all pairs u <= v inside every bucket
+  guide_trees         average-linkage (UPGMA) tree of every bucket from its
+                      pair scores, the progressive aligner's first step
 
 Parity status: every function here is pinned by tests that do not reuse this
 code (brute-force alignment enumeration, sorted-list k-mer intersection,
@@ -69,6 +71,7 @@ def _bind(lib):
     lib.orc_alignment_score.argtypes = [P, i32, P, i32, P, i32, P, i32, i32, i32, P]
     lib.orc_bucket_pair_scores.restype = ctypes.c_int
     lib.orc_bucket_pair_scores.argtypes = [P, P, i32, P, P, i32, P, i32, i32, i32, i32, P, P]
+    lib.orc_guide_trees.argtypes = [P, i32, P, P, P, P, P, P, P]
     return lib
 
 
@@ -249,6 +252,24 @@ def bucket_pair_scores(residues, offsets, bucket_offsets, order, subst, gap_open
     if rc != 0:
         raise ValueError("oracle bucket_pair_scores: invalid arguments")
     return so, scores[:total]
+
+
+def guide_trees(bucket_offsets, score_offsets, scores, lib=None):
+    """Average-linkage guide tree of every bucket (see oracle.cpp): returns
+    dict(merge_offsets int64[p+1], left, right int32[M], num, den int64[M]); in
+    bucket b merge k joins clusters left < right into nb + k at distance num/den."""
+    lib = lib or _load()
+    bo = _c(bucket_offsets, np.int32)
+    so, sc = _c(score_offsets, np.int64), _c(scores, np.int32)
+    p = len(bo) - 1
+    nb = np.diff(bo).astype(np.int64)
+    M = int(np.maximum(nb - 1, 0).sum())
+    mo = np.zeros(p + 1, np.int64)
+    left, right = np.zeros(max(M, 1), np.int32), np.zeros(max(M, 1), np.int32)
+    num, den = np.zeros(max(M, 1), np.int64), np.zeros(max(M, 1), np.int64)
+    lib.orc_guide_trees(_ptr(bo), p, _ptr(so), _ptr(sc if sc.size else np.zeros(1, np.int32)), _ptr(mo),
+                        _ptr(left), _ptr(right), _ptr(num), _ptr(den))
+    return {"merge_offsets": mo, "left": left[:M], "right": right[:M], "num": num[:M], "den": den[:M]}
 
 
 def tri_index(u: int, v: int, nb: int) -> int:

@@ -27,6 +27,12 @@
  *   - per-bucket all-pairs global alignment scores with affine gaps (Gotoh),
  *     the aligner each processor runs on its bucket (Section 2.3.3; the paper
  *     allows any sequential aligner), as the textbook three-state recursion.
+ *   - per-bucket guide tree, the first step of the progressive aligner that
+ *     runs on each bucket (Section 2.3.3): average linkage (UPGMA) on the
+ *     integer distances d_uv = S_uu + S_vv - 2 S_uv of the bucket's scores,
+ *     the distance of two clusters being the pair sum over the product of
+ *     their sizes, compared as exact rationals; ties go to the lexicographically
+ *     smallest pair of cluster ids (leaves 0..nb-1, merge k creates nb + k).
  */
 #include <algorithm>
 #include <atomic>
@@ -536,6 +542,76 @@ int orc_bucket_pair_scores(const uint8_t* res, const int64_t* offs, int32_t n,
             scores[score_offsets[b] + u * nb - u * (u - 1) / 2 + (v - u)] = (int32_t)s;
         }
     });
+    return 0;
+}
+
+/* Average-linkage guide tree of every bucket from its pair scores (layout of
+ * orc_bucket_pair_scores). merge_offsets: p+1 (filled; bucket b's merges are
+ * [merge_offsets[b], merge_offsets[b+1]), nb - 1 of them when nb >= 1). Merge k
+ * of a bucket joins clusters left < right into cluster nb + k at distance
+ * num / den (num = sum of d_uv over the pairs between the two clusters, den =
+ * the product of their sizes). Plain O(nb^3): every step scans every pair of
+ * live clusters. Returns 0. */
+int orc_guide_trees(const int32_t* bucket_offsets, int32_t p, const int64_t* score_offsets,
+                    const int32_t* scores, int64_t* merge_offsets, int32_t* left, int32_t* right,
+                    int64_t* num, int64_t* den) {
+    merge_offsets[0] = 0;
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bucket_offsets[b + 1] - bucket_offsets[b];
+        merge_offsets[b + 1] = merge_offsets[b] + (nb > 0 ? nb - 1 : 0);
+    }
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bucket_offsets[b + 1] - bucket_offsets[b];
+        if (nb < 2) continue;
+        const int32_t* sc = scores + score_offsets[b];
+        auto S = [&](int64_t u, int64_t v) {  // u <= v
+            return (int64_t)sc[u * nb - u * (u - 1) / 2 + (v - u)];
+        };
+        // clusters: id, size, alive; W[i][j] = sum of d over member pairs of clusters i, j
+        const int64_t cap = 2 * nb - 1;
+        std::vector<int64_t> size(cap, 0);
+        std::vector<char> alive(cap, 0);
+        std::vector<std::vector<int64_t>> W(cap, std::vector<int64_t>(cap, 0));
+        for (int64_t u = 0; u < nb; u++) {
+            size[u] = 1;
+            alive[u] = 1;
+            for (int64_t v = 0; v < nb; v++)
+                if (u != v) W[u][v] = S(u, u) + S(v, v) - 2 * S(std::min(u, v), std::max(u, v));
+        }
+        for (int64_t k = 0; k < nb - 1; k++) {
+            int64_t bi = -1, bj = -1;
+            for (int64_t i = 0; i < nb + k; i++) {
+                if (!alive[i]) continue;
+                for (int64_t j = i + 1; j < nb + k; j++) {
+                    if (!alive[j]) continue;
+                    if (bi < 0) {
+                        bi = i;
+                        bj = j;
+                        continue;
+                    }
+                    // W[i][j] / (size_i size_j) < W[bi][bj] / (size_bi size_bj), exactly
+                    const __int128 lhs = (__int128)W[i][j] * (size[bi] * size[bj]);
+                    const __int128 rhs = (__int128)W[bi][bj] * (size[i] * size[j]);
+                    if (lhs < rhs) {  // on equality the pair met first (smaller ids) stays
+                        bi = i;
+                        bj = j;
+                    }
+                }
+            }
+            const int64_t c = nb + k, m = merge_offsets[b] + k;
+            left[m] = (int32_t)bi;
+            right[m] = (int32_t)bj;
+            num[m] = W[bi][bj];
+            den[m] = size[bi] * size[bj];
+            size[c] = size[bi] + size[bj];
+            alive[c] = 1;
+            alive[bi] = alive[bj] = 0;
+            for (int64_t x = 0; x < c; x++) {
+                if (!alive[x]) continue;
+                W[c][x] = W[x][c] = W[bi][x] + W[bj][x];
+            }
+        }
+    }
     return 0;
 }
 

@@ -36,6 +36,10 @@ MUTANTS = {
     "bucket by pivots <= key": ("if (less(s, i)) c++;", "if (!less(i, s)) c++;"),
     "key denominator ignores GA": ("int64_t b = denom(len[i], len[g], k);", "int64_t b = denom(len[i], len[i], k);"),
     "self term dropped": ("for (int32_t j = 0; j < n; j++) {\n            int64_t a", "for (int32_t j = 0; j < n; j++) {\n            if (j == i) continue;\n            int64_t a"),
+    "tree distance with one self score": ("W[u][v] = S(u, u) + S(v, v) - 2 * S(", "W[u][v] = 2 * S(u, u) - 2 * S("),
+    "tree comparison without sizes": ("const __int128 lhs = (__int128)W[i][j] * (size[bi] * size[bj]);", "const __int128 lhs = (__int128)W[i][j];"),
+    "tree tie to the last pair": ("if (lhs < rhs) {  // on equality", "if (lhs <= rhs) {  // on equality"),
+    "tree merge sums one child": ("W[c][x] = W[x][c] = W[bi][x] + W[bj][x];", "W[c][x] = W[x][c] = 2 * W[bi][x];"),
 }
 
 
@@ -89,6 +93,53 @@ def battery(lib):
         check_partition(ka, kb, 7, oracle.partition(ka, kb, 7, lib=lib))
     except AssertionError:
         failed.append("partition properties")
+    # 5. guide trees: golden examples and the mean-over-member-pairs invariant
+    with open(os.path.join(GOLD, "guide_tree_tiny.json")) as f:
+        for c in json.load(f)["cases"][:2]:
+            nb = int(round((np.sqrt(8 * len(c["scores"]) + 1) - 1) / 2))
+            t = oracle.guide_trees(np.array([0, nb], np.int32), np.array([0, len(c["scores"])]),
+                                   np.array(c["scores"], np.int32), lib=lib)
+            if any(t[f].tolist() != c[f] for f in ("left", "right", "num", "den")):
+                failed.append("golden guide tree " + c["name"])
+    nb = 9
+    rs = np.random.default_rng(5)
+    sc = rs.integers(-30, 30, nb * (nb + 1) // 2).astype(np.int32)
+    t = oracle.guide_trees(np.array([0, nb], np.int32), np.array([0, len(sc)]), sc, lib=lib)
+    S = {}
+    for (u, v), x in zip([(u, v) for u in range(nb) for v in range(u, nb)], sc):
+        S[u, v] = S[v, u] = int(x)
+    members = {i: [i] for i in range(nb)}
+    for m in range(nb - 1):
+        a, c = int(t["left"][m]), int(t["right"][m])
+        if a not in members or c not in members:
+            failed.append("guide tree structure")
+            break
+        pairs = [(u, v) for u in members[a] for v in members[c]]
+        if t["num"][m] != sum(S[u, u] + S[v, v] - 2 * S[u, v] for u, v in pairs) or t["den"][m] != len(pairs):
+            failed.append("guide tree member pairs")
+            break
+        members[nb + m] = members.pop(a) + members.pop(c)
+    # 6. guide tree against scipy's average linkage (tie-free distances)
+    try:
+        from scipy.cluster.hierarchy import linkage
+    except ImportError:
+        linkage = None
+    if linkage is not None:
+        nb = 24
+        vals = np.random.default_rng(11).choice(10 ** 6, size=nb * (nb - 1) // 2, replace=False) + 1
+        sc, cond, k = [], [], 0
+        for u in range(nb):
+            for v in range(u, nb):
+                if u == v:
+                    sc.append(0)
+                else:
+                    sc.append(-int(vals[k]))
+                    cond.append(2.0 * vals[k])
+                    k += 1
+        t = oracle.guide_trees(np.array([0, nb], np.int32), np.array([0, len(sc)]), np.array(sc, np.int32), lib=lib)
+        Z = linkage(np.array(cond), method="average")
+        if any(sorted((int(Z[m, 0]), int(Z[m, 1]))) != [t["left"][m], t["right"][m]] for m in range(nb - 1)):
+            failed.append("guide tree vs scipy")
     return failed
 
 
