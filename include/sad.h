@@ -16,6 +16,8 @@
  *                                inside every bucket
  *        sad_align_pairs         the alignments themselves (traceback) of
  *                                given pairs
+ *        sad_guide_trees         average-linkage guide tree of every bucket
+ *                                from its pair scores
  * plus sad_pipeline (both stages in one call) and a continuous-batching
  * serving loop (sad_server_*).
  *
@@ -184,7 +186,8 @@ const char* sad_version(void);
 #define SAD_STAGE_SCORES_PACKED 6 /* alignment-score kernels, two problems per 16x2 lane */
 #define SAD_STAGE_GLOBAL 7     /* globalized rank: sample selection and sums against the samples */
 #define SAD_STAGE_ALIGN 8      /* alignments with traceback (sad_align_pairs) */
-#define SAD_NUM_STAGES 9
+#define SAD_STAGE_TREE 9       /* guide trees (sad_guide_trees) */
+#define SAD_NUM_STAGES 10
 
 /* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
  * accumulated times. */
@@ -333,6 +336,29 @@ int sad_scores_autotune(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* buc
                         const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
                         int32_t gap_extend, const int32_t* bin_upper, int32_t nbins, int32_t reps,
                         int32_t mem, void* stream);
+
+/* ---- guide trees ------------------------------------------------------------ */
+
+/* Average-linkage (UPGMA) guide tree of every bucket from its pair scores: the
+ * first step of the progressive multiple aligner that each processor runs on
+ * its bucket (Section 2.3.3 lets it be any sequential aligner). Inside bucket b
+ * (nb members, local positions 0..nb-1 as in sad_bucket_pair_scores) the
+ * distance of u and v is d_uv = S_uu + S_vv - 2 S_uv; two clusters are at
+ * W / (|A| |B|), W the sum of d over their member pairs; the closest pair is
+ * joined first (exact rational comparison), ties to the smallest pair of
+ * cluster ids (lower id, then higher id); merge k creates cluster nb + k.
+ * Inputs: bucket_offsets[p+1], score_offsets[p+1] and scores as written by
+ * sad_bucket_pair_scores. Outputs (caller-owned, `mem` space):
+ * merge_offsets[p+1] (filled: bucket b's merges are [merge_offsets[b],
+ * merge_offsets[b+1]), nb - 1 of them for nb >= 1), and per merge m: left[m] <
+ * right[m] (cluster ids joined), num[m] and den[m] (their distance num / den;
+ * den = |A| |B|). M = sum over buckets of max(nb - 1, 0) = n minus the number of
+ * non-empty buckets. Errors: SAD_EINVAL (offsets that do not describe upper
+ * triangles, a bucket above 2^20 members), SAD_ENOMEM (the buckets' nb x nb
+ * cluster matrices above 12 GiB), SAD_ECUDA. */
+int sad_guide_trees(sad_ctx* ctx, const int32_t* bucket_offsets, int32_t p, const int64_t* score_offsets,
+                    const int32_t* scores, int64_t* merge_offsets, int32_t* left, int32_t* right, int64_t* num,
+                    int64_t* den, int32_t mem, void* stream);
 
 /* ---- alignments (traceback) ----------------------------------------------- */
 

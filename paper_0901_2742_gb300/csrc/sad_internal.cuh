@@ -81,6 +81,7 @@ enum Slot : int {
     WS_TRACE,          // alignment (traceback) call: pairs, offsets, outputs
     WS_TRACE_DIRS,     // traceback direction words
     WS_KBLOCKS,        // per 128-row panel of the planes: bitmap of nonzero 128-byte k-blocks
+    WS_TREE,           // guide trees: tables, cluster matrices, staging
     WS_NUM_SLOTS
 };
 

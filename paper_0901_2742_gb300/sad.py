@@ -87,6 +87,7 @@ def load():
         "sad_trace_enable": (ctypes.c_int, [P, i32]),
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
         "sad_kmer_gemm_work": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "sad_guide_trees": (ctypes.c_int, [P, P, i32, P, P, P, P, P, P, P, i32, P]),
         "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -195,7 +196,8 @@ def _ctx(ctx):
     return None if ctx is None else ctx.handle
 
 
-STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global", "align")
+STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global", "align",
+          "tree")
 
 
 def trace_enable(on: bool = True, ctx=None):
@@ -223,6 +225,24 @@ def trace_timeline(ctx=None) -> list:
     t1 = (ctypes.c_double * max(m, 1))()
     _check(lib.sad_trace_timeline(_ctx(ctx), st, t0, t1, m, ctypes.byref(n)))
     return [(STAGES[st[i]], t0[i], t1[i]) for i in range(min(m, n.value))]
+
+
+def guide_trees(bucket_offsets, score_offsets, scores, ctx=None, stream=None) -> dict:
+    """sad_guide_trees: dict(merge_offsets[p+1], left, right, num, den) -- in
+    bucket b merge k joins clusters left < right into nb + k at num / den."""
+    mem = _mode(bucket_offsets, score_offsets, scores)
+    bo = _as(bucket_offsets, np.int32, mem)
+    so = _as(score_offsets, np.int64, mem)
+    sc = _as(scores, np.int32, mem)
+    p = bo.shape[0] - 1
+    bo_h = bo.cpu().numpy() if mem == MEM_DEVICE else bo
+    M = int(np.maximum(np.diff(bo_h.astype(np.int64)) - 1, 0).sum())
+    mo = _empty(p + 1, np.int64, mem, bo)
+    left, right = _empty(max(M, 1), np.int32, mem, bo), _empty(max(M, 1), np.int32, mem, bo)
+    num, den = _empty(max(M, 1), np.int64, mem, bo), _empty(max(M, 1), np.int64, mem, bo)
+    _check(load().sad_guide_trees(_ctx(ctx), _ptr(bo), p, _ptr(so), _ptr(sc), _ptr(mo), _ptr(left), _ptr(right),
+                                  _ptr(num), _ptr(den), mem, _stream(stream, mem)))
+    return {"merge_offsets": mo, "left": left[:M], "right": right[:M], "num": num[:M], "den": den[:M]}
 
 
 def kmer_gemm_work(ctx=None) -> tuple:
