@@ -439,6 +439,20 @@ def main():
                                         if peaks else "(fallback 1.9 PFLOP/s, of fallback)")),
                          "pairs_per_s": n * (n + 1) / 2 / (ap_ms * 1e-3)}
 
+    # the per-bucket guide trees (the progressive aligner's first step) on this step's own device
+    # outputs, outside the timed region; the tracer times the tree kernel on its stream
+    sad.trace_enable(True)
+    tree_reps = 5
+    for _ in range(tree_reps):
+        tr = sad.guide_trees(out_d["bucket_offsets"], out_d["score_offsets"], out_d["scores"])
+    torch.cuda.synchronize()
+    tree_trace = sad.trace_read()["tree"]
+    sad.trace_enable(False)
+    sizes = np.diff(bo.astype(np.int64))
+    guide_trees = {"kernel": "k_guide_trees (average linkage, one CTA per bucket, exact rational argmin)",
+                   "ms": tree_trace[0] / max(tree_trace[1], 1), "buckets": int(p),
+                   "largest_bucket": int(sizes.max()), "merges": int(tr["left"].shape[0])}
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -519,6 +533,7 @@ def main():
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the score launches "
                                       "of one step (" + SCORE_TRAFFIC["profile"] + ")"},
         "kmer_roofline": kmer_roofline,
+        "guide_trees": guide_trees,
         "gpu_launches": int(launches),
         "wall_s": wall,
         "clocks": clocks,

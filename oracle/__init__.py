@@ -16,6 +16,8 @@ Functions follow the paper:
   bucket_pair_scores  all pairs u <= v inside every bucket
   guide_trees         average-linkage (UPGMA) tree of every bucket from its
                       pair scores, the progressive aligner's first step
+  progressive         progressive profile alignment of every bucket along its
+                      guide tree (one multiple alignment per bucket)
 
 Parity status: every function here is pinned by tests that do not reuse this
 code (brute-force alignment enumeration, sorted-list k-mer intersection,
@@ -72,6 +74,8 @@ def _bind(lib):
     lib.orc_bucket_pair_scores.restype = ctypes.c_int
     lib.orc_bucket_pair_scores.argtypes = [P, P, i32, P, P, i32, P, i32, i32, i32, i32, P, P]
     lib.orc_guide_trees.argtypes = [P, i32, P, P, P, P, P, P, P]
+    lib.orc_progressive.restype = ctypes.c_int
+    lib.orc_progressive.argtypes = [P, P, i32, P, P, i32, P, P, P, P, i32, i32, i32, i32, P, P, P, P]
     return lib
 
 
@@ -270,6 +274,35 @@ def guide_trees(bucket_offsets, score_offsets, scores, lib=None):
     lib.orc_guide_trees(_ptr(bo), p, _ptr(so), _ptr(sc if sc.size else np.zeros(1, np.int32)), _ptr(mo),
                         _ptr(left), _ptr(right), _ptr(num), _ptr(den))
     return {"merge_offsets": mo, "left": left[:M], "right": right[:M], "num": num[:M], "den": den[:M]}
+
+
+def progressive(residues, offsets, bucket_offsets, order, merge_offsets, left, right, subst, gap_open, gap_extend,
+                nthreads=None, lib=None):
+    """Progressive alignment of every bucket along its guide tree (see
+    oracle.cpp): dict(widths int32[p], merge_scores int64[M], merge_widths
+    int32[M], colmap int32[residues]); colmap runs over the residues of
+    order[0], order[1], ... and gives each one's column in its bucket's
+    alignment."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    bo, od = _c(bucket_offsets, np.int32), _c(order, np.int32)
+    mo, lf, rt = _c(merge_offsets, np.int64), _c(left, np.int32), _c(right, np.int32)
+    sub = _c(subst, np.int8)
+    n, p = len(offs) - 1, len(bo) - 1
+    alphabet = int(round(np.sqrt(sub.size)))
+    M = int(mo[-1])
+    total = int(sum(offs[od[q] + 1] - offs[od[q]] for q in range(len(od))))
+    widths = np.zeros(p, np.int32)
+    ms, mw = np.zeros(max(M, 1), np.int64), np.zeros(max(M, 1), np.int32)
+    colmap = np.zeros(max(total, 1), np.int32)
+    one = np.zeros(1, np.int32)
+    rc = lib.orc_progressive(_ptr(res if res.size else np.zeros(1, np.uint8)), _ptr(offs), n, _ptr(bo),
+                             _ptr(od if od.size else one), p, _ptr(mo), _ptr(lf if lf.size else one),
+                             _ptr(rt if rt.size else one), _ptr(sub), alphabet, int(gap_open), int(gap_extend),
+                             nthreads or default_threads(), _ptr(widths), _ptr(ms), _ptr(mw), _ptr(colmap))
+    if rc != 0:
+        raise ValueError("orc_progressive: the merges do not form a tree")
+    return {"widths": widths, "merge_scores": ms[:M], "merge_widths": mw[:M], "colmap": colmap[:total]}
 
 
 def tri_index(u: int, v: int, nb: int) -> int:

@@ -33,6 +33,12 @@
  *     the distance of two clusters being the pair sum over the product of
  *     their sizes, compared as exact rationals; ties go to the lexicographically
  *     smallest pair of cluster ids (leaves 0..nb-1, merge k creates nb + k).
+ *   - per-bucket progressive alignment along that tree (Section 2.3.3): each
+ *     merge aligns the two clusters' profiles with the three-state affine-gap
+ *     recursion, a column pair scoring the sum of the substitution scores of
+ *     the letter pairs across the profiles and a new gap run costing the
+ *     member-count product times the pairwise run cost; the tie order and the
+ *     column bookkeeping are stated at orc_progressive.
  */
 #include <algorithm>
 #include <atomic>
@@ -613,6 +619,187 @@ int orc_guide_trees(const int32_t* bucket_offsets, int32_t p, const int64_t* sco
         }
     }
     return 0;
+}
+
+/* Progressive alignment of every bucket along its guide tree (the aligner
+ * each processor runs on its bucket, Section 2.3.3), merge by merge in the
+ * tree's order. A cluster is a multiple alignment of its members: its profile
+ * column c holds, per letter a, the number of members with letter a in column
+ * c. Merge k aligns the profile P of cluster left[k] (rows) with the profile Q
+ * of cluster right[k] (columns) by the three-state global affine-gap
+ * recursion of orc_align, where pairing column i of P with column j of Q
+ * scores the sum of S over the letter pairs across the two profiles,
+ *   s(i, j) = sum_a sum_b cntP[i][a] cntQ[j][b] S[a][b]
+ * (a gap in an existing column pairs with nothing), and a new gap run of
+ * length g costs nP nQ (go + g ge), nP and nQ being the member counts: every
+ * cross pair of members receives the run. Ties are taken as in orc_align. The
+ * merged cluster has one column per alignment column, in order; its members
+ * are P's followed by Q's, each residue moved to the column its old column
+ * went to. Outputs: widths[b] = the number of columns of bucket b's final
+ * alignment (the root cluster; a one-member bucket is its sequence, an empty
+ * one 0); merge_scores / merge_widths per merge (layout of orc_guide_trees);
+ * colmap = the final column of every residue, over the residues of order[0],
+ * order[1], ... in turn. Returns 0, or -1 on a tree that is not a tree. */
+int orc_progressive(const uint8_t* res, const int64_t* offs, int32_t n, const int32_t* bucket_offsets,
+                    const int32_t* order, int32_t p, const int64_t* merge_offsets, const int32_t* left,
+                    const int32_t* right, const int8_t* S, int32_t alphabet, int32_t go, int32_t ge,
+                    int32_t nthreads, int32_t* widths, int64_t* merge_scores, int32_t* merge_widths,
+                    int32_t* colmap) {
+    if (p < 1 || n < 0) return -1;
+    // where each bucket position's residues start in colmap
+    std::vector<int64_t> pos_off((size_t)n + 1, 0);
+    for (int32_t q = 0; q < n; q++) pos_off[q + 1] = pos_off[q] + (offs[order[q] + 1] - offs[order[q]]);
+    std::atomic<int> bad(0);
+    parallel_for(p, nthreads, [&](int64_t b) {
+        const int32_t boff = bucket_offsets[b];
+        const int64_t nb = bucket_offsets[b + 1] - boff;
+        struct Cluster {
+            std::vector<int32_t> members;           // bucket positions
+            std::vector<std::vector<int64_t>> col;  // per member: the column of each residue
+            int64_t width = 0;
+            bool alive = false;
+        };
+        std::vector<Cluster> cl(nb > 0 ? 2 * nb - 1 : 0);
+        for (int64_t u = 0; u < nb; u++) {
+            const int32_t sq = order[boff + u];
+            const int64_t len = offs[sq + 1] - offs[sq];
+            cl[u].members = {(int32_t)u};
+            std::vector<int64_t> c(len);
+            for (int64_t r = 0; r < len; r++) c[r] = r;
+            cl[u].col = {c};
+            cl[u].width = len;
+            cl[u].alive = true;
+        }
+        auto residues_of = [&](int32_t u) { return res + offs[order[boff + u]]; };
+        auto profile = [&](const Cluster& c) {  // counts[col * alphabet + letter]
+            std::vector<int64_t> cnt((size_t)c.width * alphabet, 0);
+            for (size_t t = 0; t < c.members.size(); t++) {
+                const uint8_t* x = residues_of(c.members[t]);
+                for (size_t r = 0; r < c.col[t].size(); r++) cnt[c.col[t][r] * alphabet + x[r]]++;
+            }
+            return cnt;
+        };
+        for (int64_t k = 0; k + 1 < nb; k++) {
+            const int64_t mi = merge_offsets[b] + k;
+            const int32_t li = left[mi], ri = right[mi];
+            if (li < 0 || ri < 0 || li >= nb + k || ri >= nb + k || li == ri || !cl[li].alive || !cl[ri].alive) {
+                bad = 1;
+                return;
+            }
+            Cluster &P = cl[li], &Q = cl[ri];
+            const int64_t m = P.width, w = Q.width;
+            const int64_t np = (int64_t)P.members.size(), nq = (int64_t)Q.members.size();
+            const std::vector<int64_t> cp = profile(P), cq = profile(Q);
+            // sum_b S[a][b] cntQ[j][b] for every column j and letter a (a factor of s(i, j))
+            std::vector<int64_t> sq((size_t)w * alphabet, 0);
+            for (int64_t j = 0; j < w; j++)
+                for (int32_t a = 0; a < alphabet; a++)
+                    for (int32_t c = 0; c < alphabet; c++) sq[j * alphabet + a] += S[a * alphabet + c] * cq[j * alphabet + c];
+            auto s = [&](int64_t i, int64_t j) {  // 1-based column indices
+                int64_t v = 0;
+                for (int32_t a = 0; a < alphabet; a++) v += cp[(i - 1) * alphabet + a] * sq[(j - 1) * alphabet + a];
+                return v;
+            };
+            const int64_t gop = (int64_t)go * np * nq, gex = (int64_t)ge * np * nq;
+            // the three tables, as in fill_gotoh
+            const int64_t W = w + 1;
+            std::vector<int64_t> TM((size_t)(m + 1) * W, NEG_INF), TX(TM), TY(TM);
+            auto at = [&](int64_t i, int64_t j) { return i * W + j; };
+            TM[at(0, 0)] = 0;
+            for (int64_t i = 0; i <= m; i++)
+                for (int64_t j = 0; j <= w; j++) {
+                    if (i == 0 && j == 0) continue;
+                    if (i > 0 && j > 0) {
+                        const int64_t prev = std::max({TM[at(i - 1, j - 1)], TX[at(i - 1, j - 1)], TY[at(i - 1, j - 1)]});
+                        if (prev > NEG_INF) TM[at(i, j)] = prev + s(i, j);
+                    }
+                    if (i > 0) {
+                        const int64_t open = std::max(TM[at(i - 1, j)], TY[at(i - 1, j)]);
+                        int64_t v = NEG_INF;
+                        if (open > NEG_INF) v = open + gop + gex;
+                        if (TX[at(i - 1, j)] > NEG_INF) v = std::max(v, TX[at(i - 1, j)] + gex);
+                        TX[at(i, j)] = v;
+                    }
+                    if (j > 0) {
+                        const int64_t open = std::max(TM[at(i, j - 1)], TX[at(i, j - 1)]);
+                        int64_t v = NEG_INF;
+                        if (open > NEG_INF) v = open + gop + gex;
+                        if (TY[at(i, j - 1)] > NEG_INF) v = std::max(v, TY[at(i, j - 1)] + gex);
+                        TY[at(i, j)] = v;
+                    }
+                }
+            // traceback with the tie order of orc_align
+            auto best_of = [&](int64_t i, int64_t j, bool useM, bool useX, bool useY, int64_t want, int64_t add) {
+                if (useM && TM[at(i, j)] > NEG_INF && TM[at(i, j)] + add == want) return 'M';
+                if (useX && TX[at(i, j)] > NEG_INF && TX[at(i, j)] + add == want) return 'X';
+                if (useY && TY[at(i, j)] > NEG_INF && TY[at(i, j)] + add == want) return 'Y';
+                return '?';
+            };
+            const int64_t score = std::max({TM[at(m, w)], TX[at(m, w)], TY[at(m, w)]});
+            char state = best_of(m, w, true, true, true, score, 0);
+            std::string rev;
+            int64_t i = m, j = w;
+            while (i > 0 || j > 0) {
+                rev.push_back(state);
+                if (state == 'M') {
+                    state = best_of(i - 1, j - 1, true, true, true, TM[at(i, j)] - s(i, j), 0);
+                    i--;
+                    j--;
+                } else if (state == 'X') {
+                    const int64_t v = TX[at(i, j)];
+                    const char ext = best_of(i - 1, j, false, true, false, v, gex);
+                    state = ext == 'X' ? 'X' : best_of(i - 1, j, true, false, true, v, gop + gex);
+                    i--;
+                } else if (state == 'Y') {
+                    const int64_t v = TY[at(i, j)];
+                    const char ext = best_of(i, j - 1, false, false, true, v, gex);
+                    state = ext == 'Y' ? 'Y' : best_of(i, j - 1, true, true, false, v, gop + gex);
+                    j--;
+                } else {
+                    bad = 1;
+                    return;
+                }
+            }
+            // the merged cluster: alignment column c takes P's column and/or Q's column
+            const int64_t len = (int64_t)rev.size();
+            std::vector<int64_t> mapP(m), mapQ(w);
+            int64_t pi = 0, qj = 0;
+            for (int64_t c = 0; c < len; c++) {
+                const char op = rev[len - 1 - c];
+                if (op == 'M' || op == 'X') mapP[pi++] = c;
+                if (op == 'M' || op == 'Y') mapQ[qj++] = c;
+            }
+            Cluster& R = cl[nb + k];
+            R.members = P.members;
+            R.members.insert(R.members.end(), Q.members.begin(), Q.members.end());
+            for (auto c : P.col) {
+                for (auto& v : c) v = mapP[v];
+                R.col.push_back(c);
+            }
+            for (auto c : Q.col) {
+                for (auto& v : c) v = mapQ[v];
+                R.col.push_back(c);
+            }
+            R.width = len;
+            R.alive = true;
+            P.alive = Q.alive = false;
+            P.col.clear();
+            Q.col.clear();
+            merge_scores[mi] = score;
+            merge_widths[mi] = (int32_t)len;
+        }
+        if (nb == 0) {
+            widths[b] = 0;
+            return;
+        }
+        const Cluster& root = cl[2 * nb - 2];
+        widths[b] = (int32_t)root.width;
+        for (size_t t = 0; t < root.members.size(); t++) {
+            const int64_t q = boff + root.members[t];
+            for (size_t r = 0; r < root.col[t].size(); r++) colmap[pos_off[q] + r] = (int32_t)root.col[t][r];
+        }
+    });
+    return bad ? -1 : 0;
 }
 
 }  // extern "C"

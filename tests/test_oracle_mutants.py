@@ -40,6 +40,15 @@ MUTANTS = {
     "tree comparison without sizes": ("const __int128 lhs = (__int128)W[i][j] * (size[bi] * size[bj]);", "const __int128 lhs = (__int128)W[i][j];"),
     "tree tie to the last pair": ("if (lhs < rhs) {  // on equality", "if (lhs <= rhs) {  // on equality"),
     "tree merge sums one child": ("W[c][x] = W[x][c] = W[bi][x] + W[bj][x];", "W[c][x] = W[x][c] = 2 * W[bi][x];"),
+    "profile gaps not scaled by the member counts": ("const int64_t gop = (int64_t)go * np * nq, gex = (int64_t)ge * np * nq;",
+                                                     "const int64_t gop = go, gex = ge;"),
+    "profile column counts the wrong letter": ("S[a * alphabet + c] * cq[j * alphabet + c];",
+                                               "S[a * alphabet + c] * cq[j * alphabet + a];"),
+    "profile end tie prefers a gap": ("char state = best_of(m, w, true, true, true, score, 0);",
+                                      "char state = best_of(m, w, false, true, true, score, 0);\n"
+                                      "            if (state == '?') state = 'M';"),
+    "profile of the first member only": ("for (size_t t = 0; t < c.members.size(); t++) {\n                const uint8_t* x",
+                                         "for (size_t t = 0; t < 1; t++) {\n                const uint8_t* x"),
 }
 
 
@@ -140,6 +149,34 @@ def battery(lib):
         Z = linkage(np.array(cond), method="average")
         if any(sorted((int(Z[m, 0]), int(Z[m, 1]))) != [t["left"][m], t["right"][m]] for m in range(nb - 1)):
             failed.append("guide tree vs scipy")
+    # 7. progressive alignment: the golden example, and every merge of random tiny
+    #    buckets against the best of all its alignments, enumerated
+    import test_oracle_progressive as tp
+    with open(os.path.join(GOLD, "progressive_tiny.json")) as f:
+        c = json.load(f)
+    res, offs = synth.pack(c["seqs"])
+    r = oracle.progressive(res, offs, c["bucket_offsets"], c["order"], c["merge_offsets"], c["left"], c["right"],
+                           np.array(c["subst"]).ravel(), c["gap_open"], c["gap_extend"], lib=lib)
+    if any(r[f].tolist() != c[f] for f in ("widths", "merge_scores", "merge_widths", "colmap")):
+        failed.append("golden progressive")
+    rng = random.Random(7)
+    for _ in range(6):
+        A = rng.choice([2, 3])
+        S = random_symmetric(rng, A, -4, 6).astype(np.int64).tolist()
+        nb = rng.randint(2, 4)
+        seqs = [[rng.randrange(A) for _ in range(rng.randint(0, 3))] for _ in range(nb)]
+        left, right = tp.random_tree(rng, nb)
+        res, offs = synth.pack(seqs)
+        r = oracle.progressive(res, offs, [0, nb], list(range(nb)), [0, nb - 1], left, right,
+                               np.array(S, np.int8).ravel(), -3, -1, lib=lib)
+        rows = tp.rows_of(seqs, [0, nb], list(range(nb)), r["colmap"])[0]
+        try:
+            tp.check_rows(rows, int(r["widths"][0]))
+            tp.check_merges({u: seqs[u] for u in range(nb)}, nb, left, right, r["merge_scores"].tolist(),
+                            r["merge_widths"].tolist(), rows, S, -3, -1)
+        except AssertionError:
+            failed.append("progressive brute force")
+            break
     return failed
 
 
