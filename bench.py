@@ -126,6 +126,41 @@ def device_gaps(spans):
             "gap_after_ms": {s: g / k for s, g in gap_after.items()}}
 
 
+def progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od, reps=3):
+    """Time sad_progressive_align on the step's buckets and guide trees: the
+    traced span (device time including the per-level host reads) and the DP
+    cells of all merges (the product of the two children's widths)."""
+    import torch
+    sad.trace_enable(True)
+    for _ in range(reps):
+        pa = sad.progressive_align(res_d, offs_d, w.alphabet, out_d["bucket_offsets"], out_d["order"][:w.n],
+                                   tr["merge_offsets"], tr["left"], tr["right"], w.subst, w.gap_open,
+                                   w.gap_extend)
+    torch.cuda.synchronize()
+    span = sad.trace_read()["prog"]
+    sad.trace_enable(False)
+    lens = np.diff(w.offsets)[od]
+    mo, lt, rt = (tr[f].cpu().numpy() for f in ("merge_offsets", "left", "right"))
+    mw = pa["merge_widths"].cpu().numpy()
+    cells, levels = 0, 0
+    for b in range(len(bo) - 1):
+        nb = int(bo[b + 1] - bo[b])
+        width = list(lens[bo[b]:bo[b + 1]]) + [0] * max(nb - 1, 0)
+        depth = [0] * (2 * nb)
+        for k in range(max(nb - 1, 0)):
+            m = int(mo[b]) + k
+            cells += int(width[lt[m]]) * int(width[rt[m]])
+            width[nb + k] = int(mw[m])
+            depth[nb + k] = 1 + max(depth[lt[m]], depth[rt[m]])
+            levels = max(levels, depth[nb + k])
+    ms = span[0] / max(span[1], 1)
+    return {"kernel": "k_prof_dp (profile-profile affine-gap DP with traceback, one warp per merge) "
+                      "+ k_prof_scores + k_prof_pb + k_colmap",
+            "ms": ms, "merges": int(len(lt)), "tree_levels": int(levels), "dp_cells": int(cells),
+            "gcups": cells / (ms * 1e-3) / 1e9 if ms > 0 else None,
+            "alignment_widths": [int(x) for x in pa["widths"].cpu().numpy()]}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -452,6 +487,8 @@ def main():
     guide_trees = {"kernel": "k_guide_trees (average linkage, one CTA per bucket, exact rational argmin)",
                    "ms": tree_trace[0] / max(tree_trace[1], 1), "buckets": int(p),
                    "largest_bucket": int(sizes.max()), "merges": int(tr["left"].shape[0])}
+    # then the progressive alignment of every bucket along its tree (also outside the timed region)
+    progressive = progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -534,6 +571,7 @@ def main():
                                       "of one step (" + SCORE_TRAFFIC["profile"] + ")"},
         "kmer_roofline": kmer_roofline,
         "guide_trees": guide_trees,
+        "progressive": progressive,
         "gpu_launches": int(launches),
         "wall_s": wall,
         "clocks": clocks,

@@ -18,6 +18,8 @@
  *                                given pairs
  *        sad_guide_trees         average-linkage guide tree of every bucket
  *                                from its pair scores
+ *        sad_progressive_align   one multiple alignment per bucket, profile
+ *                                against profile along its guide tree
  * plus sad_pipeline (both stages in one call) and a continuous-batching
  * serving loop (sad_server_*).
  *
@@ -187,7 +189,8 @@ const char* sad_version(void);
 #define SAD_STAGE_GLOBAL 7     /* globalized rank: sample selection and sums against the samples */
 #define SAD_STAGE_ALIGN 8      /* alignments with traceback (sad_align_pairs) */
 #define SAD_STAGE_TREE 9       /* guide trees (sad_guide_trees) */
-#define SAD_NUM_STAGES 10
+#define SAD_STAGE_PROG 10      /* progressive alignment (sad_progressive_align) */
+#define SAD_NUM_STAGES 11
 
 /* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
  * accumulated times. */
@@ -359,6 +362,38 @@ int sad_scores_autotune(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* buc
 int sad_guide_trees(sad_ctx* ctx, const int32_t* bucket_offsets, int32_t p, const int64_t* score_offsets,
                     const int32_t* scores, int64_t* merge_offsets, int32_t* left, int32_t* right, int64_t* num,
                     int64_t* den, int32_t mem, void* stream);
+
+/* Progressive alignment of every bucket along its guide tree (the
+ * per-processor multiple aligner of Section 2.3.3; the paper allows any
+ * sequential one). Inputs: the buckets (bucket_offsets[p+1], order[npos],
+ * npos = bucket_offsets[p], positions of sequence ids of seqs, as
+ * sad_partition writes them) and their trees (merge_offsets[p+1],
+ * left/right[M], as sad_guide_trees writes them: merge k of bucket b joins
+ * clusters left < right into nb + k; leaves are the bucket positions 0..nb-1).
+ * Merge k aligns the multiple alignment of cluster left[k] (profile P, nP
+ * members) with that of right[k] (profile Q, nQ members), both kept fixed, by
+ * the global affine-gap recursion of sad_align_pairs in which pairing a column
+ * of P with a column of Q scores the sum of subst over the letter pairs across
+ * them (a gap already in a column pairs with nothing) and a new run of g gap
+ * columns costs nP nQ (gap_open + g gap_extend). The optimal alignment is
+ * taken with fixed ties: a cell's best state is match, then a gap in Q's
+ * columns, then a gap in P's; a gap column extends its run before it opens
+ * one and opens from a match before the other gap state. Outputs (caller-
+ * owned, `mem` space): widths[p] (columns of bucket b's alignment; a
+ * one-member bucket is its sequence, an empty one 0), merge_scores[M] (int64
+ * optimum of each merge), merge_widths[M] (columns of each merged cluster),
+ * colmap[sum of the lengths of order[0..npos)] (the column of every residue
+ * in its bucket's alignment, over the residues of order[0], order[1], ... in
+ * turn). Errors: SAD_EINVAL (layout or tree inconsistent, a bucket above
+ * 65535 members, nP nQ max|subst| >= 2^31, an asymmetric subst, gap costs
+ * > 0 or below -1000, a residue >= alphabet), SAD_ENOMEM, SAD_ECUDA. The host
+ * reads the new widths back after every tree level (one synchronisation of
+ * `stream` per level). */
+int sad_progressive_align(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                          const int32_t* order, int32_t p, const int64_t* merge_offsets, const int32_t* left,
+                          const int32_t* right, const int8_t* subst, int32_t gap_open, int32_t gap_extend,
+                          int32_t* widths, int64_t* merge_scores, int32_t* merge_widths, int32_t* colmap,
+                          int32_t mem, void* stream);
 
 /* ---- alignments (traceback) ----------------------------------------------- */
 

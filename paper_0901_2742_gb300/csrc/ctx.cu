@@ -371,6 +371,8 @@ int sad_ctx_destroy(sad_ctx* ctx) {
     SAD_CUDA(cudaDeviceSynchronize());
     for (auto& b : ctx->ws)
         if (b.ptr) cudaFree(b.ptr);
+    for (auto& b : ctx->prog_chunks)
+        if (b.ptr) cudaFree(b.ptr);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

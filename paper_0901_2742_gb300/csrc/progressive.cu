@@ -1,0 +1,781 @@
+// Progressive alignment of every bucket along its guide tree: the aligner
+// each processor runs on its bucket (Section 2.3.3 lets it be any sequential
+// multiple aligner; a progressive aligner joins the members two clusters at a
+// time, in guide-tree order, each join aligning two fixed alignments).
+//
+// Definition (exact integers). A cluster is a multiple alignment of its
+// members; column c of its profile counts, per letter a, the members with
+// letter a there. Merge k aligns the profile P of cluster left[k] (rows,
+// width m, nP members) with the profile Q of cluster right[k] (columns, width
+// n, nQ members) by the three-state global affine-gap recursion
+//   M(i,j) = max(M, X, Y)(i-1, j-1) + s(i, j)
+//   X(i,j) = max(max(M, Y)(i-1, j) + go' + ge', X(i-1, j) + ge')
+//   Y(i,j) = max(max(M, X)(i, j-1) + go' + ge', Y(i, j-1) + ge')
+// with s(i, j) = sum_a sum_b cntP[i][a] cntQ[j][b] S[a][b] (letter pairs
+// across the two profiles; gaps already in a column pair with nothing) and
+// go' = nP nQ go, ge' = nP nQ ge (every cross pair of members receives a new
+// gap run). One optimal alignment is taken back from (m, n) with the ties
+// fixed: a cell's best state is M, then X, then Y; an X or Y column extends
+// its run before it opens one, and opens from M before the other gap state.
+// The merged cluster has one column per alignment column; every residue moves
+// to the column its old column went to.
+//
+// GPU mapping. The merges of a bucket depend on each other only through the
+// tree, so the host runs them level by level (a merge's level is one more
+// than its children's), all buckets' merges of a level in one batch, and
+// reads the new widths back after each level. Per batch:
+//   k_prof_scores  tiles of 128 rows x 32 columns over all SMs: PB[j][a] =
+//                  sum_b S[a][b] cntQ[j][b] in shared memory, then s(i, j) =
+//                  sum_a cntP[i][a] PB[j][a], laid out as one stream per DP lane
+//   k_prof_dp<T>   one warp per merge: the lanes hold 4 rows each of a strip of
+//                  128 rows and sweep the columns as a diagonal wavefront (M, X
+//                  and Y of a lane's bottom row move one lane down per step);
+//                  a lane loads its scores 8 steps ahead; every cell stores one
+//                  byte of tie-resolved directions; the strip boundary, a window
+//                  of direction words for the walk back and the columns sit in
+//                  shared memory; then the warp writes the column maps and the
+//                  merged profile. T is int32 when the host proves every value
+//                  fits, else int64.
+// At the end k_colmap composes each residue's column maps up the tree.
+// Profiles (uint16 counts, the alphabet padded to 8) and column maps live in
+// an arena of device chunks that only grows during a call.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sad_internal.cuh"
+
+namespace sad {
+
+namespace {
+
+constexpr int kPrR = 4;                  // rows per lane
+constexpr int kPrG = 32;                 // lanes per merge (one warp)
+constexpr int kPrStrip = kPrR * kPrG;    // rows per strip
+constexpr int kPrWarps = 4;              // warps per CTA of the DP kernel
+
+// One merge of a batch.
+struct ProgJob {
+    const uint16_t* prof_p;  // P: m columns of Ap counts
+    const uint16_t* prof_q;  // Q: n columns
+    uint16_t* prof_r;        // the merged cluster (capacity m + n columns)
+    int32_t* map;            // m entries for P's columns, then n for Q's
+    int64_t s_off;           // cell-score streams (int4): strips x 32 lanes x (n + 31) steps, then padding
+    int64_t d_off;           // direction words (uint32, strips x (n + 31) x 32)
+    int32_t m, n, np, nq;
+    int32_t merge;           // index into the per-merge outputs
+    int32_t tile0;           // first score tile (a job has strips x ceil(n / 32) of them)
+};
+
+struct ProgArgs {
+    const ProgJob* jobs;
+    int32_t njobs;
+    int32_t ntiles;
+    int32_t Ap;              // counts per profile column
+    int32_t alphabet;
+    int32_t go, ge;
+    const int8_t* subst;
+    int4* S;
+    uint32_t* dirs;
+    long long* scores;       // per merge
+    int32_t* widths;         // per merge
+    uint32_t* status;
+    int32_t maxw;            // widest profile of the batch
+    int32_t warp_smem;       // shared bytes per warp of the DP kernel
+};
+
+constexpr int kPrWin = 32;       // steps of direction words the traceback holds in shared memory
+constexpr int kPrPre = 8;        // steps of cell scores a lane loads ahead
+
+template <typename T>
+__device__ __forceinline__ T neg_inf();
+template <>
+__device__ __forceinline__ int32_t neg_inf<int32_t>() { return -(1 << 30); }
+template <>
+__device__ __forceinline__ long long neg_inf<long long>() { return -(1ll << 60); }
+
+template <typename T>
+__device__ __forceinline__ T max3(T a, T b, T c) { return max(a, max(b, c)); }
+
+// Shared-memory layout of one DP warp: strip boundary (3 values per column),
+// the traceback's window of direction words, the alignment columns.
+template <typename T>
+__host__ __device__ inline int64_t bnd_bytes(int32_t maxw) {
+    return (3ll * (maxw + 2) * (int64_t)sizeof(T) + 15) / 16 * 16;
+}
+__host__ __device__ inline int64_t win_bytes() { return 4ll * kPrWin * kPrG; }
+__host__ __device__ inline int64_t ops_bytes(int32_t maxw) { return (2ll * maxw + 16 + 15) / 16 * 16; }
+
+// Leaf profiles: one column per residue, a count of 1 for its letter.
+__global__ void k_leaf_profiles(const uint8_t* __restrict__ res, const int64_t* __restrict__ pad_off,
+                                const int32_t* __restrict__ len, const int32_t* __restrict__ order, int32_t npos,
+                                const int64_t* __restrict__ pos_off, int32_t Ap, uint16_t* __restrict__ prof) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = wid; q < npos; q += nw) {
+        const int32_t sq = order[q];
+        const uint8_t* x = res + pad_off[sq];
+        uint16_t* out = prof + pos_off[q] * Ap;
+        const int64_t cells = (int64_t)len[sq] * Ap;
+        for (int64_t t = lane; t < cells; t += 32) {
+            const int64_t r = t / Ap;
+            out[t] = (uint16_t)((t - r * Ap) == x[r] ? 1 : 0);
+        }
+    }
+}
+
+// Cell scores of one tile: 128 rows (one strip) x 32 columns of one merge.
+// PB[j][a] = sum_b S[a][b] cntQ[j][b] is formed in shared memory for the
+// tile's columns, then s(i, j) = sum_a cntP[i][a] PB[j][a]; thread (g, c4)
+// holds rows 4g..4g+3 and columns 4c4..4c4+3. Lane g of the DP warp reads its
+// rows' scores as one stream over its steps: column j (1-based) sits at step
+// tau = j - 1 + g.
+constexpr int kScThreads = 256;
+__global__ void __launch_bounds__(kScThreads)
+k_prof_scores(ProgArgs a) {
+    __shared__ int32_t sub[SAD_MAX_ALPHABET * SAD_MAX_ALPHABET];
+    __shared__ int32_t cps[kPrStrip * (SAD_MAX_ALPHABET + 1)];
+    __shared__ int32_t pbs[32 * (SAD_MAX_ALPHABET + 1)];
+    const int32_t A = a.alphabet, Ap = a.Ap, st = A + 1;
+    for (int t = threadIdx.x; t < A * A; t += blockDim.x) sub[t] = a.subst[t];
+    for (int32_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        // the job holding this tile: the last one whose first tile is <= tile
+        int32_t lo = 0, hi = a.njobs - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (a.jobs[mid].tile0 <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const ProgJob& jb = a.jobs[lo];
+        const int32_t m = jb.m, n = jb.n;
+        const int32_t cblocks = (n + 31) / 32, nsteps = n + kPrG - 1;
+        const int32_t tt = tile - jb.tile0, s = tt / cblocks, cb = tt - s * cblocks;
+        __syncthreads();  // the previous tile's reads of cps / pbs are done (and sub is loaded)
+        for (int t = threadIdx.x; t < kPrStrip * A; t += blockDim.x) {
+            const int32_t r = t / A, l = t - r * A;
+            const int64_t i = (int64_t)s * kPrStrip + r;
+            cps[r * st + l] = i < m ? (int32_t)jb.prof_p[i * Ap + l] : 0;
+        }
+        for (int t = threadIdx.x; t < 32 * A; t += blockDim.x) {
+            const int32_t c = t / A, l = t - c * A;
+            const int64_t j = (int64_t)cb * 32 + c;
+            int32_t v = 0;
+            if (j < n) {
+                const uint16_t* cq = jb.prof_q + j * Ap;
+                for (int32_t b = 0; b < A; b++) v += sub[l * A + b] * (int32_t)cq[b];
+            }
+            pbs[c * st + l] = v;
+        }
+        __syncthreads();
+        const int g = threadIdx.x >> 3, c4 = threadIdx.x & 7;
+        int32_t acc[kPrR][4];
+#pragma unroll
+        for (int r = 0; r < kPrR; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[r][c] = 0;
+        for (int32_t l = 0; l < A; l++) {
+            int32_t pv[kPrR], qv[4];
+#pragma unroll
+            for (int r = 0; r < kPrR; r++) pv[r] = cps[(g * kPrR + r) * st + l];
+#pragma unroll
+            for (int c = 0; c < 4; c++) qv[c] = pbs[(c4 * 4 + c) * st + l];
+#pragma unroll
+            for (int r = 0; r < kPrR; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] += pv[r] * qv[c];
+        }
+        int4* out = a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int32_t j0 = cb * 32 + c4 * 4 + c;  // 0-based column
+            if (j0 < n) out[j0 + g] = make_int4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+        }
+    }
+}
+
+__device__ __forceinline__ int32_t take_row(const int4& v, int r) {
+    return r == 0 ? v.x : (r == 1 ? v.y : (r == 2 ? v.z : v.w));
+}
+
+// Direction byte of a cell: bits 0-1 its best state (0 M, 1 X, 2 Y); bit 2
+// X extends; bit 3 X opens from M (else from Y); bit 4 Y extends; bit 5 Y
+// opens from M (else from X).
+template <typename T>
+__global__ void __launch_bounds__(kPrG * kPrWarps)
+k_prof_dp(ProgArgs a) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const int64_t nslots = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned char* my = psm + (int64_t)wib * a.warp_smem;
+    T* bnd = (T*)my;
+    uint32_t* win = (uint32_t*)(my + bnd_bytes<T>(a.maxw));
+    uint8_t* ops = my + bnd_bytes<T>(a.maxw) + win_bytes();
+    const T NEG = neg_inf<T>();
+    const int32_t Ap = a.Ap;
+    for (int64_t k = slot; k < a.njobs; k += nslots) {
+        const ProgJob& jb = a.jobs[k];
+        const int32_t m = jb.m, n = jb.n;
+        const T w = (T)jb.np * (T)jb.nq;
+        const T gop = w * (T)a.go, gex = w * (T)a.ge, goe = gop + gex;
+        const int32_t cap = m + n;
+        T score = 0;
+        int32_t L = 0;
+        if (m == 0 || n == 0) {  // one gap run, or nothing
+            for (int32_t c = lane; c < cap; c += 32) ops[c] = m == 0 ? 'Y' : 'X';
+            score = cap == 0 ? (T)0 : gop + (T)cap * gex;
+            L = cap;
+        } else {
+            const int32_t strips = (m + kPrStrip - 1) / kPrStrip;
+            const int32_t nsteps = n + kPrG - 1;
+            uint32_t* dirs = a.dirs + jb.d_off;
+            for (int32_t s = 0; s < strips; s++) {
+                const int32_t row0 = s * kPrStrip + lane * kPrR;  // rows row0+1 .. row0+4 (1-based)
+                T mm[kPrR], xx[kPrR], yy[kPrR];                    // values at the previous column
+#pragma unroll
+                for (int r = 0; r < kPrR; r++) {
+                    mm[r] = NEG;
+                    xx[r] = gop + (T)(row0 + r + 1) * gex;  // X(i, 0)
+                    yy[r] = NEG;
+                }
+                T hdiag = row0 == 0 ? (T)0 : gop + (T)row0 * gex;  // H(row0, 0)
+                T min_ = NEG, xin = NEG, yin = NEG;                // (row0, j) from above
+                const bool last_strip = s == strips - 1;
+                // this lane's score stream (the job's padding keeps the look-ahead in bounds)
+                const int4* Sl = a.S + jb.s_off + ((int64_t)s * kPrG + lane) * nsteps;
+                int4 cur[kPrPre], nxt[kPrPre];
+#pragma unroll
+                for (int u = 0; u < kPrPre; u++) cur[u] = Sl[u];
+                for (int32_t tau0 = 0; tau0 < nsteps; tau0 += kPrPre) {
+#pragma unroll
+                    for (int u = 0; u < kPrPre; u++) nxt[u] = Sl[tau0 + kPrPre + u];
+#pragma unroll
+                    for (int u = 0; u < kPrPre; u++) {
+                        const int32_t tau = tau0 + u;
+                        if (tau >= nsteps) break;
+                        if (lane == 0 && tau < n) {
+                            if (s == 0) {
+                                min_ = NEG;
+                                xin = NEG;
+                                yin = gop + (T)(tau + 1) * gex;  // Y(0, j)
+                            } else {
+                                min_ = bnd[3 * (tau + 1)];
+                                xin = bnd[3 * (tau + 1) + 1];
+                                yin = bnd[3 * (tau + 1) + 2];
+                            }
+                        }
+                        const int32_t j = tau - lane + 1;
+                        T mo = min_, xo = xin, yo = yin;
+                        if (j >= 1 && j <= n) {
+                            const int4 sv = cur[u];
+                            T hd = hdiag, am = min_, ax = xin, ay = yin;
+                            uint32_t bits = 0;
+#pragma unroll
+                            for (int r = 0; r < kPrR; r++) {
+                                const T hleft = max3(mm[r], xx[r], yy[r]);  // H(i, j-1)
+                                const T M = hd + (T)take_row(sv, r);
+                                const T oX = max(am, ay) + goe, eX = ax + gex;
+                                const T X = max(oX, eX);
+                                const T oY = max(mm[r], xx[r]) + goe, eY = yy[r] + gex;
+                                const T Y = max(oY, eY);
+                                const uint32_t best = (M >= X && M >= Y) ? 0u : (X >= Y ? 1u : 2u);
+                                const uint32_t b = best | (eX >= oX ? 4u : 0u) | (am >= ay ? 8u : 0u) |
+                                                   (eY >= oY ? 16u : 0u) | (mm[r] >= xx[r] ? 32u : 0u);
+                                bits |= b << (8 * r);
+                                hd = hleft;
+                                mm[r] = M;
+                                xx[r] = X;
+                                yy[r] = Y;
+                                am = M;
+                                ax = X;
+                                ay = Y;
+                            }
+                            dirs[((int64_t)s * nsteps + tau) * kPrG + lane] = bits;
+                            hdiag = max3(min_, xin, yin);  // H(row0, j): the next column's diagonal
+                            mo = am;
+                            xo = ax;
+                            yo = ay;
+                            if (!last_strip && lane == kPrG - 1) {
+                                bnd[3 * j] = mo;
+                                bnd[3 * j + 1] = xo;
+                                bnd[3 * j + 2] = yo;
+                            }
+                        }
+                        min_ = __shfl_up_sync(0xffffffffu, mo, 1);
+                        xin = __shfl_up_sync(0xffffffffu, xo, 1);
+                        yin = __shfl_up_sync(0xffffffffu, yo, 1);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPrPre; u++) cur[u] = nxt[u];
+                }
+                __syncwarp();
+                if (last_strip) {
+                    // (four named values: a select over the arrays would put them in local memory)
+                    static_assert(kPrR == 4, "four rows per lane");
+                    const int32_t rr = (m - 1) - s * kPrStrip;
+                    const int32_t rsel = rr % kPrR;
+                    const T h0 = max3(mm[0], xx[0], yy[0]), h1 = max3(mm[1], xx[1], yy[1]);
+                    const T h2 = max3(mm[2], xx[2], yy[2]), h3 = max3(mm[3], xx[3], yy[3]);
+                    const T v = rsel == 0 ? h0 : (rsel == 1 ? h1 : (rsel == 2 ? h2 : h3));
+                    score = __shfl_sync(0xffffffffu, v, rr / kPrR);
+                }
+            }
+            // traceback: every lane walks the same path (the direction words come
+            // from a shared window of kPrWin steps of one strip, reloaded by the
+            // whole warp when the path leaves it); lane 0 writes the columns
+            // backwards from the end of the slot
+            __syncwarp();
+            int32_t i = m, jj = n, state = 3;  // 0 M, 1 X, 2 Y, 3 a cell's best state
+            int32_t ws = -1, wt0 = 0;
+            int64_t guard = 2ll * cap + 4;
+            while (i > 0 && jj > 0 && guard-- > 0) {
+                const int32_t s = (i - 1) / kPrStrip;
+                const int32_t t = ((i - 1) % kPrStrip) / kPrR;
+                const int32_t tau = jj - 1 + t;
+                if (s != ws || tau < wt0 || tau >= wt0 + kPrWin) {
+                    ws = s;
+                    wt0 = max(0, tau - kPrWin + 1);
+                    __syncwarp();
+#pragma unroll 8
+                    for (int u = 0; u < kPrWin; u++)
+                        if (wt0 + u < nsteps) win[u * kPrG + lane] = dirs[((int64_t)s * nsteps + wt0 + u) * kPrG + lane];
+                    __syncwarp();
+                }
+                const uint32_t b = (win[(tau - wt0) * kPrG + t] >> (8 * ((i - 1) % kPrR))) & 0xffu;
+                if (state == 3) {
+                    state = (int32_t)(b & 3u);
+                } else if (state == 0) {
+                    if (lane == 0) ops[cap - 1 - L] = 'M';
+                    L++;
+                    i--;
+                    jj--;
+                    state = 3;
+                } else if (state == 1) {
+                    if (lane == 0) ops[cap - 1 - L] = 'X';
+                    L++;
+                    state = (b & 4u) ? 1 : ((b & 8u) ? 0 : 2);
+                    i--;
+                } else {
+                    if (lane == 0) ops[cap - 1 - L] = 'Y';
+                    L++;
+                    state = (b & 16u) ? 2 : ((b & 32u) ? 0 : 1);
+                    jj--;
+                }
+            }
+            if (guard < 0 && lane == 0) atomicOr(a.status, STATUS_CAPACITY);
+            // the border: X(i, 0) and Y(0, j) are single gap runs
+            for (int32_t c = lane; c < i; c += 32) ops[cap - 1 - L - c] = 'X';
+            L += i;
+            for (int32_t c = lane; c < jj; c += 32) ops[cap - 1 - L - c] = 'Y';
+            L += jj;
+            L = min(L, cap);
+        }
+        __syncwarp();
+        // the column maps and the merged profile, column by column in order
+        const uint8_t* col = ops + (cap - L);
+        int32_t* mapP = jb.map;
+        int32_t* mapQ = jb.map + m;
+        int32_t pi = 0, qj = 0;
+        for (int32_t c0 = 0; c0 < L; c0 += 32) {
+            const int32_t c = c0 + lane;
+            const uint8_t op = c < L ? col[c] : 0;
+            const bool inP = c < L && op != 'Y', inQ = c < L && op != 'X';
+            const unsigned bp = __ballot_sync(0xffffffffu, inP), bq = __ballot_sync(0xffffffffu, inQ);
+            const unsigned below = (1u << lane) - 1u;
+            const int32_t i = pi + __popc(bp & below), j = qj + __popc(bq & below);
+            if (inP) mapP[i] = c;
+            if (inQ) mapQ[j] = c;
+            if (c < L) {
+                const uint4* cp = (const uint4*)(jb.prof_p + (int64_t)i * Ap);
+                const uint4* cq = (const uint4*)(jb.prof_q + (int64_t)j * Ap);
+                uint4* cr = (uint4*)(jb.prof_r + (int64_t)c * Ap);
+                for (int32_t h = 0; h < Ap / 8; h++) {
+                    const uint4 u = inP ? cp[h] : make_uint4(0, 0, 0, 0);
+                    const uint4 v = inQ ? cq[h] : make_uint4(0, 0, 0, 0);
+                    // two 16-bit counts per word; their sums stay below 2^16
+                    cr[h] = make_uint4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+                }
+            }
+            pi += __popc(bp);
+            qj += __popc(bq);
+        }
+        if (lane == 0) {
+            a.scores[jb.merge] = (long long)score;
+            a.widths[jb.merge] = L;
+        }
+        __syncwarp();
+    }
+}
+
+// Final columns: each residue's leaf column, moved through the column map of
+// every merge on its way to the root. One warp per bucket position.
+__global__ void k_colmap(int32_t npos, const int32_t* __restrict__ order, const int32_t* __restrict__ len,
+                         const int64_t* __restrict__ pos_off, const int32_t* __restrict__ leaf_gc,
+                         const int32_t* __restrict__ par_merge, const int32_t* __restrict__ par_gc,
+                         const uint8_t* __restrict__ par_side, int32_t* const* __restrict__ map_ptr,
+                         const int32_t* __restrict__ map_split, int32_t max_depth, int32_t* __restrict__ colmap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = wid; q < npos; q += nw) {
+        const int32_t L = len[order[q]];
+        for (int32_t r = lane; r < L; r += 32) {
+            int32_t c = r, g = leaf_gc[q];
+            for (int32_t d = 0; d < max_depth; d++) {
+                const int32_t k = par_merge[g];
+                if (k < 0) break;
+                c = map_ptr[k][(par_side[g] ? map_split[k] : 0) + c];
+                g = par_gc[g];
+            }
+            colmap[pos_off[q] + r] = c;
+        }
+    }
+}
+
+// Bump allocation over a grow-only list of device chunks (profiles and
+// column maps; what a merge writes must outlive its batch).
+struct Arena {
+    sad_ctx* ctx;
+    size_t cur = 0, off = 0;
+    int alloc(size_t bytes, void** out) {
+        bytes = (size_t)round_up((int64_t)std::max<size_t>(bytes, 16), 256);
+        while (cur < ctx->prog_chunks.size() && off + bytes > ctx->prog_chunks[cur].bytes) {
+            cur++;
+            off = 0;
+        }
+        if (cur == ctx->prog_chunks.size()) {
+            Buffer b;
+            b.bytes = std::max<size_t>(bytes, (size_t)64 << 20);
+            cudaError_t e = cudaMalloc(&b.ptr, b.bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_error("cudaMalloc of %zu bytes for the alignment arena failed: %s", b.bytes,
+                          cudaGetErrorString(e));
+                return SAD_ENOMEM;
+            }
+            ctx->prog_chunks.push_back(b);
+            off = 0;
+        }
+        *out = (char*)ctx->prog_chunks[cur].ptr + off;
+        off += bytes;
+        return SAD_OK;
+    }
+};
+
+}  // namespace
+
+}  // namespace sad
+
+extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                                     const int32_t* order, int32_t p, const int64_t* merge_offsets,
+                                     const int32_t* left, const int32_t* right, const int8_t* subst,
+                                     int32_t gap_open, int32_t gap_extend, int32_t* widths, int64_t* merge_scores,
+                                     int32_t* merge_widths, int32_t* colmap, int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(p >= 1, SAD_EINVAL, "p = %d < 1", p);
+    SAD_CHECK(seqs && subst && bucket_offsets && merge_offsets && widths, SAD_EINVAL, "a required pointer is NULL");
+    SAD_CHECK(gap_open <= 0 && gap_extend <= 0, SAD_EINVAL, "gap costs must be <= 0");
+    SAD_CHECK(gap_open >= -1000 && gap_extend >= -1000, SAD_EINVAL, "gap costs below -1000");
+    const int32_t A = seqs->alphabet;
+    SAD_CHECK(A >= 1 && A <= SAD_MAX_ALPHABET, SAD_EINVAL, "alphabet %d outside 1..%d", A, SAD_MAX_ALPHABET);
+    for (int32_t x = 0; x < A; x++)
+        for (int32_t y = 0; y < A; y++)
+            SAD_CHECK(subst[x * A + y] == subst[y * A + x], SAD_EINVAL, "the substitution matrix is not symmetric");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    SAD_RET(status_clear(ctx, stream));
+    DevSeqs S;
+    SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
+    // the layout and the trees on the host
+    std::vector<int32_t> bo((size_t)p + 1);
+    std::vector<int64_t> mo((size_t)p + 1);
+    SAD_RET(arg_to_host(bucket_offsets, 4ull * (p + 1), mem, stream, bo.data()));
+    SAD_RET(arg_to_host(merge_offsets, 8ull * (p + 1), mem, stream, mo.data()));
+    SAD_CHECK(bo[0] == 0 && mo[0] == 0, SAD_EINVAL, "bucket_offsets and merge_offsets must start at 0");
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bo[b + 1] - bo[b];
+        SAD_CHECK(nb >= 0, SAD_EINVAL, "bucket_offsets decreases at %d", b);
+        SAD_CHECK(nb < 65536, SAD_EINVAL, "bucket %d has %lld members (at most 65535)", b, (long long)nb);
+        SAD_CHECK(mo[b + 1] - mo[b] == (nb > 0 ? nb - 1 : 0), SAD_EINVAL,
+                  "merge_offsets of bucket %d do not hold its %lld merges", b, (long long)(nb > 0 ? nb - 1 : 0));
+    }
+    const int32_t npos = bo[p];
+    const int64_t M = mo[p];
+    SAD_CHECK(npos == 0 || order, SAD_EINVAL, "order is NULL");
+    SAD_CHECK(M == 0 || (left && right && merge_scores && merge_widths), SAD_EINVAL, "a required pointer is NULL");
+    std::vector<int32_t> od((size_t)npos), lt((size_t)M), rt((size_t)M);
+    SAD_RET(arg_to_host(order, 4ull * npos, mem, stream, od.data()));
+    SAD_RET(arg_to_host(left, 4ull * M, mem, stream, lt.data()));
+    SAD_RET(arg_to_host(right, 4ull * M, mem, stream, rt.data()));
+    std::vector<int64_t> pos_off((size_t)npos + 1, 0);
+    for (int32_t q = 0; q < npos; q++) {
+        SAD_CHECK(od[q] >= 0 && od[q] < S.n, SAD_EINVAL, "order[%d] = %d outside 0..%d", q, od[q], S.n - 1);
+        pos_off[q + 1] = pos_off[q] + S.h_len[od[q]];
+    }
+    const int64_t T_res = pos_off[npos];
+    SAD_CHECK(T_res == 0 || colmap, SAD_EINVAL, "colmap is NULL");
+    // clusters: global id cl_off[b] + local id (leaves 0..nb-1, merge k -> nb + k)
+    std::vector<int64_t> cl_off((size_t)p + 1, 0);
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bo[b + 1] - bo[b];
+        cl_off[b + 1] = cl_off[b] + (nb > 0 ? 2 * nb - 1 : 0);
+    }
+    const int64_t C = cl_off[p];
+    std::vector<int32_t> width((size_t)C, 0), nmem((size_t)C, 0), level((size_t)C, 0), par_merge((size_t)C, -1),
+        par_gc((size_t)C, -1), leaf_gc((size_t)npos, 0);
+    std::vector<uint8_t> par_side((size_t)C, 0), alive((size_t)C, 0);
+    std::vector<int32_t> merge_level((size_t)M, 0), merge_bucket((size_t)M, 0);
+    int32_t max_level = 0, max_depth = 1;
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bo[b + 1] - bo[b];
+        for (int64_t u = 0; u < nb; u++) {
+            const int64_t g = cl_off[b] + u;
+            width[g] = S.h_len[od[bo[b] + u]];
+            nmem[g] = 1;
+            alive[g] = 1;
+            leaf_gc[bo[b] + u] = (int32_t)g;
+        }
+        for (int64_t k = 0; k + 1 < nb; k++) {
+            const int64_t mi = mo[b] + k;
+            const int32_t l = lt[mi], r = rt[mi];
+            SAD_CHECK(l >= 0 && r >= 0 && l < nb + k && r < nb + k && l != r, SAD_EINVAL,
+                      "merge %lld of bucket %d joins clusters %d and %d, not two of 0..%lld", (long long)k, b, l, r,
+                      (long long)(nb + k - 1));
+            const int64_t gl = cl_off[b] + l, gr = cl_off[b] + r, gn = cl_off[b] + nb + k;
+            SAD_CHECK(alive[gl] && alive[gr], SAD_EINVAL, "merge %lld of bucket %d reuses a merged cluster",
+                      (long long)k, b);
+            alive[gl] = alive[gr] = 0;
+            alive[gn] = 1;
+            nmem[gn] = nmem[gl] + nmem[gr];
+            level[gn] = 1 + std::max(level[gl], level[gr]);
+            merge_level[mi] = level[gn];
+            merge_bucket[mi] = b;
+            max_level = std::max(max_level, level[gn]);
+            par_merge[gl] = par_merge[gr] = (int32_t)mi;
+            par_gc[gl] = par_gc[gr] = (int32_t)gn;
+            par_side[gl] = 0;
+            par_side[gr] = 1;
+        }
+    }
+    max_depth = max_level + 1;
+    int32_t smax = 0;
+    for (int32_t t = 0; t < A * A; t++) smax = std::max(smax, (int32_t)std::abs((int)subst[t]));
+    const int64_t cmax = std::max<int64_t>(smax, (int64_t)-gap_open - gap_extend);
+    const int32_t Ap = (int32_t)round_up(A, 8);
+    // device tables of the call (copied once), outputs staged in host mode
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return o;
+    };
+    const size_t o_sub = carve(1024), o_od = carve(4ull * (npos + 1)), o_pos = carve(8ull * (npos + 1)),
+                 o_leaf = carve(4ull * (npos + 1)), o_pm = carve(4ull * (C + 1)), o_pg = carve(4ull * (C + 1)),
+                 o_ps = carve(C + 16), o_mp = carve(8ull * (M + 1)), o_ms = carve(4ull * (M + 1)),
+                 o_sc = carve(8ull * (M + 1)), o_w = carve(4ull * (M + 1)),
+                 o_cm = carve(mem == SAD_MEM_HOST ? 4ull * (T_res + 1) : 0);
+    void* wsp = nullptr;
+    SAD_RET(workspace(ctx, WS_PROG, off, stream, &wsp));
+    char* w = (char*)wsp;
+    int8_t* d_sub = (int8_t*)(w + o_sub);
+    int32_t* d_od = (int32_t*)(w + o_od);
+    int64_t* d_pos = (int64_t*)(w + o_pos);
+    long long* d_sc = mem == SAD_MEM_HOST ? (long long*)(w + o_sc) : (long long*)merge_scores;
+    int32_t* d_mw = mem == SAD_MEM_HOST ? (int32_t*)(w + o_w) : merge_widths;
+    int32_t* d_cm = mem == SAD_MEM_HOST ? (int32_t*)(w + o_cm) : colmap;
+    if (M == 0) {
+        d_sc = (long long*)(w + o_sc);
+        d_mw = (int32_t*)(w + o_w);
+    }
+    SAD_CUDA(cudaMemcpyAsync(d_sub, subst, (size_t)A * A, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_od, od.data(), 4ull * npos, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_pos, pos_off.data(), 8ull * (npos + 1), cudaMemcpyHostToDevice, stream));
+    // leaf profiles
+    Arena arena{ctx};
+    void* leaf_prof = nullptr;
+    SAD_RET(arena.alloc(2ull * Ap * std::max<int64_t>(T_res, 1), &leaf_prof));
+    std::vector<const uint16_t*> prof((size_t)C, nullptr);
+    for (int32_t b = 0; b < p; b++)
+        for (int32_t u = 0; u < bo[b + 1] - bo[b]; u++)
+            prof[cl_off[b] + u] = (const uint16_t*)leaf_prof + pos_off[bo[b] + u] * Ap;
+    TraceScope ts(ctx, SAD_STAGE_PROG, stream);
+    if (npos > 0) {
+        const int64_t blocks = std::min<int64_t>(((int64_t)npos * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
+        k_leaf_profiles<<<(unsigned)blocks, 256, 0, stream>>>(S.res, S.pad_off, S.len, d_od, npos, d_pos, Ap,
+                                                              (uint16_t*)leaf_prof);
+        SAD_LAUNCHED();
+    }
+    // merges level by level
+    std::vector<std::vector<int32_t>> by_level((size_t)max_level + 1);
+    for (int64_t mi = 0; mi < M; mi++) by_level[merge_level[mi]].push_back((int32_t)mi);
+    std::vector<int32_t*> map_ptr((size_t)M, nullptr);
+    std::vector<int32_t> map_split((size_t)M, 0);
+    std::vector<int32_t> h_mw((size_t)M + 1, 0);
+    const int64_t budget = (int64_t)1 << 30;  // bytes of cell scores and directions per batch
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<int32_t>));
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<long long>));
+    std::vector<ProgJob> jobs;
+    for (int32_t lv = 1; lv <= max_level; lv++) {
+        const std::vector<int32_t>& ms = by_level[lv];
+        for (size_t j0 = 0; j0 < ms.size();) {
+            jobs.clear();
+            int64_t s_vecs = 0, d_words = 0, maxw = 1;
+            int32_t tiles = 0;
+            bool wide = false;
+            size_t j1 = j0;
+            while (j1 < ms.size()) {
+                const int32_t mi = ms[j1];
+                const int32_t b = merge_bucket[mi];
+                const int64_t nb = bo[b + 1] - bo[b];
+                const int64_t k = mi - mo[b];
+                const int64_t gl = cl_off[b] + lt[mi], gr = cl_off[b] + rt[mi], gn = cl_off[b] + nb + k;
+                const int64_t m = width[gl], n = width[gr];
+                const bool cells = m > 0 && n > 0;
+                const int64_t strips = (m + kPrStrip - 1) / kPrStrip;
+                // score streams plus the look-ahead of the last lane
+                const int64_t sv = cells ? strips * kPrG * (n + kPrG - 1) + 2 * kPrPre : 0;
+                const int64_t dw = cells ? strips * (n + kPrG - 1) * kPrG : 0;
+                const int64_t bytes_here = 16 * (s_vecs + sv) + 4 * (d_words + dw);
+                if (j1 > j0 && bytes_here > budget) break;
+                const int64_t pq = (int64_t)nmem[gl] * nmem[gr];
+                SAD_CHECK(pq * smax < (1ll << 31), SAD_EINVAL,
+                          "merge %d: %lld member pairs x max |S| exceed the 32-bit cell scores", mi, (long long)pq);
+                if ((m + n + 2 * kPrStrip) * pq * cmax >= (1ll << 28)) wide = true;
+                ProgJob jb;
+                jb.prof_p = prof[gl];
+                jb.prof_q = prof[gr];
+                void* pr = nullptr;
+                SAD_RET(arena.alloc(2ull * Ap * (m + n), &pr));
+                jb.prof_r = (uint16_t*)pr;
+                void* mp = nullptr;
+                SAD_RET(arena.alloc(4ull * (m + n), &mp));
+                jb.map = (int32_t*)mp;
+                jb.s_off = s_vecs;
+                jb.d_off = d_words;
+                jb.m = (int32_t)m;
+                jb.n = (int32_t)n;
+                jb.np = nmem[gl];
+                jb.nq = nmem[gr];
+                jb.merge = mi;
+                jb.tile0 = tiles;
+                jobs.push_back(jb);
+                prof[gn] = jb.prof_r;
+                map_ptr[mi] = jb.map;
+                map_split[mi] = (int32_t)m;
+                s_vecs += sv;
+                d_words += dw;
+                tiles += cells ? (int32_t)(strips * ((n + 31) / 32)) : 0;
+                maxw = std::max(maxw, std::max(m, n));
+                j1++;
+            }
+            const int32_t nj = (int32_t)jobs.size();
+            // shared memory of one DP warp: strip boundary, traceback window, columns
+            const int64_t warp_smem = (wide ? bnd_bytes<long long>((int32_t)maxw) : bnd_bytes<int32_t>((int32_t)maxw)) +
+                                      win_bytes() + ops_bytes((int32_t)maxw);
+            const int64_t warps_cta = std::min<int64_t>(kPrWarps, ((int64_t)ctx->smem_optin - 1024) / warp_smem);
+            SAD_CHECK(warps_cta >= 1, SAD_EINVAL, "profiles of %lld columns exceed the DP kernel's shared memory",
+                      (long long)maxw);
+            const int64_t grid_dp = std::min<int64_t>(((int64_t)nj + warps_cta - 1) / warps_cta,
+                                                      (int64_t)ctx->num_sms * 8);
+            size_t lo = 0;
+            auto lcarve = [&](size_t bytes) {
+                const size_t o = lo;
+                lo = (size_t)round_up((int64_t)(lo + bytes), 256);
+                return o;
+            };
+            const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(16ull * s_vecs + 16),
+                         l_d = lcarve(4ull * d_words + 4);
+            void* lv_ws = nullptr;
+            SAD_RET(workspace(ctx, WS_PROG_LEVEL, lo, stream, &lv_ws));
+            char* lw = (char*)lv_ws;
+            SAD_CUDA(cudaMemcpyAsync(lw + l_jobs, jobs.data(), sizeof(ProgJob) * nj, cudaMemcpyHostToDevice, stream));
+            ProgArgs pa;
+            pa.jobs = (const ProgJob*)(lw + l_jobs);
+            pa.njobs = nj;
+            pa.ntiles = tiles;
+            pa.Ap = Ap;
+            pa.alphabet = A;
+            pa.go = gap_open;
+            pa.ge = gap_extend;
+            pa.subst = d_sub;
+            pa.S = (int4*)(lw + l_s);
+            pa.dirs = (uint32_t*)(lw + l_d);
+            pa.scores = d_sc;
+            pa.widths = d_mw;
+            pa.status = ctx->d_status;
+            pa.maxw = (int32_t)maxw;
+            pa.warp_smem = (int32_t)warp_smem;
+            if (tiles > 0) {
+                const unsigned g1 = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx->num_sms * 8);
+                k_prof_scores<<<g1, kScThreads, 0, stream>>>(pa);
+                SAD_LAUNCHED();
+            }
+            const size_t dyn = (size_t)(warp_smem * warps_cta);
+            if (wide) {
+                k_prof_dp<long long><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), dyn, stream>>>(pa);
+            } else {
+                k_prof_dp<int32_t><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), dyn, stream>>>(pa);
+            }
+            SAD_LAUNCHED();
+            // the new widths, for the next level's layout (the jobs' table copy
+            // from pageable memory has been consumed when this returns)
+            SAD_CUDA(cudaMemcpyAsync(h_mw.data(), d_mw, 4ull * std::max<int64_t>(M, 1), cudaMemcpyDeviceToHost,
+                                     stream));
+            SAD_CUDA(cudaStreamSynchronize(stream));
+            for (const ProgJob& jb : jobs) {
+                const int32_t b = merge_bucket[jb.merge];
+                const int64_t nb = bo[b + 1] - bo[b];
+                const int64_t gn = cl_off[b] + nb + (jb.merge - mo[b]);
+                SAD_CHECK(h_mw[jb.merge] >= std::max(jb.m, jb.n) && h_mw[jb.merge] <= jb.m + jb.n, SAD_ECUDA,
+                          "merge %d returned width %d for widths %d and %d", jb.merge, h_mw[jb.merge], jb.m, jb.n);
+                width[gn] = h_mw[jb.merge];
+            }
+            j0 = j1;
+        }
+    }
+    // the final column of every residue, and the widths of the buckets' alignments
+    std::vector<int32_t> h_w((size_t)p, 0);
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = bo[b + 1] - bo[b];
+        h_w[b] = nb > 0 ? width[cl_off[b] + 2 * nb - 2] : 0;
+    }
+    if (npos > 0) {
+        int32_t* d_leaf = (int32_t*)(w + o_leaf);
+        int32_t* d_pm = (int32_t*)(w + o_pm);
+        int32_t* d_pg = (int32_t*)(w + o_pg);
+        uint8_t* d_ps = (uint8_t*)(w + o_ps);
+        int32_t** d_mp = (int32_t**)(w + o_mp);
+        int32_t* d_msp = (int32_t*)(w + o_ms);
+        SAD_CUDA(cudaMemcpyAsync(d_leaf, leaf_gc.data(), 4ull * npos, cudaMemcpyHostToDevice, stream));
+        SAD_CUDA(cudaMemcpyAsync(d_pm, par_merge.data(), 4ull * C, cudaMemcpyHostToDevice, stream));
+        SAD_CUDA(cudaMemcpyAsync(d_pg, par_gc.data(), 4ull * C, cudaMemcpyHostToDevice, stream));
+        SAD_CUDA(cudaMemcpyAsync(d_ps, par_side.data(), (size_t)C, cudaMemcpyHostToDevice, stream));
+        if (M > 0) {
+            SAD_CUDA(cudaMemcpyAsync(d_mp, map_ptr.data(), 8ull * M, cudaMemcpyHostToDevice, stream));
+            SAD_CUDA(cudaMemcpyAsync(d_msp, map_split.data(), 4ull * M, cudaMemcpyHostToDevice, stream));
+        }
+        const int64_t blocks = std::min<int64_t>(((int64_t)npos * 32 + 255) / 256, (int64_t)ctx->num_sms * 16);
+        k_colmap<<<(unsigned)blocks, 256, 0, stream>>>(npos, d_od, S.len, d_pos, d_leaf, d_pm, d_pg, d_ps, d_mp,
+                                                       d_msp, max_depth, d_cm);
+        SAD_LAUNCHED();
+    }
+    // outputs (host mode: copied back; device mode: widths from the host table)
+    if (mem == SAD_MEM_HOST) {
+        memcpy(widths, h_w.data(), 4ull * p);
+        if (M > 0) {
+            SAD_CUDA(cudaMemcpyAsync(merge_scores, d_sc, 8ull * M, cudaMemcpyDeviceToHost, stream));
+            SAD_CUDA(cudaMemcpyAsync(merge_widths, d_mw, 4ull * M, cudaMemcpyDeviceToHost, stream));
+        }
+        if (T_res > 0) SAD_CUDA(cudaMemcpyAsync(colmap, d_cm, 4ull * T_res, cudaMemcpyDeviceToHost, stream));
+    } else {
+        SAD_CUDA(cudaMemcpyAsync(widths, h_w.data(), 4ull * p, cudaMemcpyHostToDevice, stream));
+    }
+    SAD_RET(status_check(ctx, stream));
+    return SAD_OK;
+}

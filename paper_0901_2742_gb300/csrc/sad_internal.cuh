@@ -82,6 +82,8 @@ enum Slot : int {
     WS_TRACE_DIRS,     // traceback direction words
     WS_KBLOCKS,        // per 128-row panel of the planes: bitmap of nonzero 128-byte k-blocks
     WS_TREE,           // guide trees: tables, cluster matrices, staging
+    WS_PROG,           // progressive alignment: call tables and staged outputs
+    WS_PROG_LEVEL,     // progressive alignment: one batch of merges (jobs, scores, directions)
     WS_NUM_SLOTS
 };
 
@@ -145,6 +147,7 @@ struct sad_ctx {
     std::vector<cudaEvent_t> event_pool;
     unsigned long long* gemm_work = nullptr;  // device: k-blocks x BN the last plane GEMM ran
     int64_t gemm_dense_units = 0;             // k-blocks x BN of all its tiles
+    std::vector<sad::Buffer> prog_chunks;     // progressive alignment: profile and column-map arena
 };
 
 namespace sad {

@@ -88,6 +88,7 @@ def load():
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
         "sad_kmer_gemm_work": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "sad_guide_trees": (ctypes.c_int, [P, P, i32, P, P, P, P, P, P, P, i32, P]),
+        "sad_progressive_align": (ctypes.c_int, [P, P, P, P, i32, P, P, P, P, i32, i32, P, P, P, P, i32, P]),
         "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -197,7 +198,7 @@ def _ctx(ctx):
 
 
 STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global", "align",
-          "tree")
+          "tree", "prog")
 
 
 def trace_enable(on: bool = True, ctx=None):
@@ -410,6 +411,34 @@ def align_pairs(residues, offsets, alphabet: int, pairs, subst, gap_open: int, g
                                   gap_extend, _ptr(sc), _ptr(oo), _ptr(ops), cap, _ptr(ol), mem,
                                   _stream(stream, mem)))
     return dict(scores=sc[:npairs], ops_offsets=oo, ops=ops, ops_len=ol[:npairs])
+
+
+def progressive_align(residues, offsets, alphabet: int, bucket_offsets, order, merge_offsets, left, right, subst,
+                      gap_open: int, gap_extend: int, ctx=None, stream=None) -> dict:
+    """sad_progressive_align: dict(widths[p], merge_scores[M], merge_widths[M],
+    colmap) -- one multiple alignment per bucket along its guide tree; colmap
+    gives the column of every residue of order[0], order[1], ... in turn."""
+    mem = _mode(residues, offsets, bucket_offsets, order, merge_offsets)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    bo, od = _as(bucket_offsets, np.int32, mem), _as(order, np.int32, mem)
+    mo, lt, rt = _as(merge_offsets, np.int64, mem), _as(left, np.int32, mem), _as(right, np.int32, mem)
+    S = _host(subst, np.int8)
+    p = bo.shape[0] - 1
+    offs_h = offs.cpu().numpy() if mem == MEM_DEVICE else offs
+    od_h = od.cpu().numpy() if mem == MEM_DEVICE else od
+    mo_h = mo.cpu().numpy() if mem == MEM_DEVICE else mo
+    lens = np.diff(offs_h)
+    ids = od_h[(od_h >= 0) & (od_h < len(lens))]   # the library reports ids out of range
+    total = int(lens[ids].sum())
+    M = int(mo_h[-1])
+    widths = _empty(p, np.int32, mem, offs)
+    ms, mw = _empty(max(M, 1), np.int64, mem, offs), _empty(max(M, 1), np.int32, mem, offs)
+    cm = _empty(max(total, 1), np.int32, mem, offs)
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_progressive_align(_ctx(ctx), ctypes.byref(ss), _ptr(bo), _ptr(od), p, _ptr(mo), _ptr(lt),
+                                        _ptr(rt), S.ctypes.data, gap_open, gap_extend, _ptr(widths), _ptr(ms),
+                                        _ptr(mw), _ptr(cm), mem, _stream(stream, mem)))
+    return dict(widths=widths, merge_scores=ms[:M], merge_widths=mw[:M], colmap=cm[:total])
 
 
 def columns(out: dict, k: int) -> str:
