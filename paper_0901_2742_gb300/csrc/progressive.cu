@@ -24,16 +24,17 @@
 // tree, so the host runs them level by level (a merge's level is one more
 // than its children's), all buckets' merges of a level in one batch, and
 // reads the new widths back after each level. Per batch:
-//   k_prof_scores  tiles of 128 rows x 32 columns over all SMs: PB[j][a] =
+//   k_prof_scores  tiles of 64 rows x 32 columns over all SMs: PB[j][a] =
 //                  sum_b S[a][b] cntQ[j][b] in shared memory, then s(i, j) =
 //                  sum_a cntP[i][a] PB[j][a], laid out as one stream per DP lane
-//   k_prof_dp<T>   one warp per merge: the lanes hold 4 rows each of a strip of
-//                  128 rows and sweep the columns as a diagonal wavefront (M, X
-//                  and Y of a lane's bottom row move one lane down per step);
-//                  a lane loads its scores 8 steps ahead; every cell stores one
-//                  byte of tie-resolved directions; the strip boundary, a window
-//                  of direction words for the walk back and the columns sit in
-//                  shared memory; then the warp writes the column maps and the
+//   k_prof_dp<T>   one CTA per merge: its rows are cut into strips of 64, one
+//                  warp per strip (up to 8 side by side, each following the one
+//                  above through a shared boundary row); the lanes hold 2 rows
+//                  each and sweep the columns as a diagonal wavefront (M, X and
+//                  Y of a lane's bottom row move one lane down per step); a lane
+//                  loads its scores 8 steps ahead; every cell stores one byte of
+//                  tie-resolved directions; warp 0 walks them back through a
+//                  shared window, then all warps write the column maps and the
 //                  merged profile. T is int32 when the host proves every value
 //                  fits, else int64.
 // At the end k_colmap composes each residue's column maps up the tree.
@@ -49,10 +50,10 @@ namespace sad {
 
 namespace {
 
-constexpr int kPrR = 4;                  // rows per lane
+constexpr int kPrR = 2;                  // rows per lane
 constexpr int kPrG = 32;                 // lanes per merge (one warp)
 constexpr int kPrStrip = kPrR * kPrG;    // rows per strip
-constexpr int kPrWarps = 4;              // warps per CTA of the DP kernel
+constexpr int kPrWarps = 8;              // most warps (strips side by side) per merge
 
 // One merge of a batch.
 struct ProgJob {
@@ -60,8 +61,8 @@ struct ProgJob {
     const uint16_t* prof_q;  // Q: n columns
     uint16_t* prof_r;        // the merged cluster (capacity m + n columns)
     int32_t* map;            // m entries for P's columns, then n for Q's
-    int64_t s_off;           // cell-score streams (int4): strips x 32 lanes x (n + 31) steps, then padding
-    int64_t d_off;           // direction words (uint32, strips x (n + 31) x 32)
+    int64_t s_off;           // cell-score streams (int2): strips x 32 lanes x (n + 31) steps, then padding
+    int64_t d_off;           // direction words (uint16, strips x (n + 31) x 32)
     int32_t m, n, np, nq;
     int32_t merge;           // index into the per-merge outputs
     int32_t tile0;           // first score tile (a job has strips x ceil(n / 32) of them)
@@ -75,16 +76,16 @@ struct ProgArgs {
     int32_t alphabet;
     int32_t go, ge;
     const int8_t* subst;
-    int4* S;
-    uint32_t* dirs;
+    int2* S;
+    uint16_t* dirs;
     long long* scores;       // per merge
     int32_t* widths;         // per merge
     uint32_t* status;
     int32_t maxw;            // widest profile of the batch
-    int32_t warp_smem;       // shared bytes per warp of the DP kernel
+    int32_t warp_smem;       // dynamic shared bytes of one DP CTA
 };
 
-constexpr int kPrWin = 32;       // steps of direction words the traceback holds in shared memory
+constexpr int kPrWin = 128;      // steps of direction words the traceback holds in shared memory
 constexpr int kPrPre = 8;        // steps of cell scores a lane loads ahead
 
 template <typename T>
@@ -97,14 +98,23 @@ __device__ __forceinline__ long long neg_inf<long long>() { return -(1ll << 60);
 template <typename T>
 __device__ __forceinline__ T max3(T a, T b, T c) { return max(a, max(b, c)); }
 
+// max(a, b) and whether a >= b: one DPX instruction for 32-bit values.
+__device__ __forceinline__ int32_t bmax(int32_t a, int32_t b, bool& ge) { return __vibmax_s32(a, b, &ge); }
+__device__ __forceinline__ long long bmax(long long a, long long b, bool& ge) {
+    ge = a >= b;
+    return ge ? a : b;
+}
+
 // Shared-memory layout of one DP warp: strip boundary (3 values per column),
 // the traceback's window of direction words, the alignment columns.
 template <typename T>
 __host__ __device__ inline int64_t bnd_bytes(int32_t maxw) {
     return (3ll * (maxw + 2) * (int64_t)sizeof(T) + 15) / 16 * 16;
 }
-__host__ __device__ inline int64_t win_bytes() { return 4ll * kPrWin * kPrG; }
+__host__ __device__ inline int64_t win_bytes() { return 2ll * kPrWin * kPrG; }
 __host__ __device__ inline int64_t ops_bytes(int32_t maxw) { return (2ll * maxw + 16 + 15) / 16 * 16; }
+// chunks of 32 alignment columns (at most 2 maxw columns), rounded to 4 for alignment
+__host__ __device__ inline int32_t chunk_count(int32_t maxw) { return ((2 * maxw + 31) / 32 + 4) / 4 * 4; }
 
 // Leaf profiles: one column per residue, a count of 1 for its letter.
 __global__ void k_leaf_profiles(const uint8_t* __restrict__ res, const int64_t* __restrict__ pad_off,
@@ -125,10 +135,10 @@ __global__ void k_leaf_profiles(const uint8_t* __restrict__ res, const int64_t* 
     }
 }
 
-// Cell scores of one tile: 128 rows (one strip) x 32 columns of one merge.
+// Cell scores of one tile: 64 rows (one strip) x 32 columns of one merge.
 // PB[j][a] = sum_b S[a][b] cntQ[j][b] is formed in shared memory for the
 // tile's columns, then s(i, j) = sum_a cntP[i][a] PB[j][a]; thread (g, c4)
-// holds rows 4g..4g+3 and columns 4c4..4c4+3. Lane g of the DP warp reads its
+// holds rows 2g, 2g+1 and columns 4c4..4c4+3. Lane g of the DP warp reads its
 // rows' scores as one stream over its steps: column j (1-based) sits at step
 // tau = j - 1 + g.
 constexpr int kScThreads = 256;
@@ -185,227 +195,325 @@ k_prof_scores(ProgArgs a) {
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[r][c] += pv[r] * qv[c];
         }
-        int4* out = a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
+        int2* out = a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const int32_t j0 = cb * 32 + c4 * 4 + c;  // 0-based column
-            if (j0 < n) out[j0 + g] = make_int4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+            if (j0 < n) out[j0 + g] = make_int2(acc[0][c], acc[1][c]);
         }
     }
 }
 
-__device__ __forceinline__ int32_t take_row(const int4& v, int r) {
-    return r == 0 ? v.x : (r == 1 ? v.y : (r == 2 ? v.z : v.w));
-}
+__device__ __forceinline__ int32_t take_row(const int2& v, int r) { return r == 0 ? v.x : v.y; }
 
 // Direction byte of a cell: bits 0-1 its best state (0 M, 1 X, 2 Y); bit 2
 // X extends; bit 3 X opens from M (else from Y); bit 4 Y extends; bit 5 Y
 // opens from M (else from X).
+//
+// One CTA per merge, W = blockDim.x / 32 warps: warp w takes strips w, w + W,
+// ... in order. The bottom row of strip s goes to boundary slot s mod W with
+// a progress count (the last column written); the warp of strip s + 1 reads
+// it one column at a time once the count has passed that column. A slot is
+// rewritten by strip s + W, which reaches a column only after strip s + 1 has
+// read it, so W slots suffice. Then warp 0 walks the directions back.
+constexpr int kMaxStrips = 256;
+constexpr int64_t kSpinLimit = 1ll << 22;
+
 template <typename T>
 __global__ void __launch_bounds__(kPrG * kPrWarps)
 k_prof_dp(ProgArgs a) {
     extern __shared__ __align__(16) unsigned char psm[];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-    const int64_t nslots = (int64_t)gridDim.x * (blockDim.x >> 5);
-    unsigned char* my = psm + (int64_t)wib * a.warp_smem;
-    T* bnd = (T*)my;
-    uint32_t* win = (uint32_t*)(my + bnd_bytes<T>(a.maxw));
-    uint8_t* ops = my + bnd_bytes<T>(a.maxw) + win_bytes();
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int64_t slot_bytes = bnd_bytes<T>(a.maxw);
+    volatile int32_t* prog = (volatile int32_t*)(psm + W * slot_bytes);
+    T* score_sh = (T*)(psm + W * slot_bytes + 4 * kMaxStrips);
+    int32_t* len_sh = (int32_t*)(psm + W * slot_bytes + 4 * kMaxStrips + 8);
+    uint16_t* win = (uint16_t*)(psm + W * slot_bytes + 4 * kMaxStrips + 16);
+    uint8_t* ops = psm + W * slot_bytes + 4 * kMaxStrips + 16 + win_bytes();
+    int32_t* chP = (int32_t*)(ops + ops_bytes(a.maxw));
+    int32_t* chQ = chP + chunk_count(a.maxw);
     const T NEG = neg_inf<T>();
     const int32_t Ap = a.Ap;
-    for (int64_t k = slot; k < a.njobs; k += nslots) {
+    for (int64_t k = blockIdx.x; k < a.njobs; k += gridDim.x) {
         const ProgJob& jb = a.jobs[k];
         const int32_t m = jb.m, n = jb.n;
         const T w = (T)jb.np * (T)jb.nq;
         const T gop = w * (T)a.go, gex = w * (T)a.ge, goe = gop + gex;
         const int32_t cap = m + n;
-        T score = 0;
-        int32_t L = 0;
-        if (m == 0 || n == 0) {  // one gap run, or nothing
-            for (int32_t c = lane; c < cap; c += 32) ops[c] = m == 0 ? 'Y' : 'X';
-            score = cap == 0 ? (T)0 : gop + (T)cap * gex;
-            L = cap;
-        } else {
-            const int32_t strips = (m + kPrStrip - 1) / kPrStrip;
-            const int32_t nsteps = n + kPrG - 1;
-            uint32_t* dirs = a.dirs + jb.d_off;
-            for (int32_t s = 0; s < strips; s++) {
-                const int32_t row0 = s * kPrStrip + lane * kPrR;  // rows row0+1 .. row0+4 (1-based)
-                T mm[kPrR], xx[kPrR], yy[kPrR];                    // values at the previous column
+        const int32_t strips = (m + kPrStrip - 1) / kPrStrip;
+        const int32_t nsteps = n + kPrG - 1;
+        uint16_t* dirs = a.dirs + jb.d_off;
+        const bool cells = m > 0 && n > 0;
+        for (int t = threadIdx.x; t < strips; t += blockDim.x) prog[t] = 0;
+        __syncthreads();
+        for (int32_t s = warp; cells && s < strips; s += W) {
+            const T* bin = (const T*)(psm + ((s + W - 1) % W) * slot_bytes);
+            T* bout = (T*)(psm + (s % W) * slot_bytes);
+            const int32_t row0 = s * kPrStrip + lane * kPrR;  // rows row0+1 .. row0+2 (1-based)
+            T mm[kPrR], xx[kPrR], yy[kPrR], hh[kPrR];          // values at the previous column
 #pragma unroll
-                for (int r = 0; r < kPrR; r++) {
-                    mm[r] = NEG;
-                    xx[r] = gop + (T)(row0 + r + 1) * gex;  // X(i, 0)
-                    yy[r] = NEG;
-                }
-                T hdiag = row0 == 0 ? (T)0 : gop + (T)row0 * gex;  // H(row0, 0)
-                T min_ = NEG, xin = NEG, yin = NEG;                // (row0, j) from above
-                const bool last_strip = s == strips - 1;
-                // this lane's score stream (the job's padding keeps the look-ahead in bounds)
-                const int4* Sl = a.S + jb.s_off + ((int64_t)s * kPrG + lane) * nsteps;
-                int4 cur[kPrPre], nxt[kPrPre];
+            for (int r = 0; r < kPrR; r++) {
+                mm[r] = NEG;
+                xx[r] = gop + (T)(row0 + r + 1) * gex;  // X(i, 0)
+                yy[r] = NEG;
+                hh[r] = xx[r];
+            }
+            T hdiag = row0 == 0 ? (T)0 : gop + (T)row0 * gex;  // H(row0, 0)
+            T min_ = NEG, xin = NEG, yin = NEG;                // (row0, j) from above
+            const bool last_strip = s == strips - 1;
+            int32_t avail = s == 0 ? n : 0;                    // columns of the strip above known written
+            // this lane's score stream (the job's padding keeps the look-ahead in bounds)
+            const int2* Sl = a.S + jb.s_off + ((int64_t)s * kPrG + lane) * nsteps;
+            int2 cur[kPrPre], nxt[kPrPre];
 #pragma unroll
-                for (int u = 0; u < kPrPre; u++) cur[u] = Sl[u];
-                for (int32_t tau0 = 0; tau0 < nsteps; tau0 += kPrPre) {
+            for (int u = 0; u < kPrPre; u++) cur[u] = Sl[u];
+            for (int32_t tau0 = 0; tau0 < nsteps; tau0 += kPrPre) {
 #pragma unroll
-                    for (int u = 0; u < kPrPre; u++) nxt[u] = Sl[tau0 + kPrPre + u];
+                for (int u = 0; u < kPrPre; u++) nxt[u] = Sl[tau0 + kPrPre + u];
 #pragma unroll
-                    for (int u = 0; u < kPrPre; u++) {
-                        const int32_t tau = tau0 + u;
-                        if (tau >= nsteps) break;
-                        if (lane == 0 && tau < n) {
-                            if (s == 0) {
-                                min_ = NEG;
-                                xin = NEG;
-                                yin = gop + (T)(tau + 1) * gex;  // Y(0, j)
-                            } else {
-                                min_ = bnd[3 * (tau + 1)];
-                                xin = bnd[3 * (tau + 1) + 1];
-                                yin = bnd[3 * (tau + 1) + 2];
+                for (int u = 0; u < kPrPre; u++) {
+                    const int32_t tau = tau0 + u;
+                    if (tau >= nsteps) break;
+                    if (lane == 0 && tau < n) {
+                        if (s == 0) {
+                            min_ = NEG;
+                            xin = NEG;
+                            yin = gop + (T)(tau + 1) * gex;  // Y(0, j)
+                        } else {
+                            if (avail < tau + 1) {  // wait (bounded) for the strip above
+                                int64_t spins = 0;
+                                while ((avail = prog[s - 1]) < tau + 1 && ++spins < kSpinLimit) __nanosleep(32);
+                                if (spins >= kSpinLimit) {
+                                    atomicOr(a.status, STATUS_TIMEOUT);
+                                    avail = n;
+                                }
+                                __threadfence_block();
                             }
+                            const volatile T* vb = bin;
+                            min_ = vb[3 * (tau + 1)];
+                            xin = vb[3 * (tau + 1) + 1];
+                            yin = vb[3 * (tau + 1) + 2];
                         }
-                        const int32_t j = tau - lane + 1;
-                        T mo = min_, xo = xin, yo = yin;
-                        if (j >= 1 && j <= n) {
-                            const int4 sv = cur[u];
-                            T hd = hdiag, am = min_, ax = xin, ay = yin;
-                            uint32_t bits = 0;
-#pragma unroll
-                            for (int r = 0; r < kPrR; r++) {
-                                const T hleft = max3(mm[r], xx[r], yy[r]);  // H(i, j-1)
-                                const T M = hd + (T)take_row(sv, r);
-                                const T oX = max(am, ay) + goe, eX = ax + gex;
-                                const T X = max(oX, eX);
-                                const T oY = max(mm[r], xx[r]) + goe, eY = yy[r] + gex;
-                                const T Y = max(oY, eY);
-                                const uint32_t best = (M >= X && M >= Y) ? 0u : (X >= Y ? 1u : 2u);
-                                const uint32_t b = best | (eX >= oX ? 4u : 0u) | (am >= ay ? 8u : 0u) |
-                                                   (eY >= oY ? 16u : 0u) | (mm[r] >= xx[r] ? 32u : 0u);
-                                bits |= b << (8 * r);
-                                hd = hleft;
-                                mm[r] = M;
-                                xx[r] = X;
-                                yy[r] = Y;
-                                am = M;
-                                ax = X;
-                                ay = Y;
-                            }
-                            dirs[((int64_t)s * nsteps + tau) * kPrG + lane] = bits;
-                            hdiag = max3(min_, xin, yin);  // H(row0, j): the next column's diagonal
-                            mo = am;
-                            xo = ax;
-                            yo = ay;
-                            if (!last_strip && lane == kPrG - 1) {
-                                bnd[3 * j] = mo;
-                                bnd[3 * j + 1] = xo;
-                                bnd[3 * j + 2] = yo;
-                            }
-                        }
-                        min_ = __shfl_up_sync(0xffffffffu, mo, 1);
-                        xin = __shfl_up_sync(0xffffffffu, xo, 1);
-                        yin = __shfl_up_sync(0xffffffffu, yo, 1);
                     }
+                    const int32_t j = tau - lane + 1;
+                    T mo = min_, xo = xin, yo = yin;
+                    if (j >= 1 && j <= n) {
+                        const int2 sv = cur[u];
+                        T hd = hdiag, am = min_, ax = xin, ay = yin;
+                        uint32_t bits = 0;
 #pragma unroll
-                    for (int u = 0; u < kPrPre; u++) cur[u] = nxt[u];
+                        for (int r = 0; r < kPrR; r++) {
+                            bool xs, xe, ys, ye, xy, mb;
+                            const T M = hd + (T)take_row(sv, r);
+                            const T X = bmax(ax + gex, bmax(am, ay, xs) + goe, xe);
+                            const T Y = bmax(yy[r] + gex, bmax(mm[r], xx[r], ys) + goe, ye);
+                            const T H = bmax(M, bmax(X, Y, xy), mb);
+                            const uint32_t b = (mb ? 0u : (xy ? 1u : 2u)) | (xe ? 4u : 0u) | (xs ? 8u : 0u) |
+                                               (ye ? 16u : 0u) | (ys ? 32u : 0u);
+                            bits |= b << (8 * r);
+                            hd = hh[r];  // H(i, j-1): the next row's diagonal
+                            mm[r] = M;
+                            xx[r] = X;
+                            yy[r] = Y;
+                            hh[r] = H;
+                            am = M;
+                            ax = X;
+                            ay = Y;
+                        }
+                        dirs[((int64_t)s * nsteps + tau) * kPrG + lane] = (uint16_t)bits;
+                        hdiag = max3(min_, xin, yin);  // H(row0, j): the next column's diagonal
+                        mo = am;
+                        xo = ax;
+                        yo = ay;
+                        if (!last_strip && lane == kPrG - 1) {
+                            volatile T* vb = bout;
+                            vb[3 * j] = mo;
+                            vb[3 * j + 1] = xo;
+                            vb[3 * j + 2] = yo;
+                            __threadfence_block();
+                            prog[s] = j;
+                        }
+                    }
+                    min_ = __shfl_up_sync(0xffffffffu, mo, 1);
+                    xin = __shfl_up_sync(0xffffffffu, xo, 1);
+                    yin = __shfl_up_sync(0xffffffffu, yo, 1);
                 }
-                __syncwarp();
-                if (last_strip) {
-                    // (four named values: a select over the arrays would put them in local memory)
-                    static_assert(kPrR == 4, "four rows per lane");
-                    const int32_t rr = (m - 1) - s * kPrStrip;
-                    const int32_t rsel = rr % kPrR;
-                    const T h0 = max3(mm[0], xx[0], yy[0]), h1 = max3(mm[1], xx[1], yy[1]);
-                    const T h2 = max3(mm[2], xx[2], yy[2]), h3 = max3(mm[3], xx[3], yy[3]);
-                    const T v = rsel == 0 ? h0 : (rsel == 1 ? h1 : (rsel == 2 ? h2 : h3));
-                    score = __shfl_sync(0xffffffffu, v, rr / kPrR);
-                }
+#pragma unroll
+                for (int u = 0; u < kPrPre; u++) cur[u] = nxt[u];
             }
-            // traceback: every lane walks the same path (the direction words come
-            // from a shared window of kPrWin steps of one strip, reloaded by the
-            // whole warp when the path leaves it); lane 0 writes the columns
-            // backwards from the end of the slot
+            if (last_strip) {
+                // (named values: a select over the array would put it in local memory)
+                static_assert(kPrR == 2, "two rows per lane");
+                const int32_t rr = (m - 1) - s * kPrStrip;
+                const T v = (rr % kPrR) == 0 ? hh[0] : hh[1];
+                const T sc = __shfl_sync(0xffffffffu, v, rr / kPrR);
+                if (lane == 0) *score_sh = sc;
+            }
             __syncwarp();
-            int32_t i = m, jj = n, state = 3;  // 0 M, 1 X, 2 Y, 3 a cell's best state
-            int32_t ws = -1, wt0 = 0;
-            int64_t guard = 2ll * cap + 4;
-            while (i > 0 && jj > 0 && guard-- > 0) {
-                const int32_t s = (i - 1) / kPrStrip;
-                const int32_t t = ((i - 1) % kPrStrip) / kPrR;
-                const int32_t tau = jj - 1 + t;
-                if (s != ws || tau < wt0 || tau >= wt0 + kPrWin) {
-                    ws = s;
-                    wt0 = max(0, tau - kPrWin + 1);
-                    __syncwarp();
-#pragma unroll 8
-                    for (int u = 0; u < kPrWin; u++)
-                        if (wt0 + u < nsteps) win[u * kPrG + lane] = dirs[((int64_t)s * nsteps + wt0 + u) * kPrG + lane];
-                    __syncwarp();
+        }
+        __syncthreads();  // every strip's directions are written
+        if (warp == 0) {
+            T score = 0;
+            int32_t L = 0;
+            if (!cells) {  // one gap run, or nothing
+                for (int32_t c = lane; c < cap; c += 32) ops[c] = m == 0 ? 'Y' : 'X';
+                score = cap == 0 ? (T)0 : gop + (T)cap * gex;
+                L = cap;
+            } else {
+                score = *score_sh;
+                // traceback, one column per step: every lane walks the same path (the
+                // direction words come from a shared window of kPrWin steps of one
+                // strip, reloaded by the whole warp when the path leaves it); lane 0
+                // writes the columns backwards from the end of the slot. The cell
+                // (i, jj) sits in strip s, lane t, row r of the lane, step tau.
+                // The walk goes a run at a time: in state M the cells ahead are the
+                // diagonal (i-k, jj-k), k >= 1, and the run goes on while a cell's best
+                // state is M; in state X (Y) they are (i-k, jj) ((i, jj-k)), k >= 0, and
+                // the run goes on while the cell extends its gap. Lane l looks at the
+                // l-th cell ahead; a ballot finds where the run ends. A cell outside the
+                // shared window (another strip, or steps not loaded) ends the look-ahead
+                // without ending the run; state 3 means the current cell's best state is
+                // still to be read.
+                int32_t i = m, jj = n, state = 3;
+                int32_t ws = -1, wt0 = 0;
+                int64_t guard = 2ll * cap + 4;
+                while (i > 0 && jj > 0 && guard-- > 0) {
+                    const int32_t k = state == 0 ? lane + 1 : (state == 3 ? 0 : lane);
+                    const int32_t ci = i - (state != 2 ? k : 0), cj = jj - (state != 1 ? k : 0);
+                    const bool valid = ci > 0 && cj > 0 && (state != 3 || lane == 0);
+                    const uint32_t q = (uint32_t)(ci - 1);
+                    const int32_t cs = (int32_t)(q / kPrStrip), ct = (int32_t)((q % kPrStrip) / kPrR);
+                    const int32_t ctau = cj - 1 + ct;
+                    bool inwin = valid && cs == ws && ctau >= wt0 && ctau < wt0 + kPrWin;
+                    // the first cell ahead must be in the window: reload around it
+                    const bool need = __shfl_sync(0xffffffffu, valid && !inwin, 0);
+                    if (need) {
+                        ws = __shfl_sync(0xffffffffu, cs, 0);
+                        wt0 = max(0, __shfl_sync(0xffffffffu, ctau, 0) - kPrWin + 1);
+                        __syncwarp();
+                        // kPrWin steps x 32 lanes of uint16 = kPrWin * 4 chunks of 16 bytes
+                        for (int e = lane; e < kPrWin * 4; e += 32) {
+                            const int32_t u = e >> 2, part = e & 3;
+                            if (wt0 + u < nsteps)
+                                ((uint4*)win)[e] =
+                                    *(const uint4*)(dirs + ((int64_t)ws * nsteps + wt0 + u) * kPrG + part * 8);
+                        }
+                        __syncwarp();
+                        inwin = valid && cs == ws && ctau >= wt0 && ctau < wt0 + kPrWin;
+                    }
+                    const uint32_t bb =
+                        inwin ? (((uint32_t)win[(ctau - wt0) * kPrG + ct] >> (8 * (q % kPrR))) & 0xffu) : 0u;
+                    if (state == 3) {
+                        state = (int32_t)(__shfl_sync(0xffffffffu, bb, 0) & 3u);
+                        continue;
+                    }
+                    const bool cont = inwin && (state == 0 ? (bb & 3u) == 0 : (state == 1 ? (bb & 4u) != 0
+                                                                                           : (bb & 16u) != 0));
+                    const unsigned stop = ~__ballot_sync(0xffffffffu, cont);
+                    const int32_t f = stop ? __ffs(stop) - 1 : 32;  // first lane whose cell ends the look-ahead
+                    const uint32_t bf = __shfl_sync(0xffffffffu, bb, f & 31);
+                    const bool real = f < 32 && __shfl_sync(0xffffffffu, inwin ? 1 : 0, f & 31);
+                    int32_t E, nstate;
+                    if (state == 0) {  // M at (i, jj), then the continuing diagonal cells
+                        E = f + 1;
+                        nstate = real ? (int32_t)(bf & 3u) : 3;
+                    } else if (state == 1) {
+                        E = real ? f + 1 : f;
+                        nstate = real ? ((bf & 8u) ? 0 : 2) : 1;
+                    } else {
+                        E = real ? f + 1 : f;
+                        nstate = real ? ((bf & 32u) ? 0 : 1) : 2;
+                    }
+                    const uint8_t opc = state == 0 ? 'M' : (state == 1 ? 'X' : 'Y');
+                    for (int32_t e = lane; e < E; e += 32) ops[cap - 1 - L - e] = opc;
+                    L += E;
+                    i -= state != 2 ? E : 0;
+                    jj -= state != 1 ? E : 0;
+                    state = nstate;
                 }
-                const uint32_t b = (win[(tau - wt0) * kPrG + t] >> (8 * ((i - 1) % kPrR))) & 0xffu;
-                if (state == 3) {
-                    state = (int32_t)(b & 3u);
-                } else if (state == 0) {
-                    if (lane == 0) ops[cap - 1 - L] = 'M';
-                    L++;
-                    i--;
-                    jj--;
-                    state = 3;
-                } else if (state == 1) {
-                    if (lane == 0) ops[cap - 1 - L] = 'X';
-                    L++;
-                    state = (b & 4u) ? 1 : ((b & 8u) ? 0 : 2);
-                    i--;
-                } else {
-                    if (lane == 0) ops[cap - 1 - L] = 'Y';
-                    L++;
-                    state = (b & 16u) ? 2 : ((b & 32u) ? 0 : 1);
-                    jj--;
+                if (guard < 0 && lane == 0) atomicOr(a.status, STATUS_CAPACITY);
+                // the border: X(i, 0) and Y(0, j) are single gap runs
+                for (int32_t c = lane; c < i; c += 32) ops[cap - 1 - L - c] = 'X';
+                L += i;
+                for (int32_t c = lane; c < jj; c += 32) ops[cap - 1 - L - c] = 'Y';
+                L += jj;
+                L = min(L, cap);
+            }
+            if (lane == 0) {
+                *len_sh = L;
+                a.scores[jb.merge] = (long long)score;
+                a.widths[jb.merge] = L;
+            }
+        }
+        __syncthreads();
+        // the column maps and the merged profile, 32 columns per warp step: the
+        // P and Q columns before each chunk come from a prefix over the chunks
+        {
+            const int32_t L = *len_sh;
+            const uint8_t* col = ops + (cap - L);
+            const int32_t nch = (L + 31) / 32;
+            for (int32_t c0 = warp * 32; c0 < L; c0 += W * 32) {
+                const int32_t c = c0 + lane;
+                const uint8_t op = c < L ? col[c] : 0;
+                const unsigned bp = __ballot_sync(0xffffffffu, c < L && op != 'Y');
+                const unsigned bq = __ballot_sync(0xffffffffu, c < L && op != 'X');
+                if (lane == 0) {
+                    chP[c0 / 32] = __popc(bp);
+                    chQ[c0 / 32] = __popc(bq);
                 }
             }
-            if (guard < 0 && lane == 0) atomicOr(a.status, STATUS_CAPACITY);
-            // the border: X(i, 0) and Y(0, j) are single gap runs
-            for (int32_t c = lane; c < i; c += 32) ops[cap - 1 - L - c] = 'X';
-            L += i;
-            for (int32_t c = lane; c < jj; c += 32) ops[cap - 1 - L - c] = 'Y';
-            L += jj;
-            L = min(L, cap);
-        }
-        __syncwarp();
-        // the column maps and the merged profile, column by column in order
-        const uint8_t* col = ops + (cap - L);
-        int32_t* mapP = jb.map;
-        int32_t* mapQ = jb.map + m;
-        int32_t pi = 0, qj = 0;
-        for (int32_t c0 = 0; c0 < L; c0 += 32) {
-            const int32_t c = c0 + lane;
-            const uint8_t op = c < L ? col[c] : 0;
-            const bool inP = c < L && op != 'Y', inQ = c < L && op != 'X';
-            const unsigned bp = __ballot_sync(0xffffffffu, inP), bq = __ballot_sync(0xffffffffu, inQ);
+            __syncthreads();
+            if (warp == 0) {  // exclusive prefix over the chunks
+                int32_t carryP = 0, carryQ = 0;
+                for (int32_t c0 = 0; c0 < nch; c0 += 32) {
+                    const int32_t c = c0 + lane;
+                    const int32_t vP = c < nch ? chP[c] : 0, vQ = c < nch ? chQ[c] : 0;
+                    int32_t iP = vP, iQ = vQ;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t xP = __shfl_up_sync(0xffffffffu, iP, o), xQ = __shfl_up_sync(0xffffffffu, iQ, o);
+                        if (lane >= o) {
+                            iP += xP;
+                            iQ += xQ;
+                        }
+                    }
+                    __syncwarp();
+                    if (c < nch) {
+                        chP[c] = carryP + iP - vP;
+                        chQ[c] = carryQ + iQ - vQ;
+                    }
+                    carryP += __shfl_sync(0xffffffffu, iP, 31);
+                    carryQ += __shfl_sync(0xffffffffu, iQ, 31);
+                }
+            }
+            __syncthreads();
+            int32_t* mapP = jb.map;
+            int32_t* mapQ = jb.map + m;
             const unsigned below = (1u << lane) - 1u;
-            const int32_t i = pi + __popc(bp & below), j = qj + __popc(bq & below);
-            if (inP) mapP[i] = c;
-            if (inQ) mapQ[j] = c;
-            if (c < L) {
-                const uint4* cp = (const uint4*)(jb.prof_p + (int64_t)i * Ap);
-                const uint4* cq = (const uint4*)(jb.prof_q + (int64_t)j * Ap);
-                uint4* cr = (uint4*)(jb.prof_r + (int64_t)c * Ap);
-                for (int32_t h = 0; h < Ap / 8; h++) {
-                    const uint4 u = inP ? cp[h] : make_uint4(0, 0, 0, 0);
-                    const uint4 v = inQ ? cq[h] : make_uint4(0, 0, 0, 0);
-                    // two 16-bit counts per word; their sums stay below 2^16
-                    cr[h] = make_uint4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+            for (int32_t c0 = warp * 32; c0 < L; c0 += W * 32) {
+                const int32_t c = c0 + lane;
+                const uint8_t op = c < L ? col[c] : 0;
+                const bool inP = c < L && op != 'Y', inQ = c < L && op != 'X';
+                const unsigned bp = __ballot_sync(0xffffffffu, inP), bq = __ballot_sync(0xffffffffu, inQ);
+                const int32_t i = chP[c0 / 32] + __popc(bp & below), j = chQ[c0 / 32] + __popc(bq & below);
+                if (inP) mapP[i] = c;
+                if (inQ) mapQ[j] = c;
+                if (c < L) {
+                    const uint4* cp = (const uint4*)(jb.prof_p + (int64_t)i * Ap);
+                    const uint4* cq = (const uint4*)(jb.prof_q + (int64_t)j * Ap);
+                    uint4* cr = (uint4*)(jb.prof_r + (int64_t)c * Ap);
+                    for (int32_t h = 0; h < Ap / 8; h++) {
+                        const uint4 u = inP ? cp[h] : make_uint4(0, 0, 0, 0);
+                        const uint4 v = inQ ? cq[h] : make_uint4(0, 0, 0, 0);
+                        // two 16-bit counts per word; their sums stay below 2^16
+                        cr[h] = make_uint4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+                    }
                 }
             }
-            pi += __popc(bp);
-            qj += __popc(bq);
         }
-        if (lane == 0) {
-            a.scores[jb.merge] = (long long)score;
-            a.widths[jb.merge] = L;
-        }
-        __syncwarp();
+        __syncthreads();  // shared memory is reused by the next merge
     }
 }
 
@@ -625,7 +733,7 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
         const std::vector<int32_t>& ms = by_level[lv];
         for (size_t j0 = 0; j0 < ms.size();) {
             jobs.clear();
-            int64_t s_vecs = 0, d_words = 0, maxw = 1;
+            int64_t s_vecs = 0, d_words = 0, maxw = 1, max_strips = 0;
             int32_t tiles = 0;
             bool wide = false;
             size_t j1 = j0;
@@ -641,8 +749,10 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
                 // score streams plus the look-ahead of the last lane
                 const int64_t sv = cells ? strips * kPrG * (n + kPrG - 1) + 2 * kPrPre : 0;
                 const int64_t dw = cells ? strips * (n + kPrG - 1) * kPrG : 0;
-                const int64_t bytes_here = 16 * (s_vecs + sv) + 4 * (d_words + dw);
+                const int64_t bytes_here = 8 * (s_vecs + sv) + 2 * (d_words + dw);
                 if (j1 > j0 && bytes_here > budget) break;
+                SAD_CHECK(strips <= kMaxStrips, SAD_EINVAL, "merge %d: a profile of %lld columns (at most %d)", mi,
+                          (long long)m, kMaxStrips * kPrStrip);
                 const int64_t pq = (int64_t)nmem[gl] * nmem[gr];
                 SAD_CHECK(pq * smax < (1ll << 31), SAD_EINVAL,
                           "merge %d: %lld member pairs x max |S| exceed the 32-bit cell scores", mi, (long long)pq);
@@ -672,25 +782,30 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
                 d_words += dw;
                 tiles += cells ? (int32_t)(strips * ((n + 31) / 32)) : 0;
                 maxw = std::max(maxw, std::max(m, n));
+                max_strips = std::max(max_strips, strips);
                 j1++;
             }
             const int32_t nj = (int32_t)jobs.size();
-            // shared memory of one DP warp: strip boundary, traceback window, columns
-            const int64_t warp_smem = (wide ? bnd_bytes<long long>((int32_t)maxw) : bnd_bytes<int32_t>((int32_t)maxw)) +
-                                      win_bytes() + ops_bytes((int32_t)maxw);
-            const int64_t warps_cta = std::min<int64_t>(kPrWarps, ((int64_t)ctx->smem_optin - 1024) / warp_smem);
-            SAD_CHECK(warps_cta >= 1, SAD_EINVAL, "profiles of %lld columns exceed the DP kernel's shared memory",
-                      (long long)maxw);
-            const int64_t grid_dp = std::min<int64_t>(((int64_t)nj + warps_cta - 1) / warps_cta,
-                                                      (int64_t)ctx->num_sms * 8);
+            // DP warps per merge: one per strip, up to kPrWarps side by side; shared memory
+            // holds one boundary slot per warp, the progress counts, the traceback window,
+            // the columns and their chunk counts
+            const int64_t slot = wide ? bnd_bytes<long long>((int32_t)maxw) : bnd_bytes<int32_t>((int32_t)maxw);
+            const int64_t fixed = 4 * kMaxStrips + 16 + win_bytes() + ops_bytes((int32_t)maxw) +
+                                  8ll * chunk_count((int32_t)maxw);
+            int64_t warps_cta = std::min<int64_t>(kPrWarps, std::max<int64_t>(1, max_strips));
+            while (warps_cta > 1 && warps_cta * slot + fixed > (int64_t)ctx->smem_optin - 1024) warps_cta--;
+            SAD_CHECK(slot + fixed <= (int64_t)ctx->smem_optin - 1024, SAD_EINVAL,
+                      "profiles of %lld columns exceed the DP kernel's shared memory", (long long)maxw);
+            const int64_t cta_smem = warps_cta * slot + fixed;
+            const int64_t grid_dp = std::min<int64_t>(nj, (int64_t)ctx->num_sms * 16);
             size_t lo = 0;
             auto lcarve = [&](size_t bytes) {
                 const size_t o = lo;
                 lo = (size_t)round_up((int64_t)(lo + bytes), 256);
                 return o;
             };
-            const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(16ull * s_vecs + 16),
-                         l_d = lcarve(4ull * d_words + 4);
+            const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(8ull * s_vecs + 16),
+                         l_d = lcarve(2ull * d_words + 4);
             void* lv_ws = nullptr;
             SAD_RET(workspace(ctx, WS_PROG_LEVEL, lo, stream, &lv_ws));
             char* lw = (char*)lv_ws;
@@ -704,19 +819,19 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
             pa.go = gap_open;
             pa.ge = gap_extend;
             pa.subst = d_sub;
-            pa.S = (int4*)(lw + l_s);
-            pa.dirs = (uint32_t*)(lw + l_d);
+            pa.S = (int2*)(lw + l_s);
+            pa.dirs = (uint16_t*)(lw + l_d);
             pa.scores = d_sc;
             pa.widths = d_mw;
             pa.status = ctx->d_status;
             pa.maxw = (int32_t)maxw;
-            pa.warp_smem = (int32_t)warp_smem;
+            pa.warp_smem = (int32_t)cta_smem;
             if (tiles > 0) {
                 const unsigned g1 = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx->num_sms * 8);
                 k_prof_scores<<<g1, kScThreads, 0, stream>>>(pa);
                 SAD_LAUNCHED();
             }
-            const size_t dyn = (size_t)(warp_smem * warps_cta);
+            const size_t dyn = (size_t)cta_smem;
             if (wide) {
                 k_prof_dp<long long><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), dyn, stream>>>(pa);
             } else {
