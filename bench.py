@@ -154,8 +154,8 @@ def progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od, reps=3):
             depth[nb + k] = 1 + max(depth[lt[m]], depth[rt[m]])
             levels = max(levels, depth[nb + k])
     ms = span[0] / max(span[1], 1)
-    return {"kernel": "k_prof_dp (profile-profile affine-gap DP with traceback, one warp per merge) "
-                      "+ k_prof_scores + k_prof_pb + k_colmap",
+    return {"kernel": "k_prof_dp (profile-profile affine-gap DP with traceback, one CTA per merge, one warp "
+                      "per 64-row strip) + k_prof_scores + k_colmap",
             "ms": ms, "merges": int(len(lt)), "tree_levels": int(levels), "dp_cells": int(cells),
             "gcups": cells / (ms * 1e-3) / 1e9 if ms > 0 else None,
             "alignment_widths": [int(x) for x in pa["widths"].cpu().numpy()]}
