@@ -18,6 +18,8 @@ Functions follow the paper:
                       pair scores, the progressive aligner's first step
   progressive         progressive profile alignment of every bucket along its
                       guide tree (one multiple alignment per bucket)
+  ancestor_glue       every bucket's alignment realigned against the global
+                      ancestor and all buckets joined through its positions
 
 Parity status: every function here is pinned by tests that do not reuse this
 code (brute-force alignment enumeration, sorted-list k-mer intersection,
@@ -76,6 +78,8 @@ def _bind(lib):
     lib.orc_guide_trees.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.orc_progressive.restype = ctypes.c_int
     lib.orc_progressive.argtypes = [P, P, i32, P, P, i32, P, P, P, P, i32, i32, i32, i32, P, P, P, P]
+    lib.orc_ancestor_glue.restype = ctypes.c_int
+    lib.orc_ancestor_glue.argtypes = [P, P, i32, P, P, i32, P, P, i32, P, i32, i32, i32, i32, P, P, P, P]
     return lib
 
 
@@ -303,6 +307,32 @@ def progressive(residues, offsets, bucket_offsets, order, merge_offsets, left, r
     if rc != 0:
         raise ValueError("orc_progressive: the merges do not form a tree")
     return {"widths": widths, "merge_scores": ms[:M], "merge_widths": mw[:M], "colmap": colmap[:total]}
+
+
+def ancestor_glue(residues, offsets, bucket_offsets, order, widths, colmap, ga, subst, gap_open, gap_extend,
+                  nthreads=None, lib=None):
+    """Realignment of every bucket's alignment against sequence ga and the glue
+    (see oracle.cpp): dict(ga_scores int64[p], anchors int32[sum widths],
+    width int, colmap int32[residues])."""
+    lib = lib or _load()
+    res, offs = _c(residues, np.uint8), _c(offsets, np.int64)
+    bo, od = _c(bucket_offsets, np.int32), _c(order, np.int32)
+    wd, cm = _c(widths, np.int32), _c(colmap, np.int32)
+    sub = _c(subst, np.int8)
+    n, p = len(offs) - 1, len(bo) - 1
+    alphabet = int(round(np.sqrt(sub.size)))
+    sc = np.zeros(p, np.int64)
+    an = np.zeros(max(int(wd.sum()), 1), np.int32)
+    gw = np.zeros(1, np.int32)
+    gc = np.zeros(max(cm.size, 1), np.int32)
+    one = np.zeros(1, np.int32)
+    rc = lib.orc_ancestor_glue(_ptr(res if res.size else np.zeros(1, np.uint8)), _ptr(offs), n, _ptr(bo),
+                               _ptr(od if od.size else one), p, _ptr(wd), _ptr(cm if cm.size else one), int(ga),
+                               _ptr(sub), alphabet, int(gap_open), int(gap_extend), nthreads or default_threads(),
+                               _ptr(sc), _ptr(an), _ptr(gw), _ptr(gc))
+    if rc != 0:
+        raise ValueError("orc_ancestor_glue: invalid arguments")
+    return {"ga_scores": sc, "anchors": an[:int(wd.sum())], "width": int(gw[0]), "colmap": gc[:cm.size]}
 
 
 def tri_index(u: int, v: int, nb: int) -> int:

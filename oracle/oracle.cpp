@@ -39,6 +39,9 @@
  *     the letter pairs across the profiles and a new gap run costing the
  *     member-count product times the pairwise run cost; the tie order and the
  *     column bookkeeping are stated at orc_progressive.
+ *   - realignment of every bucket's alignment against the global ancestor and
+ *     the glue of all buckets through the ancestor's positions (the last steps
+ *     of the algorithm box), stated at orc_ancestor_glue.
  */
 #include <algorithm>
 #include <atomic>
@@ -430,6 +433,90 @@ GotohTables fill_gotoh(const uint8_t* x, int32_t m, const uint8_t* y, int32_t n,
     return t;
 }
 
+/* One optimal alignment of profile P (m columns, np members; counts
+ * cp[column * alphabet + letter]) with profile Q (w columns, nq members): the
+ * three-state recursion of fill_gotoh in which a column pair scores the sum of
+ * S over the letter pairs across the two profiles and a new gap run of length
+ * g costs np nq (go + g ge); the traceback takes the tie order of orc_align.
+ * Writes the optimum and the columns ('M', 'X': P's column against a gap, 'Y')
+ * first to last; false when the tables are inconsistent. */
+bool profile_align(const std::vector<int64_t>& cp, int64_t np, int64_t m, const std::vector<int64_t>& cq, int64_t nq,
+                   int64_t w, const int8_t* S, int32_t alphabet, int32_t go, int32_t ge, int64_t* score_out,
+                   std::string* cols) {
+    // sum_b S[a][b] cntQ[j][b] for every column j and letter a (a factor of s(i, j))
+    std::vector<int64_t> sq((size_t)w * alphabet, 0);
+    for (int64_t j = 0; j < w; j++)
+        for (int32_t a = 0; a < alphabet; a++)
+            for (int32_t c = 0; c < alphabet; c++) sq[j * alphabet + a] += S[a * alphabet + c] * cq[j * alphabet + c];
+    auto s = [&](int64_t i, int64_t j) {  // 1-based column indices
+        int64_t v = 0;
+        for (int32_t a = 0; a < alphabet; a++) v += cp[(i - 1) * alphabet + a] * sq[(j - 1) * alphabet + a];
+        return v;
+    };
+    const int64_t gop = (int64_t)go * np * nq, gex = (int64_t)ge * np * nq;
+    // the three tables, as in fill_gotoh
+    const int64_t W = w + 1;
+    std::vector<int64_t> TM((size_t)(m + 1) * W, NEG_INF), TX(TM), TY(TM);
+    auto at = [&](int64_t i, int64_t j) { return i * W + j; };
+    TM[at(0, 0)] = 0;
+    for (int64_t i = 0; i <= m; i++)
+        for (int64_t j = 0; j <= w; j++) {
+            if (i == 0 && j == 0) continue;
+            if (i > 0 && j > 0) {
+                const int64_t prev = std::max({TM[at(i - 1, j - 1)], TX[at(i - 1, j - 1)], TY[at(i - 1, j - 1)]});
+                if (prev > NEG_INF) TM[at(i, j)] = prev + s(i, j);
+            }
+            if (i > 0) {
+                const int64_t open = std::max(TM[at(i - 1, j)], TY[at(i - 1, j)]);
+                int64_t v = NEG_INF;
+                if (open > NEG_INF) v = open + gop + gex;
+                if (TX[at(i - 1, j)] > NEG_INF) v = std::max(v, TX[at(i - 1, j)] + gex);
+                TX[at(i, j)] = v;
+            }
+            if (j > 0) {
+                const int64_t open = std::max(TM[at(i, j - 1)], TX[at(i, j - 1)]);
+                int64_t v = NEG_INF;
+                if (open > NEG_INF) v = open + gop + gex;
+                if (TY[at(i, j - 1)] > NEG_INF) v = std::max(v, TY[at(i, j - 1)] + gex);
+                TY[at(i, j)] = v;
+            }
+        }
+    // traceback with the tie order of orc_align
+    auto best_of = [&](int64_t i, int64_t j, bool useM, bool useX, bool useY, int64_t want, int64_t add) {
+        if (useM && TM[at(i, j)] > NEG_INF && TM[at(i, j)] + add == want) return 'M';
+        if (useX && TX[at(i, j)] > NEG_INF && TX[at(i, j)] + add == want) return 'X';
+        if (useY && TY[at(i, j)] > NEG_INF && TY[at(i, j)] + add == want) return 'Y';
+        return '?';
+    };
+    const int64_t score = std::max({TM[at(m, w)], TX[at(m, w)], TY[at(m, w)]});
+    char state = best_of(m, w, true, true, true, score, 0);
+    std::string rev;
+    int64_t i = m, j = w;
+    while (i > 0 || j > 0) {
+        rev.push_back(state);
+        if (state == 'M') {
+            state = best_of(i - 1, j - 1, true, true, true, TM[at(i, j)] - s(i, j), 0);
+            i--;
+            j--;
+        } else if (state == 'X') {
+            const int64_t v = TX[at(i, j)];
+            const char ext = best_of(i - 1, j, false, true, false, v, gex);
+            state = ext == 'X' ? 'X' : best_of(i - 1, j, true, false, true, v, gop + gex);
+            i--;
+        } else if (state == 'Y') {
+            const int64_t v = TY[at(i, j)];
+            const char ext = best_of(i, j - 1, false, false, true, v, gex);
+            state = ext == 'Y' ? 'Y' : best_of(i, j - 1, true, true, false, v, gop + gex);
+            j--;
+        } else {
+            return false;
+        }
+    }
+    *score_out = score;
+    cols->assign(rev.rbegin(), rev.rend());
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -646,9 +733,13 @@ int orc_progressive(const uint8_t* res, const int64_t* offs, int32_t n, const in
                     int32_t nthreads, int32_t* widths, int64_t* merge_scores, int32_t* merge_widths,
                     int32_t* colmap) {
     if (p < 1 || n < 0) return -1;
-    // where each bucket position's residues start in colmap
-    std::vector<int64_t> pos_off((size_t)n + 1, 0);
-    for (int32_t q = 0; q < n; q++) pos_off[q + 1] = pos_off[q] + (offs[order[q] + 1] - offs[order[q]]);
+    // where each bucket position's residues start in colmap (positions 0 .. bucket_offsets[p])
+    const int32_t npos = bucket_offsets[p];
+    std::vector<int64_t> pos_off((size_t)npos + 1, 0);
+    for (int32_t q = 0; q < npos; q++) {
+        if (order[q] < 0 || order[q] >= n) return -1;
+        pos_off[q + 1] = pos_off[q] + (offs[order[q] + 1] - offs[order[q]]);
+    }
     std::atomic<int> bad(0);
     parallel_for(p, nthreads, [&](int64_t b) {
         const int32_t boff = bucket_offsets[b];
@@ -690,82 +781,18 @@ int orc_progressive(const uint8_t* res, const int64_t* offs, int32_t n, const in
             const int64_t m = P.width, w = Q.width;
             const int64_t np = (int64_t)P.members.size(), nq = (int64_t)Q.members.size();
             const std::vector<int64_t> cp = profile(P), cq = profile(Q);
-            // sum_b S[a][b] cntQ[j][b] for every column j and letter a (a factor of s(i, j))
-            std::vector<int64_t> sq((size_t)w * alphabet, 0);
-            for (int64_t j = 0; j < w; j++)
-                for (int32_t a = 0; a < alphabet; a++)
-                    for (int32_t c = 0; c < alphabet; c++) sq[j * alphabet + a] += S[a * alphabet + c] * cq[j * alphabet + c];
-            auto s = [&](int64_t i, int64_t j) {  // 1-based column indices
-                int64_t v = 0;
-                for (int32_t a = 0; a < alphabet; a++) v += cp[(i - 1) * alphabet + a] * sq[(j - 1) * alphabet + a];
-                return v;
-            };
-            const int64_t gop = (int64_t)go * np * nq, gex = (int64_t)ge * np * nq;
-            // the three tables, as in fill_gotoh
-            const int64_t W = w + 1;
-            std::vector<int64_t> TM((size_t)(m + 1) * W, NEG_INF), TX(TM), TY(TM);
-            auto at = [&](int64_t i, int64_t j) { return i * W + j; };
-            TM[at(0, 0)] = 0;
-            for (int64_t i = 0; i <= m; i++)
-                for (int64_t j = 0; j <= w; j++) {
-                    if (i == 0 && j == 0) continue;
-                    if (i > 0 && j > 0) {
-                        const int64_t prev = std::max({TM[at(i - 1, j - 1)], TX[at(i - 1, j - 1)], TY[at(i - 1, j - 1)]});
-                        if (prev > NEG_INF) TM[at(i, j)] = prev + s(i, j);
-                    }
-                    if (i > 0) {
-                        const int64_t open = std::max(TM[at(i - 1, j)], TY[at(i - 1, j)]);
-                        int64_t v = NEG_INF;
-                        if (open > NEG_INF) v = open + gop + gex;
-                        if (TX[at(i - 1, j)] > NEG_INF) v = std::max(v, TX[at(i - 1, j)] + gex);
-                        TX[at(i, j)] = v;
-                    }
-                    if (j > 0) {
-                        const int64_t open = std::max(TM[at(i, j - 1)], TX[at(i, j - 1)]);
-                        int64_t v = NEG_INF;
-                        if (open > NEG_INF) v = open + gop + gex;
-                        if (TY[at(i, j - 1)] > NEG_INF) v = std::max(v, TY[at(i, j - 1)] + gex);
-                        TY[at(i, j)] = v;
-                    }
-                }
-            // traceback with the tie order of orc_align
-            auto best_of = [&](int64_t i, int64_t j, bool useM, bool useX, bool useY, int64_t want, int64_t add) {
-                if (useM && TM[at(i, j)] > NEG_INF && TM[at(i, j)] + add == want) return 'M';
-                if (useX && TX[at(i, j)] > NEG_INF && TX[at(i, j)] + add == want) return 'X';
-                if (useY && TY[at(i, j)] > NEG_INF && TY[at(i, j)] + add == want) return 'Y';
-                return '?';
-            };
-            const int64_t score = std::max({TM[at(m, w)], TX[at(m, w)], TY[at(m, w)]});
-            char state = best_of(m, w, true, true, true, score, 0);
-            std::string rev;
-            int64_t i = m, j = w;
-            while (i > 0 || j > 0) {
-                rev.push_back(state);
-                if (state == 'M') {
-                    state = best_of(i - 1, j - 1, true, true, true, TM[at(i, j)] - s(i, j), 0);
-                    i--;
-                    j--;
-                } else if (state == 'X') {
-                    const int64_t v = TX[at(i, j)];
-                    const char ext = best_of(i - 1, j, false, true, false, v, gex);
-                    state = ext == 'X' ? 'X' : best_of(i - 1, j, true, false, true, v, gop + gex);
-                    i--;
-                } else if (state == 'Y') {
-                    const int64_t v = TY[at(i, j)];
-                    const char ext = best_of(i, j - 1, false, false, true, v, gex);
-                    state = ext == 'Y' ? 'Y' : best_of(i, j - 1, true, true, false, v, gop + gex);
-                    j--;
-                } else {
-                    bad = 1;
-                    return;
-                }
+            int64_t score = 0;
+            std::string fwd;
+            if (!profile_align(cp, np, m, cq, nq, w, S, alphabet, go, ge, &score, &fwd)) {
+                bad = 1;
+                return;
             }
             // the merged cluster: alignment column c takes P's column and/or Q's column
-            const int64_t len = (int64_t)rev.size();
+            const int64_t len = (int64_t)fwd.size();
             std::vector<int64_t> mapP(m), mapQ(w);
             int64_t pi = 0, qj = 0;
             for (int64_t c = 0; c < len; c++) {
-                const char op = rev[len - 1 - c];
+                const char op = fwd[c];
                 if (op == 'M' || op == 'X') mapP[pi++] = c;
                 if (op == 'M' || op == 'Y') mapQ[qj++] = c;
             }
@@ -800,6 +827,112 @@ int orc_progressive(const uint8_t* res, const int64_t* offs, int32_t n, const in
         }
     });
     return bad ? -1 : 0;
+}
+
+/* Realignment against the global ancestor and the glue, the last steps of
+ * Algorithm Sample-Align-D (Section 2.3.3: every processor's aligned sequences
+ * are aligned with the ancestor's profile, and the aligned sets are joined
+ * through it). Bucket b's alignment (widths[b] columns; colmap as written by
+ * orc_progressive) is kept fixed and aligned, as a profile of its nb members,
+ * with the ancestor sequence ga as a profile of one member by profile_align
+ * (the bucket's columns are the rows). A bucket column matched to ancestor
+ * position g is anchored at g (anchors[...] = g); one against a gap in the
+ * ancestor is an insertion in slot s, s being the number of ancestor positions
+ * before it (anchors[...] = -(s + 1)); anchors holds bucket b's columns at
+ * offset widths[0] + ... + widths[b - 1]. The joined alignment has, for s = 0,
+ * 1, ..., |ga|, the insertions of slot s (bucket by bucket in bucket order,
+ * inside a bucket in column order) followed by the anchor column of ancestor
+ * position s (for s < |ga|), shared by every bucket column anchored there;
+ * columns holding no residue are then dropped. Outputs: ga_scores[b] (the
+ * optimum of bucket b's alignment with the ancestor; 0 for an empty bucket),
+ * *global_width, global_colmap (the joined column of every residue, in the
+ * layout of colmap). Returns 0, or -1 on invalid arguments. */
+int orc_ancestor_glue(const uint8_t* res, const int64_t* offs, int32_t n, const int32_t* bucket_offsets,
+                      const int32_t* order, int32_t p, const int32_t* widths, const int32_t* colmap, int32_t ga,
+                      const int8_t* S, int32_t alphabet, int32_t go, int32_t ge, int32_t nthreads,
+                      int64_t* ga_scores, int32_t* anchors, int32_t* global_width, int32_t* global_colmap) {
+    if (p < 1 || n < 1 || ga < 0 || ga >= n) return -1;
+    const int32_t npos = bucket_offsets[p];
+    std::vector<int64_t> pos_off((size_t)npos + 1, 0), col_off((size_t)p + 1, 0);
+    for (int32_t q = 0; q < npos; q++) {
+        if (order[q] < 0 || order[q] >= n) return -1;
+        pos_off[q + 1] = pos_off[q] + (offs[order[q] + 1] - offs[order[q]]);
+    }
+    for (int32_t b = 0; b < p; b++) col_off[b + 1] = col_off[b] + widths[b];
+    for (int32_t b = 0; b < p; b++)
+        for (int32_t q = bucket_offsets[b]; q < bucket_offsets[b + 1]; q++)
+            for (int64_t t = pos_off[q]; t < pos_off[q + 1]; t++)
+                if (colmap[t] < 0 || colmap[t] >= widths[b]) return -1;
+    const int64_t lg = offs[ga + 1] - offs[ga];
+    std::vector<int64_t> cg((size_t)lg * alphabet, 0);  // the ancestor as a profile of one member
+    for (int64_t r = 0; r < lg; r++) cg[r * alphabet + res[offs[ga] + r]] = 1;
+    std::atomic<int> bad(0);
+    parallel_for(p, nthreads, [&](int64_t b) {
+        const int64_t nb = bucket_offsets[b + 1] - bucket_offsets[b], w = widths[b];
+        ga_scores[b] = 0;
+        if (nb == 0) return;
+        std::vector<int64_t> cp((size_t)w * alphabet, 0);  // the bucket's profile from its alignment
+        for (int32_t q = bucket_offsets[b]; q < bucket_offsets[b + 1]; q++) {
+            const uint8_t* x = res + offs[order[q]];
+            for (int64_t t = pos_off[q]; t < pos_off[q + 1]; t++) cp[(int64_t)colmap[t] * alphabet + x[t - pos_off[q]]]++;
+        }
+        int64_t score = 0;
+        std::string cols;
+        if (!profile_align(cp, nb, w, cg, 1, lg, S, alphabet, go, ge, &score, &cols)) {
+            bad = 1;
+            return;
+        }
+        ga_scores[b] = score;
+        int64_t c = 0, g = 0;
+        for (char op : cols) {
+            if (op == 'M') anchors[col_off[b] + c++] = (int32_t)g++;
+            else if (op == 'X') anchors[col_off[b] + c++] = -(int32_t)(g + 1);
+            else g++;
+        }
+    });
+    if (bad) return -1;
+    // the joined layout: per slot s the insertions of every bucket, then anchor s
+    std::vector<int64_t> ins((size_t)(lg + 1) * p, 0);
+    for (int32_t b = 0; b < p; b++)
+        for (int64_t c = 0; c < widths[b]; c++) {
+            const int32_t a = anchors[col_off[b] + c];
+            if (a < 0) ins[(int64_t)(-a - 1) * p + b]++;
+        }
+    std::vector<int64_t> start((size_t)(lg + 1) * p, 0), anchor_col((size_t)lg, 0);
+    int64_t col = 0;
+    for (int64_t sl = 0; sl <= lg; sl++) {
+        for (int32_t b = 0; b < p; b++) {
+            start[sl * p + b] = col;
+            col += ins[sl * p + b];
+        }
+        if (sl < lg) anchor_col[sl] = col++;
+    }
+    // each bucket column's joined column (insertions of a slot are consecutive in a bucket)
+    std::vector<int64_t> joined((size_t)col_off[p], 0);
+    for (int32_t b = 0; b < p; b++) {
+        std::vector<int64_t> rank((size_t)lg + 1, 0);
+        for (int64_t c = 0; c < widths[b]; c++) {
+            const int32_t a = anchors[col_off[b] + c];
+            joined[col_off[b] + c] = a >= 0 ? anchor_col[a] : start[(int64_t)(-a - 1) * p + b] + rank[-a - 1]++;
+        }
+    }
+    // drop the columns that hold no residue
+    std::vector<int64_t> used((size_t)col + 1, 0);
+    for (int32_t b = 0; b < p; b++)
+        for (int32_t q = bucket_offsets[b]; q < bucket_offsets[b + 1]; q++)
+            for (int64_t t = pos_off[q]; t < pos_off[q + 1]; t++) used[joined[col_off[b] + colmap[t]]] = 1;
+    std::vector<int64_t> renum((size_t)col + 1, 0);
+    int64_t kept = 0;
+    for (int64_t x = 0; x < col; x++) {
+        renum[x] = kept;
+        kept += used[x];
+    }
+    *global_width = (int32_t)kept;
+    for (int32_t b = 0; b < p; b++)
+        for (int32_t q = bucket_offsets[b]; q < bucket_offsets[b + 1]; q++)
+            for (int64_t t = pos_off[q]; t < pos_off[q + 1]; t++)
+                global_colmap[t] = (int32_t)renum[joined[col_off[b] + colmap[t]]];
+    return 0;
 }
 
 }  // extern "C"

@@ -47,6 +47,16 @@ MUTANTS = {
     "profile end tie prefers a gap": ("char state = best_of(m, w, true, true, true, score, 0);",
                                       "char state = best_of(m, w, false, true, true, score, 0);\n"
                                       "            if (state == '?') state = 'M';"),
+    "glue anchor before the slot's insertions": (
+        "        for (int32_t b = 0; b < p; b++) {\n            start[sl * p + b] = col;\n            col += ins[sl * p + b];\n"
+        "        }\n        if (sl < lg) anchor_col[sl] = col++;",
+        "        if (sl < lg) anchor_col[sl] = col++;\n        for (int32_t b = 0; b < p; b++) {\n"
+        "            start[sl * p + b] = col;\n            col += ins[sl * p + b];\n        }"),
+    "glue keeps empty columns": ("        kept += used[x];", "        kept += 1;"),
+    "glue profile of the first member only": (
+        "for (int32_t q = bucket_offsets[b]; q < bucket_offsets[b + 1]; q++) {\n            const uint8_t* x = res + offs[order[q]];",
+        "for (int32_t q = bucket_offsets[b]; q < bucket_offsets[b] + 1; q++) {\n            const uint8_t* x = res + offs[order[q]];"),
+    "glue insertion slot one late": ("anchors[col_off[b] + c++] = -(int32_t)(g + 1);", "anchors[col_off[b] + c++] = -(int32_t)g;"),
     "profile of the first member only": ("for (size_t t = 0; t < c.members.size(); t++) {\n                const uint8_t* x",
                                          "for (size_t t = 0; t < 1; t++) {\n                const uint8_t* x"),
 }
@@ -176,6 +186,41 @@ def battery(lib):
                             r["merge_widths"].tolist(), rows, S, -3, -1)
         except AssertionError:
             failed.append("progressive brute force")
+            break
+    # 8. realignment against the ancestor and the glue: golden examples, brute force
+    import test_oracle_glue as tg
+    with open(os.path.join(GOLD, "ancestor_glue_tiny.json")) as f:
+        g = json.load(f)
+    Sg = np.array(g["subst"], np.int8).ravel()
+    for c in g["cases"]:
+        res, offs = synth.pack(c["seqs"])
+        r = oracle.ancestor_glue(res, offs, c["bucket_offsets"], c["order"], c["widths"], c["colmap"], c["ga"], Sg,
+                                 g["gap_open"], g["gap_extend"], lib=lib)
+        if (r["ga_scores"].tolist() != c["ga_scores"] or r["anchors"].tolist() != c["anchors"]
+                or r["width"] != c["width"] or r["colmap"].tolist() != c["global_colmap"]):
+            failed.append("golden glue " + c["name"])
+    rng = random.Random(8)
+    for _ in range(4):
+        A = 2
+        S = random_symmetric(rng, A, -4, 6).astype(np.int64).tolist()
+        sizes = [rng.randint(1, 3) for _ in range(2)]
+        seqs, bo, left, right, mo = [], [0], [], [], [0]
+        for nb in sizes:
+            seqs += [[rng.randrange(A) for _ in range(rng.randint(1, 3))] for _ in range(nb)]
+            bo.append(bo[-1] + nb)
+            lt, rt = tp.random_tree(rng, nb) if nb > 1 else ([], [])
+            left += lt
+            right += rt
+            mo.append(mo[-1] + max(nb - 1, 0))
+        order = list(range(len(seqs)))
+        res, offs = synth.pack(seqs)
+        flat = np.array(S, np.int8).ravel()
+        pr = oracle.progressive(res, offs, bo, order, mo, left, right, flat, -3, -1, lib=lib)
+        r = oracle.ancestor_glue(res, offs, bo, order, pr["widths"], pr["colmap"], 0, flat, -3, -1, lib=lib)
+        try:
+            tg.check_glue(seqs, bo, order, pr["widths"].tolist(), pr["colmap"], 0, S, -3, -1, r)
+        except AssertionError:
+            failed.append("glue brute force")
             break
     return failed
 
