@@ -127,9 +127,10 @@ def device_gaps(spans):
 
 
 def progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od, reps=3):
-    """Time sad_progressive_align on the step's buckets and guide trees: the
-    traced span (device time including the per-level host reads) and the DP
-    cells of all merges (the product of the two children's widths)."""
+    """Time sad_progressive_align on the step's buckets and guide trees (the
+    traced span: device time including the per-level host reads; the DP cells
+    of all merges, the product of the two children's widths), then
+    sad_ancestor_glue on its alignments and the step's global ancestor."""
     import torch
     sad.trace_enable(True)
     for _ in range(reps):
@@ -154,8 +155,21 @@ def progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od, reps=3):
             depth[nb + k] = 1 + max(depth[lt[m]], depth[rt[m]])
             levels = max(levels, depth[nb + k])
     ms = span[0] / max(span[1], 1)
+    # then every bucket's alignment against the global ancestor, joined through it
+    ga = int(out_d["ga"].reshape(-1)[0].item())
+    sad.trace_enable(True)
+    for _ in range(reps):
+        gl = sad.ancestor_glue(res_d, offs_d, w.alphabet, out_d["bucket_offsets"], out_d["order"][:w.n],
+                               pa["widths"], pa["colmap"], ga, w.subst, w.gap_open, w.gap_extend)
+    torch.cuda.synchronize()
+    gspan = sad.trace_read()["prog"]
+    sad.trace_enable(False)
+    glue = {"kernel": "k_bucket_profiles + k_prof_scores + k_prof_dp (each bucket against the ancestor) + "
+                      "k_anchors + k_glue_layout + k_joined + k_glue_residues",
+            "ms": gspan[0] / max(gspan[1], 1), "ancestor": ga, "ancestor_length": int(np.diff(w.offsets)[ga]),
+            "joined_width": int(gl["width"])}
     return {"kernel": "k_prof_dp (profile-profile affine-gap DP with traceback, one CTA per merge, one warp "
-                      "per 64-row strip) + k_prof_scores + k_colmap",
+                      "per 64-row strip) + k_prof_scores + k_colmap", "glue": glue,
             "ms": ms, "merges": int(len(lt)), "tree_levels": int(levels), "dp_cells": int(cells),
             "gcups": cells / (ms * 1e-3) / 1e9 if ms > 0 else None,
             "alignment_widths": [int(x) for x in pa["widths"].cpu().numpy()]}

@@ -20,6 +20,8 @@
  *                                from its pair scores
  *        sad_progressive_align   one multiple alignment per bucket, profile
  *                                against profile along its guide tree
+ *        sad_ancestor_glue       every bucket realigned against the global
+ *                                ancestor and all joined through its positions
  * plus sad_pipeline (both stages in one call) and a continuous-batching
  * serving loop (sad_server_*).
  *
@@ -394,6 +396,32 @@ int sad_progressive_align(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* b
                           const int32_t* right, const int8_t* subst, int32_t gap_open, int32_t gap_extend,
                           int32_t* widths, int64_t* merge_scores, int32_t* merge_widths, int32_t* colmap,
                           int32_t mem, void* stream);
+
+/* Realignment against the global ancestor and the glue, the last steps of
+ * Algorithm Sample-Align-D (Section 2.3.3): the alignment of every bucket
+ * (widths[p] and colmap as sad_progressive_align writes them, over the
+ * residues of order[0..npos) in turn) is kept fixed and aligned, as a profile
+ * of its members (rows), with sequence ga as a profile of one member
+ * (columns), by the recursion and tie order of sad_progressive_align. A bucket
+ * column matched to position g of ga is anchored there (anchors[...] = g), one
+ * against a gap in ga is an insertion of slot s, s being the number of ga's
+ * positions before it (anchors[...] = -(s + 1)); bucket b's columns sit at
+ * offset widths[0] + ... + widths[b-1] of anchors. The joined alignment holds,
+ * for s = 0 .. |ga|, the insertions of slot s (bucket by bucket in bucket
+ * order, inside a bucket in column order) and then the anchor column of
+ * position s (s < |ga|), shared by every bucket column anchored there; columns
+ * holding no residue are dropped. Outputs (caller-owned, `mem` space):
+ * ga_scores[p] (int64 optimum of each bucket against ga; 0 for an empty
+ * bucket), anchors[sum widths], *global_width, global_colmap (the joined
+ * column of every residue, in the layout of colmap). Errors: SAD_EINVAL
+ * (layout inconsistent, ga outside 0..n-1, a colmap entry outside its
+ * bucket's width, a bucket above 65535 members, member products x max|subst|
+ * >= 2^31, an asymmetric subst, gap costs > 0 or below -1000, a residue >=
+ * alphabet), SAD_ENOMEM, SAD_ECUDA. */
+int sad_ancestor_glue(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucket_offsets, const int32_t* order,
+                      int32_t p, const int32_t* widths, const int32_t* colmap, int32_t ga, const int8_t* subst,
+                      int32_t gap_open, int32_t gap_extend, int64_t* ga_scores, int32_t* anchors,
+                      int32_t* global_width, int32_t* global_colmap, int32_t mem, void* stream);
 
 /* ---- alignments (traceback) ----------------------------------------------- */
 

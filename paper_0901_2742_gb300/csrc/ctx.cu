@@ -174,6 +174,7 @@ int status_check(sad_ctx* ctx, cudaStream_t stream) {
     SAD_CHECK(!(s & STATUS_BAD_RESIDUE), SAD_EINVAL, "a residue code is >= the alphabet size");
     SAD_CHECK(!(s & STATUS_TIMEOUT), SAD_ETIMEOUT, "a bounded device-side wait gave up");
     SAD_CHECK(!(s & STATUS_CAPACITY), SAD_ECUDA, "an internal device capacity was exceeded");
+    SAD_CHECK(!(s & STATUS_BAD_INPUT), SAD_EINVAL, "an input array holds a value out of range");
     return SAD_OK;
 }
 

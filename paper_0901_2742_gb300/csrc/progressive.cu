@@ -38,6 +38,13 @@
 //                  merged profile. T is int32 when the host proves every value
 //                  fits, else int64.
 // At the end k_colmap composes each residue's column maps up the tree.
+//
+// sad_ancestor_glue (the last steps of the algorithm box: every bucket's
+// alignment realigned with the global ancestor's profile, then all buckets
+// joined through it) reuses the same score and DP kernels, one merge per
+// bucket against the ancestor as a one-member profile; k_anchors turns the
+// column maps into anchors, k_glue_layout and k_joined lay out the joined
+// alignment, k_glue_residues drops its empty columns and writes the columns.
 // Profiles (uint16 counts, the alphabet padded to 8) and column maps live in
 // an arena of device chunks that only grows during a call.
 #include <algorithm>
@@ -572,6 +579,265 @@ struct Arena {
     }
 };
 
+// A batch of independent merges: every job's offsets into the batch's score
+// streams, direction words and score tiles, and what the launch needs.
+struct Batch {
+    std::vector<ProgJob> jobs;
+    int64_t s_vecs = 0, d_words = 0, maxw = 1, max_strips = 0;
+    int32_t tiles = 0;
+    bool wide = false;
+    static int64_t streams(int64_t m, int64_t n) {  // score streams plus the look-ahead of the last lane
+        return (m > 0 && n > 0) ? (m + kPrStrip - 1) / kPrStrip * kPrG * (n + kPrG - 1) + 2 * kPrPre : 0;
+    }
+    static int64_t words(int64_t m, int64_t n) {
+        return (m > 0 && n > 0) ? (m + kPrStrip - 1) / kPrStrip * (n + kPrG - 1) * kPrG : 0;
+    }
+    // bytes of scores and directions once a merge of m x n columns is added
+    int64_t bytes_with(int64_t m, int64_t n) const { return 8 * (s_vecs + streams(m, n)) + 2 * (d_words + words(m, n)); }
+    // checks the merge's ranges (SAD_EINVAL) and appends it
+    int add(ProgJob jb, int64_t smax, int64_t cmax) {
+        const int64_t m = jb.m, n = jb.n, strips = (m + kPrStrip - 1) / kPrStrip;
+        SAD_CHECK(strips <= kMaxStrips, SAD_EINVAL, "merge %d: a profile of %lld columns (at most %d)", jb.merge,
+                  (long long)m, kMaxStrips * kPrStrip);
+        const int64_t pq = (int64_t)jb.np * jb.nq;
+        SAD_CHECK(pq * smax < (1ll << 31), SAD_EINVAL,
+                  "merge %d: %lld member pairs x max |S| exceed the 32-bit cell scores", jb.merge, (long long)pq);
+        if ((m + n + 2 * kPrStrip) * pq * cmax >= (1ll << 28)) wide = true;
+        jb.s_off = s_vecs;
+        jb.d_off = d_words;
+        jb.tile0 = tiles;
+        jobs.push_back(jb);
+        s_vecs += streams(m, n);
+        d_words += words(m, n);
+        tiles += (m > 0 && n > 0) ? (int32_t)(strips * ((n + 31) / 32)) : 0;
+        maxw = std::max(maxw, std::max(m, n));
+        max_strips = std::max(max_strips, strips);
+        return SAD_OK;
+    }
+};
+
+// Launches one batch (score tiles, then the DP: one CTA per merge, one warp
+// per strip up to kPrWarps); `pa` carries the call's parameters and outputs.
+int run_batch(sad_ctx* ctx, const Batch& bt, ProgArgs pa, cudaStream_t stream) {
+    const int32_t nj = (int32_t)bt.jobs.size();
+    if (nj == 0) return SAD_OK;
+    // shared memory: one boundary slot per warp, the progress counts, the
+    // traceback window, the columns and their chunk counts
+    const int64_t slot = bt.wide ? bnd_bytes<long long>((int32_t)bt.maxw) : bnd_bytes<int32_t>((int32_t)bt.maxw);
+    const int64_t fixed = 4 * kMaxStrips + 16 + win_bytes() + ops_bytes((int32_t)bt.maxw) +
+                          8ll * chunk_count((int32_t)bt.maxw);
+    int64_t warps_cta = std::min<int64_t>(kPrWarps, std::max<int64_t>(1, bt.max_strips));
+    while (warps_cta > 1 && warps_cta * slot + fixed > (int64_t)ctx->smem_optin - 1024) warps_cta--;
+    SAD_CHECK(slot + fixed <= (int64_t)ctx->smem_optin - 1024, SAD_EINVAL,
+              "profiles of %lld columns exceed the DP kernel's shared memory", (long long)bt.maxw);
+    const int64_t cta_smem = warps_cta * slot + fixed;
+    const int64_t grid_dp = std::min<int64_t>(nj, (int64_t)ctx->num_sms * 16);
+    size_t lo = 0;
+    auto lcarve = [&](size_t bytes) {
+        const size_t o = lo;
+        lo = (size_t)round_up((int64_t)(lo + bytes), 256);
+        return o;
+    };
+    const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(8ull * bt.s_vecs + 16),
+                 l_d = lcarve(2ull * bt.d_words + 4);
+    void* lv_ws = nullptr;
+    SAD_RET(workspace(ctx, WS_PROG_LEVEL, lo, stream, &lv_ws));
+    char* lw = (char*)lv_ws;
+    SAD_CUDA(cudaMemcpyAsync(lw + l_jobs, bt.jobs.data(), sizeof(ProgJob) * nj, cudaMemcpyHostToDevice, stream));
+    pa.jobs = (const ProgJob*)(lw + l_jobs);
+    pa.njobs = nj;
+    pa.ntiles = bt.tiles;
+    pa.S = (int2*)(lw + l_s);
+    pa.dirs = (uint16_t*)(lw + l_d);
+    pa.maxw = (int32_t)bt.maxw;
+    pa.warp_smem = (int32_t)cta_smem;
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<int32_t>));
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<long long>));
+    if (bt.tiles > 0) {
+        const unsigned g1 = (unsigned)std::min<int64_t>(bt.tiles, (int64_t)ctx->num_sms * 8);
+        k_prof_scores<<<g1, kScThreads, 0, stream>>>(pa);
+        SAD_LAUNCHED();
+    }
+    if (bt.wide) {
+        k_prof_dp<long long><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), (size_t)cta_smem, stream>>>(pa);
+    } else {
+        k_prof_dp<int32_t><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), (size_t)cta_smem, stream>>>(pa);
+    }
+    SAD_LAUNCHED();
+    return SAD_OK;
+}
+
+
+// ---- realignment against the global ancestor and the glue ----------------
+
+// Profile of every bucket from its alignment: position q's residue r adds 1 to
+// column colmap[pos_off[q] + r] of its bucket (two 16-bit counts per word; a
+// column never counts more than the bucket's members). A column outside the
+// bucket's width is reported, not counted.
+__global__ void k_bucket_profiles(const uint8_t* __restrict__ res, const int64_t* __restrict__ pad_off,
+                                  const int32_t* __restrict__ len, const int32_t* __restrict__ order, int32_t npos,
+                                  const int64_t* __restrict__ pos_off, const int32_t* __restrict__ pos_bucket,
+                                  const int64_t* __restrict__ col_off, const int32_t* __restrict__ widths,
+                                  const int32_t* __restrict__ colmap, int32_t Ap, uint32_t* __restrict__ prof,
+                                  uint32_t* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = wid; q < npos; q += nw) {
+        const int32_t sq = order[q], b = pos_bucket[q];
+        const uint8_t* x = res + pad_off[sq];
+        for (int32_t r = lane; r < len[sq]; r += 32) {
+            const int32_t c = colmap[pos_off[q] + r];
+            if (c < 0 || c >= widths[b]) {
+                atomicOr(status, STATUS_BAD_INPUT);
+                continue;
+            }
+            if (x[r] >= Ap) continue;  // a residue code the sequence check reports
+            const int64_t e = (col_off[b] + c) * Ap + x[r];
+            atomicAdd(prof + (e >> 1), 1u << (16 * (e & 1)));
+        }
+    }
+}
+
+// Anchor of every bucket column from its realignment's column maps: with P's
+// column i at alignment column mapP[i] and ancestor position g at mapQ[g]
+// (increasing), s = #{g : mapQ[g] < mapP[i]}; the column is anchored at s when
+// mapQ[s] == mapP[i], else it is an insertion of slot s (stored -(s + 1),
+// counted in ins[s * p + b], the slot's first such column of the bucket in
+// first[s * p + b]).
+__global__ void k_anchors(int32_t p, const int64_t* __restrict__ col_off, int32_t* const* __restrict__ map_ptr,
+                          int32_t lg, int32_t* __restrict__ anchors, int32_t* __restrict__ ins,
+                          int32_t* __restrict__ first) {
+    const int64_t total = col_off[p];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = p - 1;  // the bucket holding column t: the last with col_off <= t
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (col_off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t b = lo;
+        const int64_t m = col_off[b + 1] - col_off[b], i = t - col_off[b];
+        const int32_t* mapP = map_ptr[b];
+        const int32_t* mapQ = mapP + m;
+        const int32_t c = mapP[i];
+        int32_t a = 0, z = lg;  // lower bound of c in mapQ
+        while (a < z) {
+            const int32_t mid = (a + z) >> 1;
+            if (mapQ[mid] < c) a = mid + 1;
+            else z = mid;
+        }
+        if (a < lg && mapQ[a] == c) {
+            anchors[t] = a;
+        } else {
+            anchors[t] = -(a + 1);
+            atomicAdd(&ins[(int64_t)a * p + b], 1);
+            atomicMin(&first[(int64_t)a * p + b], (int32_t)i);
+        }
+    }
+}
+
+// Exclusive prefix sums of x[0..n) into y (y[n] = the total), by one CTA.
+__device__ void block_scan(const int32_t* x, int64_t n, int32_t* y) {
+    __shared__ int32_t warp_sum[32];
+    __shared__ int32_t carry_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry_sh = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int64_t t = c0 + threadIdx.x;
+        const int32_t v = t < n ? x[t] : 0;
+        int32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) warp_sum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t ws = lane < nw ? warp_sum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += u;
+            }
+            if (lane < nw) warp_sum[lane] = ws;  // inclusive over warps
+        }
+        __syncthreads();
+        const int32_t before = carry_sh + (warp > 0 ? warp_sum[warp - 1] : 0);
+        if (t < n) y[t] = before + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_sh += warp_sum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) y[n] = carry_sh;
+}
+
+// The joined layout: slot s holds the insertions of bucket 0, 1, ..., then the
+// anchor of ancestor position s. sizes[s * (p + 1) + b] = ins[s * p + b] for
+// b < p and 1 for the anchor (0 after the last position); start = their
+// exclusive prefix sums.
+__global__ void k_glue_layout(int32_t p, int32_t lg, const int32_t* __restrict__ ins, int32_t* __restrict__ sizes,
+                              int32_t* __restrict__ start) {
+    const int64_t cells = (int64_t)(lg + 1) * (p + 1);
+    for (int64_t t = threadIdx.x; t < cells; t += blockDim.x) {
+        const int64_t s = t / (p + 1), b = t - s * (p + 1);
+        sizes[t] = b < p ? ins[s * p + b] : (s < lg ? 1 : 0);
+    }
+    __syncthreads();
+    block_scan(sizes, cells, start);
+}
+
+// Joined column of every bucket column: its anchor's column, or the slot's
+// start for its bucket plus its rank among the bucket's insertions of that
+// slot (they are consecutive columns: rank = i - the first of them).
+__global__ void k_joined(int32_t p, const int64_t* __restrict__ col_off, const int32_t* __restrict__ anchors,
+                         const int32_t* __restrict__ start, const int32_t* __restrict__ first,
+                         int32_t* __restrict__ joined) {
+    const int64_t total = col_off[p];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = p - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (col_off[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t b = lo, a = anchors[t];
+        const int64_t i = t - col_off[b];
+        if (a >= 0) {
+            joined[t] = start[(int64_t)a * (p + 1) + p];
+        } else {
+            const int64_t sl = -a - 1;
+            joined[t] = start[sl * (p + 1) + b] + (int32_t)(i - first[sl * p + b]);
+        }
+    }
+}
+
+// used[joined column of each residue] = 1 (mode 0), or the residue's final
+// column renum[...] (mode 1). One warp per bucket position.
+__global__ void k_glue_residues(int32_t mode, const int32_t* __restrict__ order, int32_t npos,
+                                const int32_t* __restrict__ len, const int64_t* __restrict__ pos_off,
+                                const int32_t* __restrict__ pos_bucket, const int64_t* __restrict__ col_off,
+                                const int32_t* __restrict__ widths, const int32_t* __restrict__ colmap,
+                                const int32_t* __restrict__ joined, int32_t* __restrict__ used,
+                                const int32_t* __restrict__ renum, int32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = wid; q < npos; q += nw) {
+        const int32_t b = pos_bucket[q];
+        for (int32_t r = lane; r < len[order[q]]; r += 32) {
+            const int32_t c = colmap[pos_off[q] + r];
+            if (c < 0 || c >= widths[b]) continue;  // reported by k_bucket_profiles
+            const int32_t g = joined[col_off[b] + c];
+            if (mode == 0) used[g] = 1;
+            else out[pos_off[q] + r] = renum[g];
+        }
+    }
+}
+
+__global__ void k_scan_one(const int32_t* __restrict__ x, int64_t n, int32_t* __restrict__ y) { block_scan(x, n, y); }
 }  // namespace
 
 }  // namespace sad
@@ -726,16 +992,19 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
     std::vector<int32_t> map_split((size_t)M, 0);
     std::vector<int32_t> h_mw((size_t)M + 1, 0);
     const int64_t budget = (int64_t)1 << 30;  // bytes of cell scores and directions per batch
-    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<int32_t>));
-    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<long long>));
-    std::vector<ProgJob> jobs;
+    ProgArgs base{};
+    base.Ap = Ap;
+    base.alphabet = A;
+    base.go = gap_open;
+    base.ge = gap_extend;
+    base.subst = d_sub;
+    base.scores = d_sc;
+    base.widths = d_mw;
+    base.status = ctx->d_status;
     for (int32_t lv = 1; lv <= max_level; lv++) {
         const std::vector<int32_t>& ms = by_level[lv];
         for (size_t j0 = 0; j0 < ms.size();) {
-            jobs.clear();
-            int64_t s_vecs = 0, d_words = 0, maxw = 1, max_strips = 0;
-            int32_t tiles = 0;
-            bool wide = false;
+            Batch bt;
             size_t j1 = j0;
             while (j1 < ms.size()) {
                 const int32_t mi = ms[j1];
@@ -744,20 +1013,8 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
                 const int64_t k = mi - mo[b];
                 const int64_t gl = cl_off[b] + lt[mi], gr = cl_off[b] + rt[mi], gn = cl_off[b] + nb + k;
                 const int64_t m = width[gl], n = width[gr];
-                const bool cells = m > 0 && n > 0;
-                const int64_t strips = (m + kPrStrip - 1) / kPrStrip;
-                // score streams plus the look-ahead of the last lane
-                const int64_t sv = cells ? strips * kPrG * (n + kPrG - 1) + 2 * kPrPre : 0;
-                const int64_t dw = cells ? strips * (n + kPrG - 1) * kPrG : 0;
-                const int64_t bytes_here = 8 * (s_vecs + sv) + 2 * (d_words + dw);
-                if (j1 > j0 && bytes_here > budget) break;
-                SAD_CHECK(strips <= kMaxStrips, SAD_EINVAL, "merge %d: a profile of %lld columns (at most %d)", mi,
-                          (long long)m, kMaxStrips * kPrStrip);
-                const int64_t pq = (int64_t)nmem[gl] * nmem[gr];
-                SAD_CHECK(pq * smax < (1ll << 31), SAD_EINVAL,
-                          "merge %d: %lld member pairs x max |S| exceed the 32-bit cell scores", mi, (long long)pq);
-                if ((m + n + 2 * kPrStrip) * pq * cmax >= (1ll << 28)) wide = true;
-                ProgJob jb;
+                if (j1 > j0 && bt.bytes_with(m, n) > budget) break;
+                ProgJob jb{};
                 jb.prof_p = prof[gl];
                 jb.prof_q = prof[gr];
                 void* pr = nullptr;
@@ -766,78 +1023,19 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
                 void* mp = nullptr;
                 SAD_RET(arena.alloc(4ull * (m + n), &mp));
                 jb.map = (int32_t*)mp;
-                jb.s_off = s_vecs;
-                jb.d_off = d_words;
                 jb.m = (int32_t)m;
                 jb.n = (int32_t)n;
                 jb.np = nmem[gl];
                 jb.nq = nmem[gr];
                 jb.merge = mi;
-                jb.tile0 = tiles;
-                jobs.push_back(jb);
+                SAD_RET(bt.add(jb, smax, cmax));
                 prof[gn] = jb.prof_r;
                 map_ptr[mi] = jb.map;
                 map_split[mi] = (int32_t)m;
-                s_vecs += sv;
-                d_words += dw;
-                tiles += cells ? (int32_t)(strips * ((n + 31) / 32)) : 0;
-                maxw = std::max(maxw, std::max(m, n));
-                max_strips = std::max(max_strips, strips);
                 j1++;
             }
-            const int32_t nj = (int32_t)jobs.size();
-            // DP warps per merge: one per strip, up to kPrWarps side by side; shared memory
-            // holds one boundary slot per warp, the progress counts, the traceback window,
-            // the columns and their chunk counts
-            const int64_t slot = wide ? bnd_bytes<long long>((int32_t)maxw) : bnd_bytes<int32_t>((int32_t)maxw);
-            const int64_t fixed = 4 * kMaxStrips + 16 + win_bytes() + ops_bytes((int32_t)maxw) +
-                                  8ll * chunk_count((int32_t)maxw);
-            int64_t warps_cta = std::min<int64_t>(kPrWarps, std::max<int64_t>(1, max_strips));
-            while (warps_cta > 1 && warps_cta * slot + fixed > (int64_t)ctx->smem_optin - 1024) warps_cta--;
-            SAD_CHECK(slot + fixed <= (int64_t)ctx->smem_optin - 1024, SAD_EINVAL,
-                      "profiles of %lld columns exceed the DP kernel's shared memory", (long long)maxw);
-            const int64_t cta_smem = warps_cta * slot + fixed;
-            const int64_t grid_dp = std::min<int64_t>(nj, (int64_t)ctx->num_sms * 16);
-            size_t lo = 0;
-            auto lcarve = [&](size_t bytes) {
-                const size_t o = lo;
-                lo = (size_t)round_up((int64_t)(lo + bytes), 256);
-                return o;
-            };
-            const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(8ull * s_vecs + 16),
-                         l_d = lcarve(2ull * d_words + 4);
-            void* lv_ws = nullptr;
-            SAD_RET(workspace(ctx, WS_PROG_LEVEL, lo, stream, &lv_ws));
-            char* lw = (char*)lv_ws;
-            SAD_CUDA(cudaMemcpyAsync(lw + l_jobs, jobs.data(), sizeof(ProgJob) * nj, cudaMemcpyHostToDevice, stream));
-            ProgArgs pa;
-            pa.jobs = (const ProgJob*)(lw + l_jobs);
-            pa.njobs = nj;
-            pa.ntiles = tiles;
-            pa.Ap = Ap;
-            pa.alphabet = A;
-            pa.go = gap_open;
-            pa.ge = gap_extend;
-            pa.subst = d_sub;
-            pa.S = (int2*)(lw + l_s);
-            pa.dirs = (uint16_t*)(lw + l_d);
-            pa.scores = d_sc;
-            pa.widths = d_mw;
-            pa.status = ctx->d_status;
-            pa.maxw = (int32_t)maxw;
-            pa.warp_smem = (int32_t)cta_smem;
-            if (tiles > 0) {
-                const unsigned g1 = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx->num_sms * 8);
-                k_prof_scores<<<g1, kScThreads, 0, stream>>>(pa);
-                SAD_LAUNCHED();
-            }
-            const size_t dyn = (size_t)cta_smem;
-            if (wide) {
-                k_prof_dp<long long><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), dyn, stream>>>(pa);
-            } else {
-                k_prof_dp<int32_t><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), dyn, stream>>>(pa);
-            }
-            SAD_LAUNCHED();
+            SAD_RET(run_batch(ctx, bt, base, stream));
+            const std::vector<ProgJob>& jobs = bt.jobs;
             // the new widths, for the next level's layout (the jobs' table copy
             // from pageable memory has been consumed when this returns)
             SAD_CUDA(cudaMemcpyAsync(h_mw.data(), d_mw, 4ull * std::max<int64_t>(M, 1), cudaMemcpyDeviceToHost,
@@ -890,6 +1088,213 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
         if (T_res > 0) SAD_CUDA(cudaMemcpyAsync(colmap, d_cm, 4ull * T_res, cudaMemcpyDeviceToHost, stream));
     } else {
         SAD_CUDA(cudaMemcpyAsync(widths, h_w.data(), 4ull * p, cudaMemcpyHostToDevice, stream));
+    }
+    SAD_RET(status_check(ctx, stream));
+    return SAD_OK;
+}
+
+extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                                 const int32_t* order, int32_t p, const int32_t* widths, const int32_t* colmap,
+                                 int32_t ga, const int8_t* subst, int32_t gap_open, int32_t gap_extend,
+                                 int64_t* ga_scores, int32_t* anchors, int32_t* global_width, int32_t* global_colmap,
+                                 int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(p >= 1, SAD_EINVAL, "p = %d < 1", p);
+    SAD_CHECK(seqs && subst && bucket_offsets && widths && ga_scores && global_width, SAD_EINVAL,
+              "a required pointer is NULL");
+    SAD_CHECK(gap_open <= 0 && gap_extend <= 0, SAD_EINVAL, "gap costs must be <= 0");
+    SAD_CHECK(gap_open >= -1000 && gap_extend >= -1000, SAD_EINVAL, "gap costs below -1000");
+    const int32_t A = seqs->alphabet;
+    SAD_CHECK(A >= 1 && A <= SAD_MAX_ALPHABET, SAD_EINVAL, "alphabet %d outside 1..%d", A, SAD_MAX_ALPHABET);
+    for (int32_t x = 0; x < A; x++)
+        for (int32_t y = 0; y < A; y++)
+            SAD_CHECK(subst[x * A + y] == subst[y * A + x], SAD_EINVAL, "the substitution matrix is not symmetric");
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    SAD_RET(status_clear(ctx, stream));
+    DevSeqs S;
+    SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
+    SAD_CHECK(ga >= 0 && ga < S.n, SAD_EINVAL, "ga = %d outside 0..%d", ga, S.n - 1);
+    // layout on the host
+    std::vector<int32_t> bo((size_t)p + 1), wd((size_t)p);
+    SAD_RET(arg_to_host(bucket_offsets, 4ull * (p + 1), mem, stream, bo.data()));
+    SAD_RET(arg_to_host(widths, 4ull * p, mem, stream, wd.data()));
+    SAD_CHECK(bo[0] == 0, SAD_EINVAL, "bucket_offsets must start at 0");
+    for (int32_t b = 0; b < p; b++) {
+        SAD_CHECK(bo[b + 1] >= bo[b], SAD_EINVAL, "bucket_offsets decreases at %d", b);
+        SAD_CHECK(bo[b + 1] - bo[b] < 65536, SAD_EINVAL, "bucket %d has more than 65535 members", b);
+        SAD_CHECK(wd[b] >= 0 && (bo[b + 1] > bo[b] || wd[b] == 0), SAD_EINVAL, "widths[%d] = %d", b, wd[b]);
+    }
+    const int32_t npos = bo[p];
+    SAD_CHECK(npos == 0 || order, SAD_EINVAL, "order is NULL");
+    std::vector<int32_t> od((size_t)npos), pos_bucket((size_t)npos);
+    SAD_RET(arg_to_host(order, 4ull * npos, mem, stream, od.data()));
+    std::vector<int64_t> pos_off((size_t)npos + 1, 0), col_off((size_t)p + 1, 0);
+    for (int32_t b = 0; b < p; b++) {
+        col_off[b + 1] = col_off[b] + wd[b];
+        for (int32_t q = bo[b]; q < bo[b + 1]; q++) {
+            SAD_CHECK(od[q] >= 0 && od[q] < S.n, SAD_EINVAL, "order[%d] = %d outside 0..%d", q, od[q], S.n - 1);
+            pos_off[q + 1] = pos_off[q] + S.h_len[od[q]];
+            pos_bucket[q] = b;
+        }
+    }
+    const int64_t T_res = pos_off[npos], Wtot = col_off[p];
+    SAD_CHECK(T_res == 0 || (colmap && global_colmap), SAD_EINVAL, "colmap or global_colmap is NULL");
+    SAD_CHECK(Wtot == 0 || anchors, SAD_EINVAL, "anchors is NULL");
+    const int32_t lg = S.h_len[ga];
+    const int64_t J = Wtot + lg;  // joined columns before the empty ones are dropped, at most
+    int32_t smax = 0;
+    for (int32_t t = 0; t < A * A; t++) smax = std::max(smax, (int32_t)std::abs((int)subst[t]));
+    const int64_t cmax = std::max<int64_t>(smax, (int64_t)-gap_open - gap_extend);
+    const int32_t Ap = (int32_t)round_up(A, 8);
+    // device tables, scratch and (host mode) staged arrays
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off = (size_t)round_up((int64_t)(off + bytes), 256);
+        return o;
+    };
+    const int64_t cells = (int64_t)(lg + 1) * p, lay = (int64_t)(lg + 1) * (p + 1);
+    const size_t o_sub = carve(1024), o_od = carve(4ull * (npos + 1)), o_pos = carve(8ull * (npos + 1)),
+                 o_pb = carve(4ull * (npos + 1)), o_coff = carve(8ull * (p + 1)), o_wd = carve(4ull * p),
+                 o_mp = carve(8ull * p), o_ins = carve(4ull * cells), o_first = carve(4ull * cells),
+                 o_sizes = carve(4ull * lay), o_start = carve(4ull * (lay + 1)), o_join = carve(4ull * (Wtot + 1)),
+                 o_used = carve(4ull * (J + 1)), o_renum = carve(4ull * (J + 1)), o_ga = carve(16),
+                 o_gpos = carve(16), o_mw = carve(4ull * p), o_sc = carve(8ull * p), o_an = carve(4ull * (Wtot + 1)),
+                 o_cm = carve(mem == SAD_MEM_HOST ? 4ull * (T_res + 1) : 0),
+                 o_gcm = carve(mem == SAD_MEM_HOST ? 4ull * (T_res + 1) : 0);
+    void* wsp = nullptr;
+    SAD_RET(workspace(ctx, WS_PROG, off, stream, &wsp));
+    char* w = (char*)wsp;
+    int32_t* d_od = (int32_t*)(w + o_od);
+    int64_t* d_pos = (int64_t*)(w + o_pos);
+    int32_t* d_pb = (int32_t*)(w + o_pb);
+    int64_t* d_coff = (int64_t*)(w + o_coff);
+    int32_t* d_wd = (int32_t*)(w + o_wd);
+    int32_t* d_ins = (int32_t*)(w + o_ins);
+    int32_t* d_first = (int32_t*)(w + o_first);
+    int32_t* d_start = (int32_t*)(w + o_start);
+    int32_t* d_join = (int32_t*)(w + o_join);
+    int32_t* d_used = (int32_t*)(w + o_used);
+    int32_t* d_renum = (int32_t*)(w + o_renum);
+    long long* d_sc = mem == SAD_MEM_HOST ? (long long*)(w + o_sc) : (long long*)ga_scores;
+    int32_t* d_an = (mem == SAD_MEM_HOST || Wtot == 0) ? (int32_t*)(w + o_an) : anchors;
+    const int32_t* d_cm = colmap;
+    int32_t* d_gcm = mem == SAD_MEM_HOST ? (int32_t*)(w + o_gcm) : global_colmap;
+    if (mem == SAD_MEM_HOST) {
+        if (T_res > 0) SAD_CUDA(cudaMemcpyAsync(w + o_cm, colmap, 4ull * T_res, cudaMemcpyHostToDevice, stream));
+        d_cm = (const int32_t*)(w + o_cm);
+    }
+    const int64_t ga_pos[2] = {0, lg};
+    SAD_CUDA(cudaMemcpyAsync(w + o_sub, subst, (size_t)A * A, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_od, od.data(), 4ull * npos, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_pos, pos_off.data(), 8ull * (npos + 1), cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_pb, pos_bucket.data(), 4ull * npos, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_coff, col_off.data(), 8ull * (p + 1), cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(d_wd, wd.data(), 4ull * p, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(w + o_ga, &ga, 4, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemcpyAsync(w + o_gpos, ga_pos, 16, cudaMemcpyHostToDevice, stream));
+    SAD_CUDA(cudaMemsetAsync(d_sc, 0, 8ull * p, stream));
+    SAD_CUDA(cudaMemsetAsync(d_ins, 0, 4ull * cells, stream));
+    SAD_CUDA(cudaMemsetAsync(d_first, 0x7f, 4ull * cells, stream));
+    SAD_CUDA(cudaMemsetAsync(d_used, 0, 4ull * (J + 1), stream));
+    TraceScope ts(ctx, SAD_STAGE_PROG, stream);
+    // profiles: every bucket's from its alignment, the ancestor's as one member
+    Arena arena{ctx};
+    void* bprof = nullptr;
+    SAD_RET(arena.alloc(2ull * Ap * std::max<int64_t>(Wtot, 1), &bprof));
+    SAD_CUDA(cudaMemsetAsync(bprof, 0, 2ull * Ap * std::max<int64_t>(Wtot, 1), stream));
+    void* gprof = nullptr;
+    SAD_RET(arena.alloc(2ull * Ap * std::max<int32_t>(lg, 1), &gprof));
+    const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)std::max(npos, 1) * 32 + 255) / 256,
+                                                        (int64_t)ctx->num_sms * 16);
+    if (npos > 0) {
+        k_bucket_profiles<<<blocks, 256, 0, stream>>>(S.res, S.pad_off, S.len, d_od, npos, d_pos, d_pb, d_coff, d_wd,
+                                                      d_cm, Ap, (uint32_t*)bprof, ctx->d_status);
+        SAD_LAUNCHED();
+    }
+    k_leaf_profiles<<<1, 32, 0, stream>>>(S.res, S.pad_off, S.len, (const int32_t*)(w + o_ga), 1,
+                                          (const int64_t*)(w + o_gpos), Ap, (uint16_t*)gprof);
+    SAD_LAUNCHED();
+    // every non-empty bucket against the ancestor (its columns are the rows)
+    std::vector<int32_t*> map_ptr((size_t)p, nullptr);
+    ProgArgs base{};
+    base.Ap = Ap;
+    base.alphabet = A;
+    base.go = gap_open;
+    base.ge = gap_extend;
+    base.subst = (const int8_t*)(w + o_sub);
+    base.scores = d_sc;
+    base.widths = (int32_t*)(w + o_mw);
+    base.status = ctx->d_status;
+    const int64_t budget = (int64_t)1 << 30;
+    for (int32_t b0 = 0; b0 < p;) {
+        Batch bt;
+        int32_t b1 = b0;
+        for (; b1 < p; b1++) {
+            const int32_t nb = bo[b1 + 1] - bo[b1];
+            if (nb == 0) continue;
+            if (!bt.jobs.empty() && bt.bytes_with(wd[b1], lg) > budget) break;
+            ProgJob jb{};
+            jb.prof_p = (const uint16_t*)bprof + col_off[b1] * Ap;
+            jb.prof_q = (const uint16_t*)gprof;
+            void* pr = nullptr;
+            SAD_RET(arena.alloc(2ull * Ap * ((int64_t)wd[b1] + lg), &pr));
+            jb.prof_r = (uint16_t*)pr;
+            void* mp = nullptr;
+            SAD_RET(arena.alloc(4ull * ((int64_t)wd[b1] + lg), &mp));
+            jb.map = (int32_t*)mp;
+            jb.m = wd[b1];
+            jb.n = lg;
+            jb.np = nb;
+            jb.nq = 1;
+            jb.merge = b1;
+            SAD_RET(bt.add(jb, smax, cmax));
+            map_ptr[b1] = jb.map;
+        }
+        SAD_RET(run_batch(ctx, bt, base, stream));
+        if (b1 < p) SAD_CUDA(cudaStreamSynchronize(stream));  // the next batch reuses the batch workspace
+        b0 = b1;
+    }
+    // anchors, the joined layout, the joined column of every bucket column
+    int32_t** d_mp = (int32_t**)(w + o_mp);
+    SAD_CUDA(cudaMemcpyAsync(d_mp, map_ptr.data(), 8ull * p, cudaMemcpyHostToDevice, stream));
+    const unsigned cblocks = (unsigned)std::min<int64_t>((std::max<int64_t>(Wtot, 1) + 255) / 256,
+                                                         (int64_t)ctx->num_sms * 16);
+    if (Wtot > 0) {
+        k_anchors<<<cblocks, 256, 0, stream>>>(p, d_coff, d_mp, lg, d_an, d_ins, d_first);
+        SAD_LAUNCHED();
+    }
+    k_glue_layout<<<1, 1024, 0, stream>>>(p, lg, d_ins, (int32_t*)(w + o_sizes), d_start);
+    SAD_LAUNCHED();
+    if (Wtot > 0) {
+        k_joined<<<cblocks, 256, 0, stream>>>(p, d_coff, d_an, d_start, d_first, d_join);
+        SAD_LAUNCHED();
+    }
+    // drop the columns without residues
+    if (npos > 0) {
+        k_glue_residues<<<blocks, 256, 0, stream>>>(0, d_od, npos, S.len, d_pos, d_pb, d_coff, d_wd, d_cm, d_join,
+                                                    d_used, nullptr, nullptr);
+        SAD_LAUNCHED();
+    }
+    k_scan_one<<<1, 1024, 0, stream>>>(d_used, J, d_renum);
+    SAD_LAUNCHED();
+    if (npos > 0) {
+        k_glue_residues<<<blocks, 256, 0, stream>>>(1, d_od, npos, S.len, d_pos, d_pb, d_coff, d_wd, d_cm, d_join,
+                                                    nullptr, d_renum, d_gcm);
+        SAD_LAUNCHED();
+    }
+    // outputs
+    const cudaMemcpyKind k_out = mem == SAD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    SAD_CUDA(cudaMemcpyAsync(global_width, d_renum + J, 4, k_out, stream));
+    if (mem == SAD_MEM_HOST) {
+        SAD_CUDA(cudaMemcpyAsync(ga_scores, d_sc, 8ull * p, cudaMemcpyDeviceToHost, stream));
+        if (Wtot > 0) SAD_CUDA(cudaMemcpyAsync(anchors, d_an, 4ull * Wtot, cudaMemcpyDeviceToHost, stream));
+        if (T_res > 0) SAD_CUDA(cudaMemcpyAsync(global_colmap, d_gcm, 4ull * T_res, cudaMemcpyDeviceToHost, stream));
     }
     SAD_RET(status_check(ctx, stream));
     return SAD_OK;

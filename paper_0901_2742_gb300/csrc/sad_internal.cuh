@@ -54,6 +54,7 @@ enum : uint32_t {
     STATUS_BAD_RESIDUE = 1u << 0,   // a residue code >= alphabet
     STATUS_TIMEOUT = 1u << 1,       // a bounded wait gave up
     STATUS_CAPACITY = 1u << 2,      // an internal capacity was exceeded
+    STATUS_BAD_INPUT = 1u << 3,     // an input array holds a value out of range
 };
 
 // Workspace slots; each slot is a grow-only device buffer owned by a context.

@@ -89,6 +89,7 @@ def load():
         "sad_kmer_gemm_work": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "sad_guide_trees": (ctypes.c_int, [P, P, i32, P, P, P, P, P, P, P, i32, P]),
         "sad_progressive_align": (ctypes.c_int, [P, P, P, P, i32, P, P, P, P, i32, i32, P, P, P, P, i32, P]),
+        "sad_ancestor_glue": (ctypes.c_int, [P, P, P, P, i32, P, P, i32, P, i32, i32, P, P, P, P, i32, P]),
         "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -439,6 +440,31 @@ def progressive_align(residues, offsets, alphabet: int, bucket_offsets, order, m
                                         _ptr(rt), S.ctypes.data, gap_open, gap_extend, _ptr(widths), _ptr(ms),
                                         _ptr(mw), _ptr(cm), mem, _stream(stream, mem)))
     return dict(widths=widths, merge_scores=ms[:M], merge_widths=mw[:M], colmap=cm[:total])
+
+
+def ancestor_glue(residues, offsets, alphabet: int, bucket_offsets, order, widths, colmap, ga: int, subst,
+                  gap_open: int, gap_extend: int, ctx=None, stream=None) -> dict:
+    """sad_ancestor_glue: dict(ga_scores[p], anchors[sum widths], width, colmap) -- every
+    bucket's alignment realigned against sequence ga and all joined through
+    its positions; colmap gives the joined column of every residue."""
+    mem = _mode(residues, offsets, bucket_offsets, order, widths, colmap)
+    res, offs = _as(residues, np.uint8, mem), _as(offsets, np.int64, mem)
+    bo, od = _as(bucket_offsets, np.int32, mem), _as(order, np.int32, mem)
+    wd, cm = _as(widths, np.int32, mem), _as(colmap, np.int32, mem)
+    S = _host(subst, np.int8)
+    p = bo.shape[0] - 1
+    wd_h = wd.cpu().numpy() if mem == MEM_DEVICE else wd
+    total_w = int(np.asarray(wd_h, np.int64).sum())
+    scores = _empty(p, np.int64, mem, offs)
+    anchors = _empty(max(total_w, 1), np.int32, mem, offs)
+    gw = _empty(1, np.int32, mem, offs)
+    gcm = _empty(max(cm.shape[0], 1), np.int32, mem, offs)
+    ss = _seqset(res, offs, alphabet)
+    _check(load().sad_ancestor_glue(_ctx(ctx), ctypes.byref(ss), _ptr(bo), _ptr(od), p, _ptr(wd), _ptr(cm), int(ga),
+                                    S.ctypes.data, gap_open, gap_extend, _ptr(scores), _ptr(anchors), _ptr(gw),
+                                    _ptr(gcm), mem, _stream(stream, mem)))
+    width = int(gw[0].item()) if mem == MEM_DEVICE else int(gw[0])
+    return dict(ga_scores=scores, anchors=anchors[:total_w], width=width, colmap=gcm[:cm.shape[0]])
 
 
 def columns(out: dict, k: int) -> str:
