@@ -169,10 +169,23 @@ k_prof_scores(ProgArgs a) {
         const int32_t cblocks = (n + 31) / 32, nsteps = n + kPrG - 1;
         const int32_t tt = tile - jb.tile0, s = tt / cblocks, cb = tt - s * cblocks;
         __syncthreads();  // the previous tile's reads of cps / pbs are done (and sub is loaded)
-        for (int t = threadIdx.x; t < kPrStrip * A; t += blockDim.x) {
-            const int32_t r = t / A, l = t - r * A;
-            const int64_t i = (int64_t)s * kPrStrip + r;
-            cps[r * st + l] = i < m ? (int32_t)jb.prof_p[i * Ap + l] : 0;
+        // a profile of one member is one letter per column (its count is 1): the
+        // sums over letters then reduce to lookups (the same integers)
+        const bool one_p = jb.np == 1, one_q = jb.nq == 1;
+        if (one_p) {
+            for (int r = threadIdx.x; r < kPrStrip; r += blockDim.x) {
+                const int64_t i = (int64_t)s * kPrStrip + r;
+                int32_t letter = -1;
+                if (i < m)
+                    for (int32_t l = 0; l < A; l++) letter = jb.prof_p[i * Ap + l] ? l : letter;
+                cps[r] = letter;
+            }
+        } else {
+            for (int t = threadIdx.x; t < kPrStrip * A; t += blockDim.x) {
+                const int32_t r = t / A, l = t - r * A;
+                const int64_t i = (int64_t)s * kPrStrip + r;
+                cps[r * st + l] = i < m ? (int32_t)jb.prof_p[i * Ap + l] : 0;
+            }
         }
         for (int t = threadIdx.x; t < 32 * A; t += blockDim.x) {
             const int32_t c = t / A, l = t - c * A;
@@ -180,7 +193,11 @@ k_prof_scores(ProgArgs a) {
             int32_t v = 0;
             if (j < n) {
                 const uint16_t* cq = jb.prof_q + j * Ap;
-                for (int32_t b = 0; b < A; b++) v += sub[l * A + b] * (int32_t)cq[b];
+                if (one_q) {
+                    for (int32_t b = 0; b < A; b++) v = cq[b] ? sub[l * A + b] : v;
+                } else {
+                    for (int32_t b = 0; b < A; b++) v += sub[l * A + b] * (int32_t)cq[b];
+                }
             }
             pbs[c * st + l] = v;
         }
@@ -191,16 +208,25 @@ k_prof_scores(ProgArgs a) {
         for (int r = 0; r < kPrR; r++)
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[r][c] = 0;
-        for (int32_t l = 0; l < A; l++) {
-            int32_t pv[kPrR], qv[4];
+        if (one_p) {
 #pragma unroll
-            for (int r = 0; r < kPrR; r++) pv[r] = cps[(g * kPrR + r) * st + l];
+            for (int r = 0; r < kPrR; r++) {
+                const int32_t letter = cps[g * kPrR + r];
 #pragma unroll
-            for (int c = 0; c < 4; c++) qv[c] = pbs[(c4 * 4 + c) * st + l];
+                for (int c = 0; c < 4; c++) acc[r][c] = letter >= 0 ? pbs[(c4 * 4 + c) * st + letter] : 0;
+            }
+        } else {
+            for (int32_t l = 0; l < A; l++) {
+                int32_t pv[kPrR], qv[4];
 #pragma unroll
-            for (int r = 0; r < kPrR; r++)
+                for (int r = 0; r < kPrR; r++) pv[r] = cps[(g * kPrR + r) * st + l];
 #pragma unroll
-                for (int c = 0; c < 4; c++) acc[r][c] += pv[r] * qv[c];
+                for (int c = 0; c < 4; c++) qv[c] = pbs[(c4 * 4 + c) * st + l];
+#pragma unroll
+                for (int r = 0; r < kPrR; r++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[r][c] += pv[r] * qv[c];
+            }
         }
         int2* out = a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
 #pragma unroll
