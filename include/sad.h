@@ -397,6 +397,13 @@ int sad_progressive_align(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* b
                           int32_t* widths, int64_t* merge_scores, int32_t* merge_widths, int32_t* colmap,
                           int32_t mem, void* stream);
 
+/* Tuning of the profile DP of sad_progressive_align and sad_ancestor_glue:
+ * columns = 1 or 2 subject columns per DP lane step for every batch, 0 (the
+ * default) lets each batch choose (two when it holds at least one merge per
+ * SM or a profile of 1024 columns or more). Results do not depend on it.
+ * Errors: SAD_EINVAL for other values. */
+int sad_progressive_columns(sad_ctx* ctx, int32_t columns);
+
 /* Realignment against the global ancestor and the glue, the last steps of
  * Algorithm Sample-Align-D (Section 2.3.3): the alignment of every bucket
  * (widths[p] and colmap as sad_progressive_align writes them, over the

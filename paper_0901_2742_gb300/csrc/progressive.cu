@@ -48,6 +48,7 @@
 // Profiles (uint16 counts, the alphabet padded to 8) and column maps live in
 // an arena of device chunks that only grows during a call.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -68,8 +69,8 @@ struct ProgJob {
     const uint16_t* prof_q;  // Q: n columns
     uint16_t* prof_r;        // the merged cluster (capacity m + n columns)
     int32_t* map;            // m entries for P's columns, then n for Q's
-    int64_t s_off;           // cell-score streams (int2): strips x 32 lanes x (n + 31) steps, then padding
-    int64_t d_off;           // direction words (uint16, strips x (n + 31) x 32)
+    int64_t s_off;           // cell-score streams (int4): strips x 32 lanes x (ceil(n/2) + 31) steps, then padding
+    int64_t d_off;           // direction words (uint32, strips x (ceil(n/2) + 31) x 32)
     int32_t m, n, np, nq;
     int32_t merge;           // index into the per-merge outputs
     int32_t tile0;           // first score tile (a job has strips x ceil(n / 32) of them)
@@ -83,8 +84,8 @@ struct ProgArgs {
     int32_t alphabet;
     int32_t go, ge;
     const int8_t* subst;
-    int2* S;
-    uint16_t* dirs;
+    void* S;                 // int2 (one column per lane step) or int4 (two) score streams
+    void* dirs;              // uint16 or uint32 direction words
     long long* scores;       // per merge
     int32_t* widths;         // per merge
     uint32_t* status;
@@ -92,7 +93,9 @@ struct ProgArgs {
     int32_t warp_smem;       // dynamic shared bytes of one DP CTA
 };
 
-constexpr int kPrWin = 128;      // steps of direction words the traceback holds in shared memory
+// steps of direction words the traceback holds in shared memory (8 KB either way)
+template <int C>
+__host__ __device__ constexpr int win_steps() { return C == 1 ? 128 : 64; }
 constexpr int kPrPre = 8;        // steps of cell scores a lane loads ahead
 
 template <typename T>
@@ -118,7 +121,7 @@ template <typename T>
 __host__ __device__ inline int64_t bnd_bytes(int32_t maxw) {
     return (3ll * (maxw + 2) * (int64_t)sizeof(T) + 15) / 16 * 16;
 }
-__host__ __device__ inline int64_t win_bytes() { return 2ll * kPrWin * kPrG; }
+__host__ __device__ inline int64_t win_bytes() { return 8192; }
 __host__ __device__ inline int64_t ops_bytes(int32_t maxw) { return (2ll * maxw + 16 + 15) / 16 * 16; }
 // chunks of 32 alignment columns (at most 2 maxw columns), rounded to 4 for alignment
 __host__ __device__ inline int32_t chunk_count(int32_t maxw) { return ((2 * maxw + 31) / 32 + 4) / 4 * 4; }
@@ -149,6 +152,7 @@ __global__ void k_leaf_profiles(const uint8_t* __restrict__ res, const int64_t* 
 // rows' scores as one stream over its steps: column j (1-based) sits at step
 // tau = j - 1 + g.
 constexpr int kScThreads = 256;
+template <int C>
 __global__ void __launch_bounds__(kScThreads)
 k_prof_scores(ProgArgs a) {
     __shared__ int32_t sub[SAD_MAX_ALPHABET * SAD_MAX_ALPHABET];
@@ -166,7 +170,7 @@ k_prof_scores(ProgArgs a) {
         }
         const ProgJob& jb = a.jobs[lo];
         const int32_t m = jb.m, n = jb.n;
-        const int32_t cblocks = (n + 31) / 32, nsteps = n + kPrG - 1;
+        const int32_t cblocks = (n + 31) / 32, nsteps = C == 1 ? n + kPrG - 1 : (n + 1) / 2 + kPrG - 1;
         const int32_t tt = tile - jb.tile0, s = tt / cblocks, cb = tt - s * cblocks;
         __syncthreads();  // the previous tile's reads of cps / pbs are done (and sub is loaded)
         // a profile of one member is one letter per column (its count is 1): the
@@ -228,14 +232,25 @@ k_prof_scores(ProgArgs a) {
                     for (int c = 0; c < 4; c++) acc[r][c] += pv[r] * qv[c];
             }
         }
-        int2* out = a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
+        if constexpr (C == 1) {  // column j0 at step j0 + g
+            int2* out = (int2*)a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const int32_t j0 = cb * 32 + c4 * 4 + c;  // 0-based column
-            if (j0 < n) out[j0 + g] = make_int2(acc[0][c], acc[1][c]);
+            for (int c = 0; c < 4; c++) {
+                const int32_t j0 = cb * 32 + c4 * 4 + c;  // 0-based column
+                if (j0 < n) out[j0 + g] = make_int2(acc[0][c], acc[1][c]);
+            }
+        } else {  // column pair qp (columns 2qp, 2qp + 1) at step qp + g
+            int4* out = (int4*)a.S + jb.s_off + ((int64_t)s * kPrG + g) * nsteps;
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int32_t qp = cb * 16 + c4 * 2 + e;
+                if (2 * qp < n)
+                    out[qp + g] = make_int4(acc[0][2 * e], acc[1][2 * e], acc[0][2 * e + 1], acc[1][2 * e + 1]);
+            }
         }
     }
 }
+
 
 __device__ __forceinline__ int32_t take_row(const int2& v, int r) { return r == 0 ? v.x : v.y; }
 
@@ -252,9 +267,11 @@ __device__ __forceinline__ int32_t take_row(const int2& v, int r) { return r == 
 constexpr int kMaxStrips = 256;
 constexpr int64_t kSpinLimit = 1ll << 22;
 
-template <typename T>
+template <typename T, int C>
 __global__ void __launch_bounds__(kPrG * kPrWarps)
 k_prof_dp(ProgArgs a) {
+    using DirT = typename std::conditional<C == 1, uint16_t, uint32_t>::type;
+    constexpr int kWin = win_steps<C>();
     extern __shared__ __align__(16) unsigned char psm[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -263,7 +280,7 @@ k_prof_dp(ProgArgs a) {
     volatile int32_t* prog = (volatile int32_t*)(psm + W * slot_bytes);
     T* score_sh = (T*)(psm + W * slot_bytes + 4 * kMaxStrips);
     int32_t* len_sh = (int32_t*)(psm + W * slot_bytes + 4 * kMaxStrips + 8);
-    uint16_t* win = (uint16_t*)(psm + W * slot_bytes + 4 * kMaxStrips + 16);
+    DirT* win = (DirT*)(psm + W * slot_bytes + 4 * kMaxStrips + 16);
     uint8_t* ops = psm + W * slot_bytes + 4 * kMaxStrips + 16 + win_bytes();
     int32_t* chP = (int32_t*)(ops + ops_bytes(a.maxw));
     int32_t* chQ = chP + chunk_count(a.maxw);
@@ -276,115 +293,258 @@ k_prof_dp(ProgArgs a) {
         const T gop = w * (T)a.go, gex = w * (T)a.ge, goe = gop + gex;
         const int32_t cap = m + n;
         const int32_t strips = (m + kPrStrip - 1) / kPrStrip;
-        const int32_t nsteps = n + kPrG - 1;
-        uint16_t* dirs = a.dirs + jb.d_off;
+        const int32_t nsteps = C == 1 ? n + kPrG - 1 : (n + 1) / 2 + kPrG - 1;  // C columns per lane step
+        DirT* dirs = (DirT*)a.dirs + jb.d_off;
         const bool cells = m > 0 && n > 0;
         for (int t = threadIdx.x; t < strips; t += blockDim.x) prog[t] = 0;
         __syncthreads();
-        for (int32_t s = warp; cells && s < strips; s += W) {
-            const T* bin = (const T*)(psm + ((s + W - 1) % W) * slot_bytes);
-            T* bout = (T*)(psm + (s % W) * slot_bytes);
-            const int32_t row0 = s * kPrStrip + lane * kPrR;  // rows row0+1 .. row0+2 (1-based)
-            T mm[kPrR], xx[kPrR], yy[kPrR], hh[kPrR];          // values at the previous column
-#pragma unroll
-            for (int r = 0; r < kPrR; r++) {
-                mm[r] = NEG;
-                xx[r] = gop + (T)(row0 + r + 1) * gex;  // X(i, 0)
-                yy[r] = NEG;
-                hh[r] = xx[r];
+        // one cell: diagonal hd = H(i-1, j-1), (am, ax, ay) = (M, X, Y)(i-1, j),
+        // (lm, lx, ly) = (M, X, Y)(i, j-1); returns the direction byte
+        auto cell = [&](T hd, T am, T ax, T ay, T lm, T lx, T ly, int32_t sc, T& M, T& X, T& Y, T& H) -> uint32_t {
+            bool xs, xe, ys, ye, xy, mb;
+            M = hd + (T)sc;
+            X = bmax(ax + gex, bmax(am, ay, xs) + goe, xe);
+            Y = bmax(ly + gex, bmax(lm, lx, ys) + goe, ye);
+            H = bmax(M, bmax(X, Y, xy), mb);
+            return (mb ? 0u : (xy ? 1u : 2u)) | (xe ? 4u : 0u) | (xs ? 8u : 0u) | (ye ? 16u : 0u) | (ys ? 32u : 0u);
+        };
+        if constexpr (C == 1) {
+            for (int32_t s = warp; cells && s < strips; s += W) {
+                const T* bin = (const T*)(psm + ((s + W - 1) % W) * slot_bytes);
+                T* bout = (T*)(psm + (s % W) * slot_bytes);
+                const int32_t row0 = s * kPrStrip + lane * kPrR;  // rows row0+1 .. row0+2 (1-based)
+                T mm[kPrR], xx[kPrR], yy[kPrR], hh[kPrR];          // values at the previous column
+    #pragma unroll
+                for (int r = 0; r < kPrR; r++) {
+                    mm[r] = NEG;
+                    xx[r] = gop + (T)(row0 + r + 1) * gex;  // X(i, 0)
+                    yy[r] = NEG;
+                    hh[r] = xx[r];
+                }
+                T hdiag = row0 == 0 ? (T)0 : gop + (T)row0 * gex;  // H(row0, 0)
+                T min_ = NEG, xin = NEG, yin = NEG;                // (row0, j) from above
+                const bool last_strip = s == strips - 1;
+                int32_t avail = s == 0 ? n : 0;                    // columns of the strip above known written
+                // this lane's score stream (the job's padding keeps the look-ahead in bounds)
+                const int2* Sl = (const int2*)a.S + jb.s_off + ((int64_t)s * kPrG + lane) * nsteps;
+                int2 cur[kPrPre], nxt[kPrPre];
+    #pragma unroll
+                for (int u = 0; u < kPrPre; u++) cur[u] = Sl[u];
+                for (int32_t tau0 = 0; tau0 < nsteps; tau0 += kPrPre) {
+    #pragma unroll
+                    for (int u = 0; u < kPrPre; u++) nxt[u] = Sl[tau0 + kPrPre + u];
+    #pragma unroll
+                    for (int u = 0; u < kPrPre; u++) {
+                        const int32_t tau = tau0 + u;
+                        if (tau >= nsteps) break;
+                        if (lane == 0 && tau < n) {
+                            if (s == 0) {
+                                min_ = NEG;
+                                xin = NEG;
+                                yin = gop + (T)(tau + 1) * gex;  // Y(0, j)
+                            } else {
+                                if (avail < tau + 1) {  // wait (bounded) for the strip above
+                                    int64_t spins = 0;
+                                    while ((avail = prog[s - 1]) < tau + 1 && ++spins < kSpinLimit) __nanosleep(32);
+                                    if (spins >= kSpinLimit) {
+                                        atomicOr(a.status, STATUS_TIMEOUT);
+                                        avail = n;
+                                    }
+                                    __threadfence_block();
+                                }
+                                const volatile T* vb = bin;
+                                min_ = vb[3 * (tau + 1)];
+                                xin = vb[3 * (tau + 1) + 1];
+                                yin = vb[3 * (tau + 1) + 2];
+                            }
+                        }
+                        const int32_t j = tau - lane + 1;
+                        T mo = min_, xo = xin, yo = yin;
+                        if (j >= 1 && j <= n) {
+                            const int2 sv = cur[u];
+                            T hd = hdiag, am = min_, ax = xin, ay = yin;
+                            uint32_t bits = 0;
+    #pragma unroll
+                            for (int r = 0; r < kPrR; r++) {
+                                bool xs, xe, ys, ye, xy, mb;
+                                const T M = hd + (T)take_row(sv, r);
+                                const T X = bmax(ax + gex, bmax(am, ay, xs) + goe, xe);
+                                const T Y = bmax(yy[r] + gex, bmax(mm[r], xx[r], ys) + goe, ye);
+                                const T H = bmax(M, bmax(X, Y, xy), mb);
+                                const uint32_t b = (mb ? 0u : (xy ? 1u : 2u)) | (xe ? 4u : 0u) | (xs ? 8u : 0u) |
+                                                   (ye ? 16u : 0u) | (ys ? 32u : 0u);
+                                bits |= b << (8 * r);
+                                hd = hh[r];  // H(i, j-1): the next row's diagonal
+                                mm[r] = M;
+                                xx[r] = X;
+                                yy[r] = Y;
+                                hh[r] = H;
+                                am = M;
+                                ax = X;
+                                ay = Y;
+                            }
+                            dirs[((int64_t)s * nsteps + tau) * kPrG + lane] = (uint16_t)bits;
+                            hdiag = max3(min_, xin, yin);  // H(row0, j): the next column's diagonal
+                            mo = am;
+                            xo = ax;
+                            yo = ay;
+                            if (!last_strip && lane == kPrG - 1) {
+                                volatile T* vb = bout;
+                                vb[3 * j] = mo;
+                                vb[3 * j + 1] = xo;
+                                vb[3 * j + 2] = yo;
+                                __threadfence_block();
+                                prog[s] = j;
+                            }
+                        }
+                        min_ = __shfl_up_sync(0xffffffffu, mo, 1);
+                        xin = __shfl_up_sync(0xffffffffu, xo, 1);
+                        yin = __shfl_up_sync(0xffffffffu, yo, 1);
+                    }
+    #pragma unroll
+                    for (int u = 0; u < kPrPre; u++) cur[u] = nxt[u];
+                }
+                if (last_strip) {
+                    // (named values: a select over the array would put it in local memory)
+                    static_assert(kPrR == 2, "two rows per lane");
+                    const int32_t rr = (m - 1) - s * kPrStrip;
+                    const T v = (rr % kPrR) == 0 ? hh[0] : hh[1];
+                    const T sc = __shfl_sync(0xffffffffu, v, rr / kPrR);
+                    if (lane == 0) *score_sh = sc;
+                }
+                __syncwarp();
             }
-            T hdiag = row0 == 0 ? (T)0 : gop + (T)row0 * gex;  // H(row0, 0)
-            T min_ = NEG, xin = NEG, yin = NEG;                // (row0, j) from above
-            const bool last_strip = s == strips - 1;
-            int32_t avail = s == 0 ? n : 0;                    // columns of the strip above known written
-            // this lane's score stream (the job's padding keeps the look-ahead in bounds)
-            const int2* Sl = a.S + jb.s_off + ((int64_t)s * kPrG + lane) * nsteps;
-            int2 cur[kPrPre], nxt[kPrPre];
-#pragma unroll
-            for (int u = 0; u < kPrPre; u++) cur[u] = Sl[u];
-            for (int32_t tau0 = 0; tau0 < nsteps; tau0 += kPrPre) {
-#pragma unroll
-                for (int u = 0; u < kPrPre; u++) nxt[u] = Sl[tau0 + kPrPre + u];
-#pragma unroll
-                for (int u = 0; u < kPrPre; u++) {
-                    const int32_t tau = tau0 + u;
-                    if (tau >= nsteps) break;
-                    if (lane == 0 && tau < n) {
-                        if (s == 0) {
-                            min_ = NEG;
-                            xin = NEG;
-                            yin = gop + (T)(tau + 1) * gex;  // Y(0, j)
-                        } else {
-                            if (avail < tau + 1) {  // wait (bounded) for the strip above
-                                int64_t spins = 0;
-                                while ((avail = prog[s - 1]) < tau + 1 && ++spins < kSpinLimit) __nanosleep(32);
-                                if (spins >= kSpinLimit) {
-                                    atomicOr(a.status, STATUS_TIMEOUT);
-                                    avail = n;
+        } else {
+            for (int32_t s = warp; cells && s < strips; s += W) {
+                const T* bin = (const T*)(psm + ((s + W - 1) % W) * slot_bytes);
+                T* bout = (T*)(psm + (s % W) * slot_bytes);
+                const int32_t row0 = s * kPrStrip + lane * kPrR;  // rows row0+1 .. row0+2 (1-based)
+                T mm[kPrR], xx[kPrR], yy[kPrR], hh[kPrR];          // values at the previous column
+    #pragma unroll
+                for (int r = 0; r < kPrR; r++) {
+                    mm[r] = NEG;
+                    xx[r] = gop + (T)(row0 + r + 1) * gex;  // X(i, 0)
+                    yy[r] = NEG;
+                    hh[r] = xx[r];
+                }
+                T hdiag = row0 == 0 ? (T)0 : gop + (T)row0 * gex;  // H(row0, 0)
+                // (row0, j0) and (row0, j1) from above, j0 = 2q + 1, j1 = 2q + 2 for pair q
+                T a0m = NEG, a0x = NEG, a0y = NEG, a1m = NEG, a1x = NEG, a1y = NEG;
+                const bool last_strip = s == strips - 1;
+                int32_t avail = s == 0 ? n : 0;                    // columns of the strip above known written
+                // this lane's score stream (the job's padding keeps the look-ahead in bounds)
+                const int4* Sl = (const int4*)a.S + jb.s_off + ((int64_t)s * kPrG + lane) * nsteps;
+                int4 cur[kPrPre], nxt[kPrPre];
+    #pragma unroll
+                for (int u = 0; u < kPrPre; u++) cur[u] = Sl[u];
+                for (int32_t tau0 = 0; tau0 < nsteps; tau0 += kPrPre) {
+    #pragma unroll
+                    for (int u = 0; u < kPrPre; u++) nxt[u] = Sl[tau0 + kPrPre + u];
+    #pragma unroll
+                    for (int u = 0; u < kPrPre; u++) {
+                        const int32_t tau = tau0 + u;
+                        if (tau >= nsteps) break;
+                        const int32_t lj0 = 2 * tau + 1;  // lane 0's columns this step
+                        if (lane == 0 && lj0 <= n) {
+                            const int32_t lj1 = min(lj0 + 1, n);
+                            if (s == 0) {
+                                a0m = a0x = a1m = a1x = NEG;
+                                a0y = gop + (T)lj0 * gex;  // Y(0, j)
+                                a1y = gop + (T)(lj0 + 1) * gex;
+                            } else {
+                                if (avail < lj1) {  // wait (bounded) for the strip above
+                                    int64_t spins = 0;
+                                    while ((avail = prog[s - 1]) < lj1 && ++spins < kSpinLimit) __nanosleep(32);
+                                    if (spins >= kSpinLimit) {
+                                        atomicOr(a.status, STATUS_TIMEOUT);
+                                        avail = n;
+                                    }
+                                    __threadfence_block();
+                                }
+                                const volatile T* vb = bin;
+                                a0m = vb[3 * lj0];
+                                a0x = vb[3 * lj0 + 1];
+                                a0y = vb[3 * lj0 + 2];
+                                a1m = vb[3 * lj1];  // (lj1 = n when lj0 = n: not used then)
+                                a1x = vb[3 * lj1 + 1];
+                                a1y = vb[3 * lj1 + 2];
+                            }
+                        }
+                        const int32_t q = tau - lane;
+                        const int32_t j0 = 2 * q + 1;
+                        T o0m = a0m, o0x = a0x, o0y = a0y, o1m = a1m, o1x = a1x, o1y = a1y;
+                        if (q >= 0 && j0 <= n) {
+                            const bool two = j0 < n;
+                            const int4 sv = cur[u];
+                            T M00, X00, Y00, H00, M10, X10, Y10, H10, M01, X01, Y01, H01, M11, X11, Y11, H11;
+                            // the two chains (one per column) interleave: (r0,c0); (r1,c0) with (r0,c1); (r1,c1)
+                            const uint32_t b00 = cell(hdiag, a0m, a0x, a0y, mm[0], xx[0], yy[0], sv.x, M00, X00, Y00, H00);
+                            const uint32_t b10 = cell(hh[0], M00, X00, Y00, mm[1], xx[1], yy[1], sv.y, M10, X10, Y10, H10);
+                            const T hup = max3(a0m, a0x, a0y);  // H(row0, j0)
+                            const uint32_t b01 = cell(hup, a1m, a1x, a1y, M00, X00, Y00, sv.z, M01, X01, Y01, H01);
+                            const uint32_t b11 = cell(H00, M01, X01, Y01, M10, X10, Y10, sv.w, M11, X11, Y11, H11);
+                            dirs[((int64_t)s * nsteps + tau) * kPrG + lane] =
+                                b00 | (b10 << 8) | (two ? (b01 << 16) | (b11 << 24) : 0u);
+                            o0m = M10;
+                            o0x = X10;
+                            o0y = Y10;
+                            if (two) {
+                                mm[0] = M01;
+                                xx[0] = X01;
+                                yy[0] = Y01;
+                                hh[0] = H01;
+                                mm[1] = M11;
+                                xx[1] = X11;
+                                yy[1] = Y11;
+                                hh[1] = H11;
+                                hdiag = max3(a1m, a1x, a1y);  // H(row0, j1): the next pair's diagonal
+                                o1m = M11;
+                                o1x = X11;
+                                o1y = Y11;
+                            } else {
+                                mm[0] = M00;
+                                xx[0] = X00;
+                                yy[0] = Y00;
+                                hh[0] = H00;
+                                mm[1] = M10;
+                                xx[1] = X10;
+                                yy[1] = Y10;
+                                hh[1] = H10;
+                            }
+                            if (!last_strip && lane == kPrG - 1) {
+                                volatile T* vb = bout;
+                                vb[3 * j0] = o0m;
+                                vb[3 * j0 + 1] = o0x;
+                                vb[3 * j0 + 2] = o0y;
+                                if (two) {
+                                    vb[3 * j0 + 3] = o1m;
+                                    vb[3 * j0 + 4] = o1x;
+                                    vb[3 * j0 + 5] = o1y;
                                 }
                                 __threadfence_block();
+                                prog[s] = two ? j0 + 1 : j0;
                             }
-                            const volatile T* vb = bin;
-                            min_ = vb[3 * (tau + 1)];
-                            xin = vb[3 * (tau + 1) + 1];
-                            yin = vb[3 * (tau + 1) + 2];
                         }
+                        a0m = __shfl_up_sync(0xffffffffu, o0m, 1);
+                        a0x = __shfl_up_sync(0xffffffffu, o0x, 1);
+                        a0y = __shfl_up_sync(0xffffffffu, o0y, 1);
+                        a1m = __shfl_up_sync(0xffffffffu, o1m, 1);
+                        a1x = __shfl_up_sync(0xffffffffu, o1x, 1);
+                        a1y = __shfl_up_sync(0xffffffffu, o1y, 1);
                     }
-                    const int32_t j = tau - lane + 1;
-                    T mo = min_, xo = xin, yo = yin;
-                    if (j >= 1 && j <= n) {
-                        const int2 sv = cur[u];
-                        T hd = hdiag, am = min_, ax = xin, ay = yin;
-                        uint32_t bits = 0;
-#pragma unroll
-                        for (int r = 0; r < kPrR; r++) {
-                            bool xs, xe, ys, ye, xy, mb;
-                            const T M = hd + (T)take_row(sv, r);
-                            const T X = bmax(ax + gex, bmax(am, ay, xs) + goe, xe);
-                            const T Y = bmax(yy[r] + gex, bmax(mm[r], xx[r], ys) + goe, ye);
-                            const T H = bmax(M, bmax(X, Y, xy), mb);
-                            const uint32_t b = (mb ? 0u : (xy ? 1u : 2u)) | (xe ? 4u : 0u) | (xs ? 8u : 0u) |
-                                               (ye ? 16u : 0u) | (ys ? 32u : 0u);
-                            bits |= b << (8 * r);
-                            hd = hh[r];  // H(i, j-1): the next row's diagonal
-                            mm[r] = M;
-                            xx[r] = X;
-                            yy[r] = Y;
-                            hh[r] = H;
-                            am = M;
-                            ax = X;
-                            ay = Y;
-                        }
-                        dirs[((int64_t)s * nsteps + tau) * kPrG + lane] = (uint16_t)bits;
-                        hdiag = max3(min_, xin, yin);  // H(row0, j): the next column's diagonal
-                        mo = am;
-                        xo = ax;
-                        yo = ay;
-                        if (!last_strip && lane == kPrG - 1) {
-                            volatile T* vb = bout;
-                            vb[3 * j] = mo;
-                            vb[3 * j + 1] = xo;
-                            vb[3 * j + 2] = yo;
-                            __threadfence_block();
-                            prog[s] = j;
-                        }
-                    }
-                    min_ = __shfl_up_sync(0xffffffffu, mo, 1);
-                    xin = __shfl_up_sync(0xffffffffu, xo, 1);
-                    yin = __shfl_up_sync(0xffffffffu, yo, 1);
+    #pragma unroll
+                    for (int u = 0; u < kPrPre; u++) cur[u] = nxt[u];
                 }
-#pragma unroll
-                for (int u = 0; u < kPrPre; u++) cur[u] = nxt[u];
+                if (last_strip) {
+                    // (named values: a select over the array would put it in local memory)
+                    static_assert(kPrR == 2, "two rows per lane");
+                    const int32_t rr = (m - 1) - s * kPrStrip;
+                    const T v = (rr % kPrR) == 0 ? hh[0] : hh[1];
+                    const T sc = __shfl_sync(0xffffffffu, v, rr / kPrR);
+                    if (lane == 0) *score_sh = sc;
+                }
+                __syncwarp();
             }
-            if (last_strip) {
-                // (named values: a select over the array would put it in local memory)
-                static_assert(kPrR == 2, "two rows per lane");
-                const int32_t rr = (m - 1) - s * kPrStrip;
-                const T v = (rr % kPrR) == 0 ? hh[0] : hh[1];
-                const T sc = __shfl_sync(0xffffffffu, v, rr / kPrR);
-                if (lane == 0) *score_sh = sc;
-            }
-            __syncwarp();
         }
         __syncthreads();  // every strip's directions are written
         if (warp == 0) {
@@ -397,7 +557,7 @@ k_prof_dp(ProgArgs a) {
             } else {
                 score = *score_sh;
                 // traceback, one column per step: every lane walks the same path (the
-                // direction words come from a shared window of kPrWin steps of one
+                // direction words come from a shared window of kWin steps of one
                 // strip, reloaded by the whole warp when the path leaves it); lane 0
                 // writes the columns backwards from the end of the slot. The cell
                 // (i, jj) sits in strip s, lane t, row r of the lane, step tau.
@@ -418,26 +578,29 @@ k_prof_dp(ProgArgs a) {
                     const bool valid = ci > 0 && cj > 0 && (state != 3 || lane == 0);
                     const uint32_t q = (uint32_t)(ci - 1);
                     const int32_t cs = (int32_t)(q / kPrStrip), ct = (int32_t)((q % kPrStrip) / kPrR);
-                    const int32_t ctau = cj - 1 + ct;
-                    bool inwin = valid && cs == ws && ctau >= wt0 && ctau < wt0 + kPrWin;
+                    const int32_t ctau = (C == 1 ? cj - 1 : (cj - 1) / 2) + ct;  // C columns per lane step
+                    bool inwin = valid && cs == ws && ctau >= wt0 && ctau < wt0 + kWin;
                     // the first cell ahead must be in the window: reload around it
                     const bool need = __shfl_sync(0xffffffffu, valid && !inwin, 0);
                     if (need) {
                         ws = __shfl_sync(0xffffffffu, cs, 0);
-                        wt0 = max(0, __shfl_sync(0xffffffffu, ctau, 0) - kPrWin + 1);
+                        wt0 = max(0, __shfl_sync(0xffffffffu, ctau, 0) - kWin + 1);
                         __syncwarp();
-                        // kPrWin steps x 32 lanes of uint16 = kPrWin * 4 chunks of 16 bytes
-                        for (int e = lane; e < kPrWin * 4; e += 32) {
-                            const int32_t u = e >> 2, part = e & 3;
+                        // kWin steps x 32 lanes of DirT, in 16-byte chunks (kChunks per step)
+                        constexpr int kChunks = 2 * (int)sizeof(DirT);
+                        for (int e = lane; e < kWin * kChunks; e += 32) {
+                            const int32_t u = e / kChunks, part = e % kChunks;
                             if (wt0 + u < nsteps)
-                                ((uint4*)win)[e] =
-                                    *(const uint4*)(dirs + ((int64_t)ws * nsteps + wt0 + u) * kPrG + part * 8);
+                                ((uint4*)win)[e] = *(const uint4*)(dirs + ((int64_t)ws * nsteps + wt0 + u) * kPrG +
+                                                                   part * (16 / (int)sizeof(DirT)));
                         }
                         __syncwarp();
-                        inwin = valid && cs == ws && ctau >= wt0 && ctau < wt0 + kPrWin;
+                        inwin = valid && cs == ws && ctau >= wt0 && ctau < wt0 + kWin;
                     }
-                    const uint32_t bb =
-                        inwin ? (((uint32_t)win[(ctau - wt0) * kPrG + ct] >> (8 * (q % kPrR))) & 0xffu) : 0u;
+                    // byte of the cell: row r; with two columns per step, column half h = (cj - 1) & 1
+                    // holds bytes 2h (row 0) and 2h + 1
+                    const int32_t byte = C == 1 ? (int32_t)(q % kPrR) : 2 * ((cj - 1) & 1) + (int32_t)(q % kPrR);
+                    const uint32_t bb = inwin ? (((uint32_t)win[(ctau - wt0) * kPrG + ct] >> (8 * byte)) & 0xffu) : 0u;
                     if (state == 3) {
                         state = (int32_t)(__shfl_sync(0xffffffffu, bb, 0) & 3u);
                         continue;
@@ -608,18 +771,22 @@ struct Arena {
 // A batch of independent merges: every job's offsets into the batch's score
 // streams, direction words and score tiles, and what the launch needs.
 struct Batch {
+    int C = 1;  // columns per DP lane step (1 or 2)
     std::vector<ProgJob> jobs;
     int64_t s_vecs = 0, d_words = 0, maxw = 1, max_strips = 0;
     int32_t tiles = 0;
     bool wide = false;
-    static int64_t streams(int64_t m, int64_t n) {  // score streams plus the look-ahead of the last lane
-        return (m > 0 && n > 0) ? (m + kPrStrip - 1) / kPrStrip * kPrG * (n + kPrG - 1) + 2 * kPrPre : 0;
+    int64_t steps(int64_t n) const { return (C == 1 ? n : (n + 1) / 2) + kPrG - 1; }  // C columns per lane step
+    int64_t streams(int64_t m, int64_t n) const {  // score streams plus the look-ahead of the last lane
+        return (m > 0 && n > 0) ? (m + kPrStrip - 1) / kPrStrip * kPrG * steps(n) + 2 * kPrPre : 0;
     }
-    static int64_t words(int64_t m, int64_t n) {
-        return (m > 0 && n > 0) ? (m + kPrStrip - 1) / kPrStrip * (n + kPrG - 1) * kPrG : 0;
+    int64_t words(int64_t m, int64_t n) const {
+        return (m > 0 && n > 0) ? (m + kPrStrip - 1) / kPrStrip * steps(n) * kPrG : 0;
     }
-    // bytes of scores and directions once a merge of m x n columns is added
-    int64_t bytes_with(int64_t m, int64_t n) const { return 8 * (s_vecs + streams(m, n)) + 2 * (d_words + words(m, n)); }
+    // bytes of scores (8 C per stream element) and directions (2 C per word) once a merge of m x n is added
+    int64_t bytes_with(int64_t m, int64_t n) const {
+        return 8ll * C * (s_vecs + streams(m, n)) + 2ll * C * (d_words + words(m, n));
+    }
     // checks the merge's ranges (SAD_EINVAL) and appends it
     int add(ProgJob jb, int64_t smax, int64_t cmax) {
         const int64_t m = jb.m, n = jb.n, strips = (m + kPrStrip - 1) / kPrStrip;
@@ -641,6 +808,13 @@ struct Batch {
         return SAD_OK;
     }
 };
+
+// Columns per DP lane step for a batch of `jobs` merges whose widest column
+// profile has `maxn` columns (the context can force one form).
+int pick_columns(const sad_ctx* ctx, int64_t jobs, int64_t maxn) {
+    if (ctx->prog_columns == 1 || ctx->prog_columns == 2) return ctx->prog_columns;
+    return (jobs >= ctx->num_sms || maxn >= 1024) ? 2 : 1;
+}
 
 // Launches one batch (score tiles, then the DP: one CTA per merge, one warp
 // per strip up to kPrWarps); `pa` carries the call's parameters and outputs.
@@ -664,8 +838,8 @@ int run_batch(sad_ctx* ctx, const Batch& bt, ProgArgs pa, cudaStream_t stream) {
         lo = (size_t)round_up((int64_t)(lo + bytes), 256);
         return o;
     };
-    const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(8ull * bt.s_vecs + 16),
-                 l_d = lcarve(2ull * bt.d_words + 4);
+    const size_t l_jobs = lcarve(sizeof(ProgJob) * nj), l_s = lcarve(8ull * bt.C * bt.s_vecs + 16),
+                 l_d = lcarve(2ull * bt.C * bt.d_words + 4);
     void* lv_ws = nullptr;
     SAD_RET(workspace(ctx, WS_PROG_LEVEL, lo, stream, &lv_ws));
     char* lw = (char*)lv_ws;
@@ -673,22 +847,20 @@ int run_batch(sad_ctx* ctx, const Batch& bt, ProgArgs pa, cudaStream_t stream) {
     pa.jobs = (const ProgJob*)(lw + l_jobs);
     pa.njobs = nj;
     pa.ntiles = bt.tiles;
-    pa.S = (int2*)(lw + l_s);
-    pa.dirs = (uint16_t*)(lw + l_d);
+    pa.S = lw + l_s;
+    pa.dirs = lw + l_d;
     pa.maxw = (int32_t)bt.maxw;
     pa.warp_smem = (int32_t)cta_smem;
-    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<int32_t>));
-    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_prof_dp<long long>));
+    void (*dp)(ProgArgs) = bt.C == 1 ? (bt.wide ? k_prof_dp<long long, 1> : k_prof_dp<int32_t, 1>)
+                                      : (bt.wide ? k_prof_dp<long long, 2> : k_prof_dp<int32_t, 2>);
+    SAD_RET(allow_max_dynamic_smem(ctx, (const void*)dp));
     if (bt.tiles > 0) {
         const unsigned g1 = (unsigned)std::min<int64_t>(bt.tiles, (int64_t)ctx->num_sms * 8);
-        k_prof_scores<<<g1, kScThreads, 0, stream>>>(pa);
+        if (bt.C == 1) k_prof_scores<1><<<g1, kScThreads, 0, stream>>>(pa);
+        else k_prof_scores<2><<<g1, kScThreads, 0, stream>>>(pa);
         SAD_LAUNCHED();
     }
-    if (bt.wide) {
-        k_prof_dp<long long><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), (size_t)cta_smem, stream>>>(pa);
-    } else {
-        k_prof_dp<int32_t><<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), (size_t)cta_smem, stream>>>(pa);
-    }
+    dp<<<(unsigned)grid_dp, (unsigned)(kPrG * warps_cta), (size_t)cta_smem, stream>>>(pa);
     SAD_LAUNCHED();
     return SAD_OK;
 }
@@ -1029,8 +1201,17 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
     base.status = ctx->d_status;
     for (int32_t lv = 1; lv <= max_level; lv++) {
         const std::vector<int32_t>& ms = by_level[lv];
+        // columns per DP lane step: two when the level holds enough merges to fill the GPU or
+        // wide profiles (fewer instructions per cell), else one (a shorter lag between strips)
+        int64_t maxn = 0;
+        for (int32_t mi : ms) {
+            const int32_t b = merge_bucket[mi];
+            maxn = std::max<int64_t>(maxn, width[cl_off[b] + rt[mi]]);
+        }
+        const int level_c = pick_columns(ctx, (int64_t)ms.size(), maxn);
         for (size_t j0 = 0; j0 < ms.size();) {
             Batch bt;
+            bt.C = level_c;
             size_t j1 = j0;
             while (j1 < ms.size()) {
                 const int32_t mi = ms[j1];
@@ -1258,8 +1439,12 @@ extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const 
     base.widths = (int32_t*)(w + o_mw);
     base.status = ctx->d_status;
     const int64_t budget = (int64_t)1 << 30;
+    int64_t glue_jobs = 0;
+    for (int32_t b = 0; b < p; b++) glue_jobs += bo[b + 1] > bo[b] ? 1 : 0;
+    const int glue_c = pick_columns(ctx, glue_jobs, lg);
     for (int32_t b0 = 0; b0 < p;) {
         Batch bt;
+        bt.C = glue_c;
         int32_t b1 = b0;
         for (; b1 < p; b1++) {
             const int32_t nb = bo[b1 + 1] - bo[b1];
@@ -1323,5 +1508,16 @@ extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const 
         if (T_res > 0) SAD_CUDA(cudaMemcpyAsync(global_colmap, d_gcm, 4ull * T_res, cudaMemcpyDeviceToHost, stream));
     }
     SAD_RET(status_check(ctx, stream));
+    return SAD_OK;
+}
+
+extern "C" int sad_progressive_columns(sad_ctx* ctx_in, int32_t columns) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(columns >= 0 && columns <= 2, SAD_EINVAL, "columns = %d (0, 1 or 2)", columns);
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->prog_columns = columns;
     return SAD_OK;
 }

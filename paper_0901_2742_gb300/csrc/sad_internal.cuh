@@ -149,6 +149,7 @@ struct sad_ctx {
     unsigned long long* gemm_work = nullptr;  // device: k-blocks x BN the last plane GEMM ran
     int64_t gemm_dense_units = 0;             // k-blocks x BN of all its tiles
     std::vector<sad::Buffer> prog_chunks;     // progressive alignment: profile and column-map arena
+    int32_t prog_columns = 0;                 // progressive DP columns per lane step: 0 chosen per batch, 1, 2
 };
 
 namespace sad {

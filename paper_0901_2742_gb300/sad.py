@@ -90,6 +90,7 @@ def load():
         "sad_guide_trees": (ctypes.c_int, [P, P, i32, P, P, P, P, P, P, P, i32, P]),
         "sad_progressive_align": (ctypes.c_int, [P, P, P, P, i32, P, P, P, P, i32, i32, P, P, P, P, i32, P]),
         "sad_ancestor_glue": (ctypes.c_int, [P, P, P, P, i32, P, P, i32, P, i32, i32, P, P, P, P, i32, P]),
+        "sad_progressive_columns": (ctypes.c_int, [P, i32]),
         "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -440,6 +441,11 @@ def progressive_align(residues, offsets, alphabet: int, bucket_offsets, order, m
                                         _ptr(rt), S.ctypes.data, gap_open, gap_extend, _ptr(widths), _ptr(ms),
                                         _ptr(mw), _ptr(cm), mem, _stream(stream, mem)))
     return dict(widths=widths, merge_scores=ms[:M], merge_widths=mw[:M], colmap=cm[:total])
+
+
+def progressive_columns(columns: int, ctx=None):
+    """sad_progressive_columns: force 1 or 2 columns per profile-DP lane step, 0 = per batch."""
+    _check(load().sad_progressive_columns(_ctx(ctx), int(columns)))
 
 
 def ancestor_glue(residues, offsets, alphabet: int, bucket_offsets, order, widths, colmap, ga: int, subst,

@@ -29,6 +29,14 @@ def sad():
     return s
 
 
+@pytest.fixture(params=[1, 2], ids=["one-column steps", "two-column steps"])
+def columns(request, sad):
+    """Force the profile DP form for one test (results must not depend on it)."""
+    sad.progressive_columns(request.param)
+    yield request.param
+    sad.progressive_columns(0)
+
+
 def to_np(x):
     return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
 
@@ -70,7 +78,7 @@ def random_case(rng, A, nbuckets, max_nb, max_len, ga_len):
 
 
 @pytest.mark.parametrize("seed", range(6))
-def test_random_buckets(sad, seed):
+def test_random_buckets(sad, seed, columns):
     """Short sequences over small alphabets (many ties), the ancestor inside or outside the buckets."""
     rng = random.Random(900 + seed)
     A = rng.choice([2, 3, 4])
@@ -88,7 +96,7 @@ def test_random_buckets(sad, seed):
 
 
 @pytest.mark.parametrize("mem", ["host", "device"])
-def test_several_strips(sad, mem):
+def test_several_strips(sad, mem, columns):
     """Bucket alignments wider than one 64-row strip against a long ancestor."""
     rng = random.Random(41)
     S = random_symmetric(rng, 20, -4, 11)

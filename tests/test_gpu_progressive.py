@@ -30,6 +30,14 @@ def sad():
     return s
 
 
+@pytest.fixture(params=[1, 2], ids=["one-column steps", "two-column steps"])
+def columns(request, sad):
+    """Force the profile DP form for one test (results must not depend on it)."""
+    sad.progressive_columns(request.param)
+    yield request.param
+    sad.progressive_columns(0)
+
+
 def to_np(x):
     return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
 
@@ -80,7 +88,7 @@ def test_golden_example(sad):
 
 
 @pytest.mark.parametrize("seed", range(6))
-def test_tiny_buckets_on_random_trees(sad, seed):
+def test_tiny_buckets_on_random_trees(sad, seed, columns):
     """Small alphabets and short sequences: many equal alternatives, so the tie order decides."""
     rng = random.Random(seed)
     A = rng.choice([2, 3, 4])
@@ -94,7 +102,7 @@ def test_tiny_buckets_on_random_trees(sad, seed):
 
 
 @pytest.mark.parametrize("mem", ["host", "device"])
-def test_several_strips_and_ragged_tails(sad, mem):
+def test_several_strips_and_ragged_tails(sad, mem, columns):
     """Profiles wider than one 128-row strip, widths not multiples of 4 or 128."""
     rng = random.Random(77)
     S = random_symmetric(rng, 20, -4, 11)
