@@ -818,7 +818,7 @@ int pick_columns(const sad_ctx* ctx, int64_t jobs, int64_t maxn) {
 
 // Launches one batch (score tiles, then the DP: one CTA per merge, one warp
 // per strip up to kPrWarps); `pa` carries the call's parameters and outputs.
-int run_batch(sad_ctx* ctx, const Batch& bt, ProgArgs pa, cudaStream_t stream) {
+int run_batch(sad_ctx* ctx, const Batch& bt, ProgArgs pa, cudaStream_t stream, ProgJob* pin_jobs) {
     const int32_t nj = (int32_t)bt.jobs.size();
     if (nj == 0) return SAD_OK;
     // shared memory: one boundary slot per warp, the progress counts, the
@@ -843,7 +843,9 @@ int run_batch(sad_ctx* ctx, const Batch& bt, ProgArgs pa, cudaStream_t stream) {
     void* lv_ws = nullptr;
     SAD_RET(workspace(ctx, WS_PROG_LEVEL, lo, stream, &lv_ws));
     char* lw = (char*)lv_ws;
-    SAD_CUDA(cudaMemcpyAsync(lw + l_jobs, bt.jobs.data(), sizeof(ProgJob) * nj, cudaMemcpyHostToDevice, stream));
+    // the job table through pinned memory (the caller synchronises before the next batch reuses it)
+    memcpy(pin_jobs, bt.jobs.data(), sizeof(ProgJob) * nj);
+    SAD_CUDA(cudaMemcpyAsync(lw + l_jobs, pin_jobs, sizeof(ProgJob) * nj, cudaMemcpyHostToDevice, stream));
     pa.jobs = (const ProgJob*)(lw + l_jobs);
     pa.njobs = nj;
     pa.ntiles = bt.tiles;
@@ -1188,7 +1190,12 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
     for (int64_t mi = 0; mi < M; mi++) by_level[merge_level[mi]].push_back((int32_t)mi);
     std::vector<int32_t*> map_ptr((size_t)M, nullptr);
     std::vector<int32_t> map_split((size_t)M, 0);
-    std::vector<int32_t> h_mw((size_t)M + 1, 0);
+    // pinned host staging: a batch's job table, and the merge widths read back per level
+    void* pin = nullptr;
+    const size_t pin_jobs_bytes = (size_t)round_up((int64_t)sizeof(ProgJob) * std::max<int64_t>(M, 1), 256);
+    SAD_RET(pinned(ctx, pin_jobs_bytes + 4ull * (M + 1), stream, &pin));
+    ProgJob* pin_jobs = (ProgJob*)pin;
+    int32_t* h_mw = (int32_t*)((char*)pin + pin_jobs_bytes);
     const int64_t budget = (int64_t)1 << 30;  // bytes of cell scores and directions per batch
     ProgArgs base{};
     base.Ap = Ap;
@@ -1241,11 +1248,11 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
                 map_split[mi] = (int32_t)m;
                 j1++;
             }
-            SAD_RET(run_batch(ctx, bt, base, stream));
+            SAD_RET(run_batch(ctx, bt, base, stream, pin_jobs));
             const std::vector<ProgJob>& jobs = bt.jobs;
             // the new widths, for the next level's layout (the jobs' table copy
             // from pageable memory has been consumed when this returns)
-            SAD_CUDA(cudaMemcpyAsync(h_mw.data(), d_mw, 4ull * std::max<int64_t>(M, 1), cudaMemcpyDeviceToHost,
+            SAD_CUDA(cudaMemcpyAsync(h_mw, d_mw, 4ull * std::max<int64_t>(M, 1), cudaMemcpyDeviceToHost,
                                      stream));
             SAD_CUDA(cudaStreamSynchronize(stream));
             for (const ProgJob& jb : jobs) {
@@ -1441,6 +1448,9 @@ extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const 
     const int64_t budget = (int64_t)1 << 30;
     int64_t glue_jobs = 0;
     for (int32_t b = 0; b < p; b++) glue_jobs += bo[b + 1] > bo[b] ? 1 : 0;
+    void* pin = nullptr;
+    SAD_RET(pinned(ctx, sizeof(ProgJob) * (size_t)std::max<int64_t>(glue_jobs, 1), stream, &pin));
+    ProgJob* pin_jobs = (ProgJob*)pin;
     const int glue_c = pick_columns(ctx, glue_jobs, lg);
     for (int32_t b0 = 0; b0 < p;) {
         Batch bt;
@@ -1467,8 +1477,8 @@ extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const 
             SAD_RET(bt.add(jb, smax, cmax));
             map_ptr[b1] = jb.map;
         }
-        SAD_RET(run_batch(ctx, bt, base, stream));
-        if (b1 < p) SAD_CUDA(cudaStreamSynchronize(stream));  // the next batch reuses the batch workspace
+        SAD_RET(run_batch(ctx, bt, base, stream, pin_jobs));
+        if (b1 < p) SAD_CUDA(cudaStreamSynchronize(stream));  // the next batch reuses the workspace and pinned table
         b0 = b1;
     }
     // anchors, the joined layout, the joined column of every bucket column
