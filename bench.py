@@ -433,8 +433,9 @@ def main():
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    clock_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                              else ".", f"clocks_rank{rank}.csv")
+    # the clock samples of the timed region go to $SAD_CLOCKS_DIR (default: the temp directory)
+    import tempfile
+    clock_path = os.path.join(os.environ.get("SAD_CLOCKS_DIR") or tempfile.gettempdir(), f"clocks_rank{rank}.csv")
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
