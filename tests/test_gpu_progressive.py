@@ -173,3 +173,9 @@ def test_bad_tree_is_reported(sad):
     with pytest.raises(sad.SadError):   # merge 1 joins cluster 0 again
         sad.progressive_align(res, offs, 2, bo, od, mo, np.array([0, 0], np.int32), np.array([1, 2], np.int32),
                               S, -3, -1)
+
+
+def test_columns_setting_is_checked(sad):
+    with pytest.raises(sad.SadError):
+        sad.progressive_columns(3)
+    sad.progressive_columns(0)
