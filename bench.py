@@ -175,6 +175,24 @@ def progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od, reps=3):
             "alignment_widths": [int(x) for x in pa["widths"].cpu().numpy()]}
 
 
+def msa_report(sad, w, res_d, offs_d, kw, reps=3):
+    """Wall time of the whole method as one job (sad.msa: device arrays in, the
+    joined alignment out), synchronised on both sides, after one warm-up call."""
+    import torch
+    args = (res_d, offs_d, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend)
+    opts = dict(cap=kw["cap"], kmer_alphabet=kw["kmer_alphabet"], class_map=kw["class_map"])
+    r = sad.msa(*args, **opts)
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = sad.msa(*args, **opts)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    return {"call": "sad.msa (pipeline, guide trees, progressive alignment, glue)",
+            "ms": 1e3 * sum(times) / len(times), "joined_width": int(r["width"]), "reps": reps}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -504,6 +522,7 @@ def main():
                    "largest_bucket": int(sizes.max()), "merges": int(tr["left"].shape[0])}
     # then the progressive alignment of every bucket along its tree (also outside the timed region)
     progressive = progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od)
+    msa = msa_report(sad, w, res_d, offs_d, kw)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -587,6 +606,7 @@ def main():
         "kmer_roofline": kmer_roofline,
         "guide_trees": guide_trees,
         "progressive": progressive,
+        "msa": msa,
         "gpu_launches": int(launches),
         "wall_s": wall,
         "clocks": clocks,

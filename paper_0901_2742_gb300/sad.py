@@ -473,6 +473,32 @@ def ancestor_glue(residues, offsets, alphabet: int, bucket_offsets, order, width
     return dict(ga_scores=scores, anchors=anchors[:total_w], width=width, colmap=gcm[:cm.shape[0]])
 
 
+def msa(residues, offsets, alphabet: int, k: int, p: int, subst, gap_open: int, gap_extend: int, cap: int = 0,
+        kmer_alphabet: int | None = None, class_map=None, ctx=None, stream=None) -> dict:
+    """The whole method on device arrays: sad_pipeline (k-mer rank, partition,
+    pair scores), sad_guide_trees, sad_progressive_align and sad_ancestor_glue
+    with the pipeline's global ancestor. Returns dict(bucket_offsets, order, ga,
+    widths, colmap (each residue's column in its bucket's alignment), width,
+    global_colmap (its column in the joined alignment)); both colmaps run over
+    the residues of order[0], order[1], ... in turn."""
+    mem = _mode(residues, offsets)
+    if mem != MEM_DEVICE:
+        raise SadError(SAD_EINVAL, "msa takes device arrays (torch CUDA tensors)")
+    o = pipeline(residues, offsets, alphabet, k, p, subst, gap_open, gap_extend, cap=cap,
+                 kmer_alphabet=kmer_alphabet, class_map=class_map, mode=PERSISTENT, ctx=ctx, stream=stream)
+    n = int(offsets.shape[0]) - 1
+    total = int(o["score_offsets"][-1].item())
+    t = guide_trees(o["bucket_offsets"], o["score_offsets"], o["scores"][:max(total, 1)], ctx=ctx, stream=stream)
+    order = o["order"][:n]
+    pa = progressive_align(residues, offsets, alphabet, o["bucket_offsets"], order, t["merge_offsets"], t["left"],
+                           t["right"], subst, gap_open, gap_extend, ctx=ctx, stream=stream)
+    ga = int(o["ga"].reshape(-1)[0].item())
+    gl = ancestor_glue(residues, offsets, alphabet, o["bucket_offsets"], order, pa["widths"], pa["colmap"], ga, subst,
+                       gap_open, gap_extend, ctx=ctx, stream=stream)
+    return dict(bucket_offsets=o["bucket_offsets"], order=order, ga=ga, widths=pa["widths"], colmap=pa["colmap"],
+                width=gl["width"], global_colmap=gl["colmap"])
+
+
 def columns(out: dict, k: int) -> str:
     """Columns of pair k of an align_pairs result as a str over M, X, Y."""
     def h(x):
