@@ -1526,10 +1526,21 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
     const int32_t nm = (int32_t)merged.size();
     void* sw = nullptr;
     SAD_RET(workspace(ctx, WS_SCORE_OUT, 4ull * (total + 1), stream, &sw));
+    // every timed run starts with L2 cleared (a 256 MiB write), as a score stage
+    // does after the k-mer stage: the variants differ in how they take misses
+    const size_t flush_bytes = (size_t)256 << 20;
+    void* flush = nullptr;
+    SAD_CUDA(cudaMalloc(&flush, flush_bytes));
+    struct FlushFree {
+        void* p;
+        ~FlushFree() { cudaFree(p); }
+    } flush_free{flush};
     const bool trace_was_on = ctx->trace_on;
     ScoreTuning table = ctx->tuning;
     table.nbins = 0;
     int rc = SAD_OK;
+    // per merged bin: every variant that ran, with its time alone
+    std::vector<std::vector<std::pair<double, std::pair<int, int>>>> ranked((size_t)nm);
     for (int32_t b = 0; b < nm && rc == SAD_OK; b++) {
         double best_ms = 1e300;
         int best_R = 0, best_G = 0;
@@ -1546,17 +1557,21 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
                 for (int32_t r = 0; r <= reps && rc == SAD_OK; r++) {
                     if (r == 1) trace_reset(ctx, true);  // the first run warms up
                     int64_t tot = 0;
-                    rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend,
-                                              SAD_SCORES_PERSISTENT, nullptr, (int32_t*)sw, total, &tot, stream);
+                    if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream) != cudaSuccess) rc = SAD_ECUDA;
+                    if (rc == SAD_OK)
+                        rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend,
+                                                  SAD_SCORES_PERSISTENT, nullptr, (int32_t*)sw, total, &tot, stream);
                 }
                 double ms[SAD_NUM_STAGES];
                 int32_t cnt[SAD_NUM_STAGES];
                 if (rc == SAD_OK) rc = trace_collect(ctx, ms, cnt, SAD_NUM_STAGES);
-                if (rc == SAD_OK && !ctx->tuning.skipped && cnt[SAD_STAGE_SCORES_PACKED] > 0 &&
-                    ms[SAD_STAGE_SCORES_PACKED] < best_ms) {
-                    best_ms = ms[SAD_STAGE_SCORES_PACKED];
-                    best_R = kPackedR[ri];
-                    best_G = kPackedG[gi];
+                if (rc == SAD_OK && !ctx->tuning.skipped && cnt[SAD_STAGE_SCORES_PACKED] > 0) {
+                    ranked[b].push_back({ms[SAD_STAGE_SCORES_PACKED], {kPackedR[ri], kPackedG[gi]}});
+                    if (ms[SAD_STAGE_SCORES_PACKED] < best_ms) {
+                        best_ms = ms[SAD_STAGE_SCORES_PACKED];
+                        best_R = kPackedR[ri];
+                        best_G = kPackedG[gi];
+                    }
                 }
             }
         if (best_R > 0) {
@@ -1567,6 +1582,78 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
         }
     }
     table.filter = false;
+    // Joint refinement: the bins' variants run side by side on forked streams, so
+    // the fastest variant of a bin alone need not be the fastest with the others
+    // running. One pass of coordinate descent over the bins, every variant of a
+    // bin (its four fastest alone when the stage is long) timed as the whole stage
+    // over at least five runs; a change must gain 1 %, and 1.5 % again when measured
+    // beside the current table, and the result must beat the per-bin table.
+    const int32_t jreps = std::max(reps, 5);
+    auto stage_ms = [&](const ScoreTuning& t, double* out) -> int {
+        ctx->tuning = t;
+        trace_reset(ctx, true);
+        for (int32_t r = 0; r <= jreps; r++) {
+            if (r == 1) trace_reset(ctx, true);  // the first run warms up
+            int64_t tot = 0;
+            SAD_CUDA(cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream));
+            SAD_RET(bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend, SAD_SCORES_PERSISTENT,
+                                         nullptr, (int32_t*)sw, total, &tot, stream));
+        }
+        double ms[SAD_NUM_STAGES];
+        int32_t cnt[SAD_NUM_STAGES];
+        SAD_RET(trace_collect(ctx, ms, cnt, SAD_NUM_STAGES));
+        *out = cnt[SAD_STAGE_SCORES_PACKED] > 0 ? ms[SAD_STAGE_SCORES_PACKED] / jreps : 1e300;
+        return SAD_OK;
+    };
+    if (rc == SAD_OK && table.nbins > 1) {
+        const ScoreTuning per_bin = table;
+        std::vector<int32_t> bin_of((size_t)table.nbins, -1);  // merged bin of each table entry
+        for (int32_t e = 0, b = 0; e < table.nbins; e++) {
+            while (b < nm && merged[b] != table.upper[e]) b++;
+            bin_of[e] = b < nm ? b : -1;
+        }
+        double best = 0;
+        rc = stage_ms(table, &best);
+        const size_t max_cands = best > 20.0 ? 4 : 64;
+        for (int pass = 0; pass < 1 && rc == SAD_OK; pass++) {
+            bool improved = false;
+            for (int32_t e = 0; e < table.nbins && rc == SAD_OK; e++) {
+                if (bin_of[e] < 0) continue;
+                auto cands = ranked[bin_of[e]];
+                std::sort(cands.begin(), cands.end());
+                for (size_t c = 0; c < cands.size() && c < max_cands && rc == SAD_OK; c++) {
+                    const int R = cands[c].second.first, G = cands[c].second.second;
+                    if (R == table.R[e] && G == table.G[e]) continue;
+                    ScoreTuning cand = table;
+                    cand.R[e] = R;
+                    cand.G[e] = G;
+                    double t = 0;
+                    rc = stage_ms(cand, &t);
+                    if (rc == SAD_OK && t < 0.99 * best) {
+                        // confirm against the current table, measured again beside it
+                        double now = 0, again = 0;
+                        rc = stage_ms(table, &now);
+                        if (rc == SAD_OK) rc = stage_ms(cand, &again);
+                        if (rc == SAD_OK && again < 0.985 * now) {
+                            best = again;
+                            table = cand;
+                            improved = true;
+                        } else if (rc == SAD_OK) {
+                            best = std::min(best, now);
+                        }
+                    }
+                }
+            }
+            if (!improved) break;
+        }
+        // keep the refined table only if it still beats the per-bin table, measured A, B, A, B
+        double a1 = 0, b1 = 0, a2 = 0, b2 = 0;
+        if (rc == SAD_OK) rc = stage_ms(per_bin, &a1);
+        if (rc == SAD_OK) rc = stage_ms(table, &b1);
+        if (rc == SAD_OK) rc = stage_ms(per_bin, &a2);
+        if (rc == SAD_OK) rc = stage_ms(table, &b2);
+        if (rc == SAD_OK && b1 + b2 > 0.99 * (a1 + a2)) table = per_bin;
+    }
     ctx->tuning = table;
     trace_reset(ctx, trace_was_on);
     return rc;
