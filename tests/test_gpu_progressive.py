@@ -74,8 +74,9 @@ def run_both(sad, alphabet, args, subst, go, ge, mem="host"):
     return got, want
 
 
-def test_golden_example(sad):
-    with open(os.path.join(GOLD, "progressive_tiny.json")) as f:
+@pytest.mark.parametrize("name", ["progressive_tiny.json", "progressive_tree3.json"])
+def test_golden_example(sad, name):
+    with open(os.path.join(GOLD, name)) as f:
         c = json.load(f)
     res, offs = synth.pack(c["seqs"])
     S = np.array(c["subst"], np.int8)
@@ -84,7 +85,7 @@ def test_golden_example(sad):
                                 np.array(c["left"], np.int32), np.array(c["right"], np.int32), S, c["gap_open"],
                                 c["gap_extend"])
     for f in ("widths", "merge_scores", "merge_widths", "colmap"):
-        assert to_np(got[f]).tolist() == c[f], f
+        assert to_np(got[f]).tolist() == c[f], (name, f)
 
 
 @pytest.mark.parametrize("seed", range(6))

@@ -126,14 +126,15 @@ def check_rows(rows, width):
     assert used == set(range(width))
 
 
-def test_golden_example():
-    with open(os.path.join(GOLD, "progressive_tiny.json")) as f:
+@pytest.mark.parametrize("name", ["progressive_tiny.json", "progressive_tree3.json"])
+def test_golden_example(name):
+    with open(os.path.join(GOLD, name)) as f:
         c = json.load(f)
     res, offs = synth.pack(c["seqs"])
     r = oracle.progressive(res, offs, c["bucket_offsets"], c["order"], c["merge_offsets"], c["left"], c["right"],
                            np.array(c["subst"]).ravel(), c["gap_open"], c["gap_extend"])
     for f in ("widths", "merge_scores", "merge_widths", "colmap"):
-        assert r[f].tolist() == c[f], f
+        assert r[f].tolist() == c[f], (name, f)
 
 
 def random_tree(rng, nb):
