@@ -146,3 +146,24 @@ def test_invariants_on_synthetic_families():
     check_glue(seqs, bo.tolist(), order.tolist(), pr["widths"].tolist(), pr["colmap"], int(rk["ga"]), S,
                w.gap_open, w.gap_extend, r, brute=False)
     assert r["width"] >= max(pr["widths"])
+
+
+def test_invariants_at_paper_scale():
+    """N = 2000 families, p = 16: the oracle's trees, bucket alignments and the
+    joined alignment satisfy the same invariants (each realignment re-scored
+    member pair by member pair from its anchors)."""
+    w = synth.workload(2)
+    rk = oracle.kmer_rank(w.residues, w.offsets, w.alphabet, w.k, w.p, want_A=False)
+    pt = oracle.partition(rk["key_a"], rk["key_b"], w.p)
+    bo, order = pt["bucket_offsets"], pt["order"]
+    so, sc = oracle.bucket_pair_scores(w.residues, w.offsets, bo, order, w.subst, w.gap_open, w.gap_extend)
+    t = oracle.guide_trees(bo, so, sc)
+    pr = oracle.progressive(w.residues, w.offsets, bo, order, t["merge_offsets"], t["left"], t["right"], w.subst,
+                            w.gap_open, w.gap_extend)
+    r = oracle.ancestor_glue(w.residues, w.offsets, bo, order, pr["widths"], pr["colmap"], rk["ga"], w.subst,
+                             w.gap_open, w.gap_extend)
+    seqs = [w.residues[w.offsets[i]:w.offsets[i + 1]].tolist() for i in range(w.n)]
+    S = np.array(w.subst, np.int64).reshape(w.alphabet, w.alphabet).tolist()
+    check_glue(seqs, bo.tolist(), order.tolist(), pr["widths"].tolist(), pr["colmap"], int(rk["ga"]), S,
+               w.gap_open, w.gap_extend, r, brute=False)
+    assert r["width"] >= max(pr["widths"])
