@@ -6,6 +6,17 @@ returns numpy arrays) or CUDA torch tensors (device memory; results are CUDA
 tensors, enqueued on the current torch stream unless ``stream`` is given).
 There is no CPU fallback: if the library is missing or the GPU unusable, the
 calls raise.
+
+The whole method on device tensors (residue codes 0..alphabet-1 concatenated,
+int64 offsets of n + 1 entries)::
+
+    out = sad.msa(residues, offsets, 20, 3, 16, subst, -11, -1, cap=4)
+    # out["bucket_offsets"], out["order"]: the p buckets of the k-mer rank partition
+    # out["colmap"]: each residue's column in its bucket's alignment
+    # out["width"], out["global_colmap"]: the joined alignment of all sequences
+
+or step by step: pipeline (rank, partition, pair scores), guide_trees,
+progressive_align, ancestor_glue; align_pairs gives pairwise alignments.
 """
 from __future__ import annotations
 
