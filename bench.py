@@ -40,17 +40,16 @@ METRIC = "Gotoh GCUPS + k-mer sim pairs/s (exact vs oracle); N=2000,L≈316 wall
 DPX_PER_CELL = 3
 SMS = 152
 SM_MAX_MHZ = 2070.0
-DPX_OPS_PER_CLK_SM = 64   # measured: VIADDMNMX and VIMNMX3 (32-bit and 16x2) each 64 lanes/clk/SM
-# measured ceiling of the packed row mix itself (3 DPX + 2 adds per row of two
-# cells, independent chains, every SM busy): 18.7 rows/clk/SM on this GPU
-MIX_ROWS_PER_CLK_SM = 18.7
+# integer lanes per clock per SM: 4 sub-partitions x 16 INT32 lanes; the DPX
+# instructions issue there. bench.py measures the rate they actually retire
+# with sad_probe_alu in every run and reports it beside this unit count.
+DPX_OPS_PER_CLK_SM = 64
 # DRAM bytes (read + write) of the packed score launches of one step of this
 # benchmark, summed from one ncu capture; reported while the score kernels'
 # source is the one that was measured (sha256 of the device code of
 # csrc/gotoh.cu: the text before its host-side planning), else null.
 SCORE_TRAFFIC = {"bytes_per_step": 2253670,
-                 "gotoh_device_sha256": "9d4052235764cd663066df8b7ede0e708d37e75f553bb8f20bd800a90c17c7a3",
-                 "profile": "profiles/gotoh_pair16_n2000.md"}
+                 "gotoh_device_sha256": "9d4052235764cd663066df8b7ede0e708d37e75f553bb8f20bd800a90c17c7a3"}
 DEVICE_CODE_END = "// Host-side plan: per bucket, members sorted by length"
 
 
@@ -193,6 +192,139 @@ def msa_report(sad, w, res_d, offs_d, kw, reps=3):
             "ms": 1e3 * sum(times) / len(times), "joined_width": int(r["width"]), "reps": reps}
 
 
+def alu_probe(sad, warps=16):
+    """The rates the DP roofline is derived for, measured on this GPU by the
+    library's register-only probe (sad_probe_alu): DPX lanes per clock per SM
+    of the two 16x2 DPX instructions alone, and DP rows of two problems per
+    clock per SM of the packed row mix (3 DPX + 2 adds)."""
+    add, _ = sad.probe_alu("viaddmax_s16x2", warps)
+    mx3, _ = sad.probe_alu("vimax3_s16x2", warps)
+    _, rows = sad.probe_alu("row_dpx3_add2", warps)
+    return {"viaddmax_s16x2_lanes_per_clk_sm": add, "vimax3_s16x2_lanes_per_clk_sm": mx3,
+            "row_mix_rows_per_clk_sm": rows, "warps_per_sm": warps}
+
+
+def probe_table(args):
+    """--probe-alu: every mix of sad_probe_alu at 4, 8, 16 and 32 warps per SM."""
+    import torch
+    from paper_0901_2742_gb300 import build, sad
+    build.build()
+    torch.cuda.set_device(0)
+    rows = []
+    for mix in sad.PROBE_MIXES:
+        for warps in (4, 8, 16, 32):
+            lanes, r = sad.probe_alu(mix, warps)
+            rows.append({"mix": mix, "warps_per_sm": warps, "lanes_per_clk_sm": round(lanes, 2),
+                         "rows_per_clk_sm": round(r, 2) if r else None})
+    print(json.dumps({"mode": "probe_alu", "gpu": torch.cuda.get_device_name(0), "table": rows}))
+    return 0
+
+
+def score_forms(sad, w, res_d, offs_d, out_d, flush, reps=3):
+    """The three forms of the alignment-score stage on the same bucket layout
+    and GPU: one launch per bucket (32-bit DP), one persistent launch over all
+    buckets (32-bit DP), and the persistent launch with two problems per 16x2
+    lane. Their score arrays must be equal. Kernel time from the tracer (the
+    score launches only), call time from the host clock (synchronised on both
+    sides, including the host's planning); L2 cleared before each call."""
+    import torch
+    n = w.n
+    args = (res_d, offs_d, w.alphabet, out_d["bucket_offsets"], out_d["order"][:n], w.subst, w.gap_open,
+            w.gap_extend)
+    forms, ref = {}, None
+    for name, mode, stage in (("per_bucket", sad.PER_BUCKET, "scores"),
+                              ("persistent_32bit", sad.PERSISTENT_32, "scores"),
+                              ("persistent_packed", sad.PERSISTENT, "scores_packed")):
+        sad.bucket_pair_scores(*args, mode=mode)  # warm-up (plans, graphs, module load)
+        torch.cuda.synchronize()
+        sad.trace_enable(True)
+        wall = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            so, sc = sad.bucket_pair_scores(*args, mode=mode)
+            torch.cuda.synchronize()
+            wall.append(time.perf_counter() - t0)
+        tr = sad.trace_read()[stage]
+        sad.trace_enable(False)
+        got = sc.cpu().numpy()
+        if ref is None:
+            ref = got
+        forms[name] = {"kernel_ms": tr[0] / reps, "call_ms": 1e3 * statistics.median(wall),
+                       "launches_per_call": tr[1] / reps, "scores_equal_to_per_bucket": bool(np.array_equal(got, ref))}
+    assert all(f["scores_equal_to_per_bucket"] for f in forms.values()), "score forms disagree"
+    pb, p32, pk = (forms[k]["kernel_ms"] for k in ("per_bucket", "persistent_32bit", "persistent_packed"))
+    forms["speedup_batching_32bit"] = pb / p32 if p32 > 0 else None
+    forms["speedup_packing"] = p32 / pk if pk > 0 else None
+    forms["speedup_total"] = pb / pk if pk > 0 else None
+    return forms
+
+
+def serving_report(jobs_n=200, slots=4, seed=5005):
+    """Serving workload: a Poisson stream of partition-and-score jobs with N
+    uniform in 100..5000 and lengths lognormal(median 300, sigma 0.55) in
+    [50, 1500] (k = 3, p = 4), admitted by device memory into a continuous-
+    batching server. Offline capacity = every job submitted at once; the
+    stream then arrives at 0.7 x that rate. Every streamed result is compared
+    with its offline run."""
+    import threading
+
+    from paper_0901_2742_gb300 import sad, synth
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(100, 5001, jobs_n)
+    jobs = [synth.workload(5, seed=10_000 + i, n_override=int(sizes[i])) for i in range(jobs_n)]
+
+    def run_offline():
+        with sad.Server(slots=slots) as srv:
+            t0 = time.perf_counter()
+            ids = [srv.submit(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend)
+                   for w in jobs]
+            for j in ids:
+                assert srv.wait(j) == sad.SAD_OK, srv.error()
+            span = time.perf_counter() - t0
+            outs = [srv.result(j, w.n) for j, w in zip(ids, jobs)]
+            return span, outs, srv.stats()
+
+    run_offline()  # warm-up (workspaces, module load)
+    span, outs, st_off = run_offline()
+    total_cells = 0
+    for w, o in zip(jobs, outs):
+        total_cells += workload_cells(w.lengths(), o["bucket_offsets"], o["order"])
+    capacity = jobs_n / span
+    rate = 0.7 * capacity
+    gaps = -np.log(1.0 - synth.uniform_f64(seed + 1, jobs_n)) / rate
+    arrivals = np.cumsum(gaps)
+    with sad.Server(slots=slots) as srv:
+        ids = [None] * jobs_n
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i, w in enumerate(jobs):
+                delay = arrivals[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids[i] = srv.submit(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open,
+                                    w.gap_extend)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        for j in ids:
+            assert srv.wait(j) == sad.SAD_OK, srv.error()
+        span_stream = time.perf_counter() - t0
+        st = srv.stats()
+        same = all(np.array_equal(srv.result(j, w.n)["scores"], o["scores"]) for j, w, o in zip(ids, jobs, outs))
+    return {"metric": "jobs/s with p50/p99 latency (Poisson arrivals)", "value": st["jobs_per_s"],
+            "unit": "jobs/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "arrival_rate_jobs_per_s": rate, "offline_jobs_per_s": capacity,
+            "offline_gcups": total_cells / span / 1e9, "stream_gcups": total_cells / span_stream / 1e9,
+            "offline_p50_ms": st_off["p50_ms"], "offline_p99_ms": st_off["p99_ms"],
+            "jobs": jobs_n, "slots": slots, "results_identical_to_offline": bool(same),
+            "config": {"workload": "N ~ U{100..5000}, L ~ logN(300, 0.55) in [50, 1500], k=3, p=4, "
+                                   "gap -11/-1"}}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -305,70 +437,12 @@ def run_reference(args, ws, rank):
 
 
 def run_serving(args):
-    """Serving workload: a Poisson stream of partition-and-score jobs with N
-    uniform in 100..5000 and lengths lognormal(median 300, sigma 0.55) in
-    [50, 1500] (k = 3, p = 4), admitted by device memory into a continuous-
-    batching server. Offline capacity = every job submitted at once; the
-    stream then arrives at 0.7 x that rate. Prints one JSON line."""
-    import threading
-
+    """--serving: the serving workload with --jobs jobs; prints one JSON line."""
     import torch
-    from paper_0901_2742_gb300 import build, sad, synth
+    from paper_0901_2742_gb300 import build
     build.build()
     torch.cuda.set_device(0)
-    rng = np.random.default_rng(args.seed)
-    njobs = args.jobs
-    sizes = rng.integers(100, 5001, njobs)
-    jobs = [synth.workload(5, seed=10_000 + i, n_override=int(sizes[i])) for i in range(njobs)]
-
-    def run_offline():
-        with sad.Server(slots=args.slots) as srv:
-            t0 = time.perf_counter()
-            ids = [srv.submit(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open, w.gap_extend)
-                   for w in jobs]
-            for j in ids:
-                assert srv.wait(j) == sad.SAD_OK, srv.error()
-            span = time.perf_counter() - t0
-            outs = [srv.result(j, w.n) for j, w in zip(ids, jobs)]
-            return span, outs, srv.stats()
-
-    run_offline()  # warm-up (workspaces, module load)
-    span, outs, st_off = run_offline()
-    total_cells = 0
-    for w, o in zip(jobs, outs):
-        total_cells += workload_cells(w.lengths(), o["bucket_offsets"], o["order"])
-    capacity = njobs / span
-    rate = 0.7 * capacity
-    gaps = -np.log(1.0 - synth.uniform_f64(args.seed + 1, njobs)) / rate
-    arrivals = np.cumsum(gaps)
-    with sad.Server(slots=args.slots) as srv:
-        ids = [None] * njobs
-        t0 = time.perf_counter()
-
-        def feeder():
-            for i, w in enumerate(jobs):
-                delay = arrivals[i] - (time.perf_counter() - t0)
-                if delay > 0:
-                    time.sleep(delay)
-                ids[i] = srv.submit(w.residues, w.offsets, w.alphabet, w.k, w.p, w.subst, w.gap_open,
-                                    w.gap_extend)
-
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        for j in ids:
-            assert srv.wait(j) == sad.SAD_OK, srv.error()
-        span_stream = time.perf_counter() - t0
-        st = srv.stats()
-        same = all(np.array_equal(srv.result(j, w.n)["scores"], o["scores"]) for j, w, o in zip(ids, jobs, outs))
-    line = {"mode": "serving", "metric": "jobs/s with p50/p99 latency (Poisson arrivals)", "value": st["jobs_per_s"],
-            "unit": "jobs/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-            "arrival_rate_jobs_per_s": rate, "offline_jobs_per_s": capacity,
-            "offline_gcups": total_cells / span / 1e9, "stream_gcups": total_cells / span_stream / 1e9,
-            "offline_p50_ms": st_off["p50_ms"], "offline_p99_ms": st_off["p99_ms"],
-            "jobs": njobs, "slots": args.slots, "results_identical_to_offline": bool(same),
-            "config": {"workload": "N ~ U{100..5000}, L ~ logN(300, 0.55) in [50, 1500], k=3, p=4, "
-                                   "gap -11/-1"}}
+    line = dict(serving_report(args.jobs, args.slots, args.seed), mode="serving")
     print(json.dumps(line))
     return 0
 
@@ -393,6 +467,10 @@ def main():
     ap.add_argument("--global-samples", type=int, default=0,
                     help="s > 0: partition by the globalized rank against s samples per block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reports outside the timed region (score forms, serving, MSA stages)")
+    ap.add_argument("--serving-jobs", type=int, default=40, help="jobs of the serving report in the bench line")
+    ap.add_argument("--probe-alu", action="store_true", help="print the integer-pipe probe table and exit")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
@@ -400,6 +478,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.serving:
         return run_serving(args) if rank == 0 else 0
+    if args.probe_alu:
+        return probe_table(args) if rank == 0 else 0
 
     import torch
     from paper_0901_2742_gb300 import build, sad, synth
@@ -487,6 +567,8 @@ def main():
     ops_per_cell = DPX_PER_CELL / 2 if packed else DPX_PER_CELL   # 16x2: one instruction, two cells
     achieved = ops_per_cell * cells / (sc_ms / args.steps * 1e-3) / 1e12
     peak = SMS * DPX_OPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    probe = alu_probe(sad)
+    mix_rows = probe["row_mix_rows_per_clk_sm"]
 
     # the k-mer all-pairs launch against the tensor-core peak (fp8: 2 x the measured bf16 burst),
     # counting the MMAs it issued (zero k-blocks of a panel are skipped)
@@ -503,10 +585,14 @@ def main():
                          "kernel": "k_plane_gemm2 (threshold-plane GEMM, tcgen05 kind::f8f6f4, fused D sums)",
                          "kernel_ms": ap_ms, "flops_per_launch": flops, "dense_flops_per_launch": dense_flops,
                          "kblocks_run_frac": flops / dense_flops if dense_flops else None,
-                         "peak_basis": ("2 x measured bf16 dense burst " + ("(MEASURED_PEAKS.json, of measured)"
-                                        if peaks else "(fallback 1.9 PFLOP/s, of fallback)")),
+                         "peak_basis": ("fp8 dense = 2 x the bf16 dense burst (the nominal fp8:bf16 ratio, "
+                                        "4.5:2.25 PFLOP/s); bf16 " + (f"{bf16:.1f} TFLOP/s measured, of measured"
+                                        if peaks else "1.9 PFLOP/s, of fallback") +
+                                        "; int8 MMA (kind::i8) does not assemble for sm_103a"),
                          "pairs_per_s": n * (n + 1) / 2 / (ap_ms * 1e-3)}
 
+    # the three forms of the score stage on this step's layout (outside the timed region)
+    forms = None if args.no_extras else score_forms(sad, w, res_d, offs_d, out_d, flush)
     # the per-bucket guide trees (the progressive aligner's first step) on this step's own device
     # outputs, outside the timed region; the tracer times the tree kernel on its stream
     sad.trace_enable(True)
@@ -570,6 +656,9 @@ def main():
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w)
+    serving = None
+    if ws == 1 and not args.no_extras and args.serving_jobs > 0:
+        serving = serving_report(args.serving_jobs, args.slots, args.seed)
     line = {
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -596,14 +685,18 @@ def main():
                      "kernel_ms": score_ms, "launches_per_step": score_launches_per_step,
                      "gcups": cells / (sc_ms / args.steps * 1e-3) / 1e9,
                      "peak_gcups": peak * 1e12 / ops_per_cell / 1e9,
-                     "mix_peak_gcups": (2 * MIX_ROWS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6 / 1e9) if packed else None,
+                     "mix_peak_gcups": (2 * mix_rows * SMS * SM_MAX_MHZ * 1e6 / 1e9) if packed else None,
                      "frac_of_mix_peak": ((cells / (sc_ms / args.steps * 1e-3)) /
-                                          (2 * MIX_ROWS_PER_CLK_SM * SMS * SM_MAX_MHZ * 1e6)) if packed else None,
-                     "peak_basis": f"{SMS} SMs x {DPX_OPS_PER_CLK_SM} DPX lanes/clk x {SM_MAX_MHZ:.0f} MHz; "
-                                   f"{ops_per_cell:g} DPX instructions per cell (the adds issue to the FMA pipe too)",
+                                          (2 * mix_rows * SMS * SM_MAX_MHZ * 1e6)) if packed else None,
+                     "peak_basis": f"{SMS} SMs x {DPX_OPS_PER_CLK_SM} integer lanes/clk (4 sub-partitions x 16) x "
+                                   f"{SM_MAX_MHZ:.0f} MHz; {ops_per_cell:g} DPX instructions per cell (the adds "
+                                   "issue to the FMA pipe too)",
+                     "probe": probe,
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the score launches "
-                                      "of one step (" + SCORE_TRAFFIC["profile"] + ")"},
+                                      "of one step, while the score kernels' device code is the one captured"},
         "kmer_roofline": kmer_roofline,
+        "score_forms": forms,
+        "serving": serving,
         "guide_trees": guide_trees,
         "progressive": progressive,
         "msa": msa,

@@ -220,6 +220,33 @@ uint64_t sad_launch_count(void);
  * result is the same. Synchronises the device; host outputs. */
 int sad_kmer_gemm_work(sad_ctx* ctx, int64_t* mma_flops, int64_t* dense_flops);
 
+/* ---- pipe probe ---------------------------------------------------------- */
+
+/* Instruction mixes of sad_probe_alu. */
+#define SAD_PROBE_VIADDMAX_S32 0   /* __viaddmax_s32 alone */
+#define SAD_PROBE_VIMAX3_S32 1     /* __vimax3_s32 alone */
+#define SAD_PROBE_VIADDMAX_S16X2 2 /* __viaddmax_s16x2 alone */
+#define SAD_PROBE_VIMAX3_S16X2 3   /* __vimax3_s16x2 alone */
+#define SAD_PROBE_IADD 4           /* plain 32-bit adds alone */
+#define SAD_PROBE_ROW_DPX3_ADD2 5  /* one packed DP row: 2 add-max, 1 3-way max, 2 adds */
+#define SAD_PROBE_ROW_DPX5 6       /* the same row with both adds as add-max against -inf */
+#define SAD_PROBE_ROW_DPX3 7       /* the row's 3 DPX instructions without the adds */
+#define SAD_PROBE_NUM_MIXES 8
+
+/* Register-only throughput of an integer instruction mix on the current
+ * device. This is not a step of the paper's method: it measures the rate that
+ * the alignment kernels' roofline is derived for (SMs x DPX lanes per clock x
+ * clock). One CTA per SM with warps_per_sm warps (1..32), each thread running
+ * 8 independent chains for iters x 16 steps; the SM-clock cycles of the median
+ * CTA give *lanes_per_clk_sm (instructions x 32 lanes per warp instruction,
+ * per clock per SM; for the row mixes the DPX instructions only) and, for the
+ * row mixes, *rows_per_clk_sm (DP rows of two 16-bit problems per clock per
+ * SM, else 0). Host outputs; synchronises the device; allocates two small
+ * device buffers for the call. Errors: SAD_EINVAL (unknown mix, warps or iters
+ * out of range, a NULL output), SAD_ENOMEM, SAD_ECUDA. */
+int sad_probe_alu(int32_t mix, int32_t warps_per_sm, int32_t iters, double* lanes_per_clk_sm,
+                  double* rows_per_clk_sm);
+
 /* ---- stage 1: k-mer rank ----------------------------------------------- */
 
 /* All-pairs k-mer similarity and the rank keys (Section 2 equations r_ij,
@@ -270,15 +297,22 @@ int sad_partition_keys64(sad_ctx* ctx, int32_t n, const uint64_t* keys, int32_t 
  * It allocates nothing: no device memory, no pinned or heap host memory, no
  * context. Its scratch is one fixed array in device memory of about 5 MiB,
  * which every GPU that loads the library holds until the process exits.
+ * The array belongs to the library's device code, and CUDA reserves it when it
+ * loads that code on a device: with lazy module loading (CUDA's default) that
+ * is the first call of this function on the device, or an earlier call of
+ * sad_partition or sad_partition_keys64, which share that code. A caller that
+ * may never allocate should therefore make one warm-up call at set-up; later
+ * calls leave the device's free memory unchanged.
  *   key_a, key_b [n], bucket_offsets [p+1], order [n], pivot_idx [p-1]
  *   (nullable): device pointers on the current device, same meaning as in
  *   sad_partition; n <= SAD_NOALLOC_MAX_N and 1 <= p <= SAD_NOALLOC_MAX_P,
  *   otherwise SAD_EINVAL before any device work.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture. Every call reuses the same array, and
- * each call clears the parts that must start at zero; two calls that overlap
- * on the GPU (other threads or streams at the same time) race and give wrong
- * results, so serialise them. The call synchronises `stream` to report bad
+ * The first call on a device looks up the array's device address (again after
+ * a device reset, which gives the device a new context and a new copy of the
+ * array); make that first call before any stream capture. Every call reuses
+ * the same array, and each call clears the parts that must start at zero; two
+ * calls that overlap on the GPU (other threads or streams at the same time)
+ * race and give wrong results, so serialise them. The call synchronises `stream` to report bad
  * keys (SAD_EINVAL), like sad_partition. */
 int sad_partition_noalloc(int32_t n, const int32_t* key_a, const int32_t* key_b, int32_t p,
                           int32_t* bucket_offsets, int32_t* order, int32_t* pivot_idx,
@@ -293,7 +327,11 @@ int sad_scores_size(const int32_t* bucket_offsets, int32_t p, int32_t mem, int64
 
 #define SAD_SCORES_PER_BUCKET 0  /* one kernel launch per bucket, 32-bit DP */
 #define SAD_SCORES_PERSISTENT 1  /* one persistent launch over a length-binned
-                                    queue of every bucket, CUDA-graph replayed */
+                                    queue of every bucket, CUDA-graph replayed;
+                                    two problems per 16x2 lane when a bias fits */
+#define SAD_SCORES_PERSISTENT_32 2 /* the batched form in 32-bit DP: one
+                                      persistent launch over every bucket's
+                                      query rows, longest first */
 
 /* Global alignment score with affine gaps for every pair u <= v inside every
  * bucket (the diagonal is the self-score). A gap run of length g scores
@@ -403,6 +441,17 @@ int sad_progressive_align(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* b
  * SM or a profile of 1024 columns or more). Results do not depend on it.
  * Errors: SAD_EINVAL for other values. */
 int sad_progressive_columns(sad_ctx* ctx, int32_t columns);
+
+/* Bound of the one device-side wait of the profile DP (sad_progressive_align,
+ * sad_ancestor_glue): a warp that aligns a strip of rows waits for the strip
+ * above to finish each column it needs, polling every 32 ns at most `polls`
+ * times. A wait that runs out sets the context's status, the kernel goes on
+ * with whatever the boundary holds (every access stays in bounds) and the call
+ * returns SAD_ETIMEOUT; the context stays usable. polls = 0 restores the
+ * default bound (2^22 polls, about 0.15 s of waiting per column); a small bound
+ * makes a multi-strip merge give up, which is how the timeout path is tested.
+ * Errors: SAD_EINVAL for polls < 0. */
+int sad_progressive_wait_limit(sad_ctx* ctx, int64_t polls);
 
 /* Realignment against the global ancestor and the glue, the last steps of
  * Algorithm Sample-Align-D (Section 2.3.3): the alignment of every bucket

@@ -1309,8 +1309,8 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
     std::vector<int64_t> score_off;
     plan_buckets(h_bo, h_order, S.h_len, p, &srt, &score_off);
     *total_out = score_off[p];
-    SAD_CHECK(mode == SAD_SCORES_PER_BUCKET || mode == SAD_SCORES_PERSISTENT, SAD_EINVAL,
-              "unknown scores mode %d", mode);
+    SAD_CHECK(mode == SAD_SCORES_PER_BUCKET || mode == SAD_SCORES_PERSISTENT || mode == SAD_SCORES_PERSISTENT_32,
+              SAD_EINVAL, "unknown scores mode %d", mode);
     // work items: the packed plan, or one item per query row (longest first for
     // the persistent 32-bit kernel)
     int32_t bias = 0;
@@ -1328,7 +1328,7 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
                 max_m = std::max(max_m, S.h_len[h_order[lo + srt[lo + q]]]);
             }
         }
-        if (mode == SAD_SCORES_PERSISTENT) {
+        if (mode != SAD_SCORES_PER_BUCKET) {
             std::vector<int64_t> cost(items.size());
             std::vector<int32_t> idx(items.size());
             for (size_t t = 0; t < items.size(); t++) {

@@ -10,6 +10,7 @@
 // Integer rank keys G_i (the globalized rank sums, up to about 2^52) are packed
 // as the 128-bit integer G_i << 32 | i; the kernels are templated on the key
 // type and the two forms share every step.
+#include <cuda.h>
 #include <cstring>
 
 #include "partition_stage.cuh"
@@ -366,6 +367,7 @@ constexpr size_t kNaBytes = kNaStatus + 256;
 
 std::mutex g_na_mu;
 void* g_na_ptr[64] = {nullptr};
+unsigned long long g_na_ctx[64] = {0};  // id of the CUDA context the cached address belongs to
 
 }  // namespace
 
@@ -374,15 +376,44 @@ static __device__ __align__(256) unsigned char g_partition_scratch[kNaBytes];
 
 namespace {
 
+// Unique id of the CUDA context current on this thread (driver entry points,
+// so that no driver library has to be linked); false when there is none or the
+// driver does not offer the calls.
+using PFN_ctx_current = CUresult (*)(CUcontext*);
+using PFN_ctx_id = CUresult (*)(CUcontext, unsigned long long*);
+bool current_ctx_id(unsigned long long* id) {
+    static PFN_ctx_current get_current = nullptr;
+    static PFN_ctx_id get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (PFN_ctx_current)f;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_ctx_id)f;
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
+
 // Device address of the scratch array on the current device. The host-side
 // name of a __device__ array is only a stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// with that device current, once per device, and cached together with the id
+// of the context it belongs to: after a device reset the runtime makes a new
+// context (and a new copy of the array), and the address is looked up again.
 int noalloc_scratch(void** out) {
     int dev = 0;
     SAD_CUDA(cudaGetDevice(&dev));
     SAD_CHECK(dev >= 0 && dev < 64, SAD_EINVAL, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    unsigned long long id = 0;
+    bool known = current_ctx_id(&id);
+    if (!g_na_ptr[dev] || !known || id != g_na_ctx[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_partition_scratch);
         if (e != cudaSuccess || p == nullptr) {
@@ -390,7 +421,9 @@ int noalloc_scratch(void** out) {
             set_error("cudaGetSymbolAddress of the partition scratch failed: %s", cudaGetErrorString(e));
             return SAD_ECUDA;
         }
+        known = current_ctx_id(&id);  // the lookup made the context current if none was
         g_na_ptr[dev] = p;
+        g_na_ctx[dev] = known ? id : 0;
     }
     *out = g_na_ptr[dev];
     return SAD_OK;

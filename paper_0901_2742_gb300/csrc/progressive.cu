@@ -89,6 +89,7 @@ struct ProgArgs {
     long long* scores;       // per merge
     int32_t* widths;         // per merge
     uint32_t* status;
+    int64_t spin_limit;      // bound of the strip hand-off wait (polls of 32 ns)
     int32_t maxw;            // widest profile of the batch
     int32_t warp_smem;       // dynamic shared bytes of one DP CTA
 };
@@ -345,8 +346,8 @@ k_prof_dp(ProgArgs a) {
                             } else {
                                 if (avail < tau + 1) {  // wait (bounded) for the strip above
                                     int64_t spins = 0;
-                                    while ((avail = prog[s - 1]) < tau + 1 && ++spins < kSpinLimit) __nanosleep(32);
-                                    if (spins >= kSpinLimit) {
+                                    while ((avail = prog[s - 1]) < tau + 1 && ++spins < a.spin_limit) __nanosleep(32);
+                                    if (spins >= a.spin_limit) {
                                         atomicOr(a.status, STATUS_TIMEOUT);
                                         avail = n;
                                     }
@@ -454,8 +455,8 @@ k_prof_dp(ProgArgs a) {
                             } else {
                                 if (avail < lj1) {  // wait (bounded) for the strip above
                                     int64_t spins = 0;
-                                    while ((avail = prog[s - 1]) < lj1 && ++spins < kSpinLimit) __nanosleep(32);
-                                    if (spins >= kSpinLimit) {
+                                    while ((avail = prog[s - 1]) < lj1 && ++spins < a.spin_limit) __nanosleep(32);
+                                    if (spins >= a.spin_limit) {
                                         atomicOr(a.status, STATUS_TIMEOUT);
                                         avail = n;
                                     }
@@ -1206,6 +1207,7 @@ extern "C" int sad_progressive_align(sad_ctx* ctx_in, const sad_seqset* seqs, co
     base.scores = d_sc;
     base.widths = d_mw;
     base.status = ctx->d_status;
+    base.spin_limit = ctx->prog_spin_limit > 0 ? ctx->prog_spin_limit : kSpinLimit;
     for (int32_t lv = 1; lv <= max_level; lv++) {
         const std::vector<int32_t>& ms = by_level[lv];
         // columns per DP lane step: two when the level holds enough merges to fill the GPU or
@@ -1445,6 +1447,7 @@ extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const 
     base.scores = d_sc;
     base.widths = (int32_t*)(w + o_mw);
     base.status = ctx->d_status;
+    base.spin_limit = ctx->prog_spin_limit > 0 ? ctx->prog_spin_limit : kSpinLimit;
     const int64_t budget = (int64_t)1 << 30;
     int64_t glue_jobs = 0;
     for (int32_t b = 0; b < p; b++) glue_jobs += bo[b + 1] > bo[b] ? 1 : 0;
@@ -1518,6 +1521,17 @@ extern "C" int sad_ancestor_glue(sad_ctx* ctx_in, const sad_seqset* seqs, const 
         if (T_res > 0) SAD_CUDA(cudaMemcpyAsync(global_colmap, d_gcm, 4ull * T_res, cudaMemcpyDeviceToHost, stream));
     }
     SAD_RET(status_check(ctx, stream));
+    return SAD_OK;
+}
+
+extern "C" int sad_progressive_wait_limit(sad_ctx* ctx_in, int64_t polls) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(polls >= 0, SAD_EINVAL, "polls = %lld < 0", (long long)polls);
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->prog_spin_limit = polls;
     return SAD_OK;
 }
 

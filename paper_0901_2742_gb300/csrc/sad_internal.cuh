@@ -150,6 +150,7 @@ struct sad_ctx {
     int64_t gemm_dense_units = 0;             // k-blocks x BN of all its tiles
     std::vector<sad::Buffer> prog_chunks;     // progressive alignment: profile and column-map arena
     int32_t prog_columns = 0;                 // progressive DP columns per lane step: 0 chosen per batch, 1, 2
+    int64_t prog_spin_limit = 0;              // progressive strip hand-off wait bound in polls: 0 = the default
 };
 
 namespace sad {

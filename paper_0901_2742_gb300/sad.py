@@ -30,7 +30,7 @@ from . import build as _build
 SAD_OK, SAD_EINVAL, SAD_ENOMEM, SAD_ECUDA, SAD_ETIMEOUT = 0, -1, -2, -3, -4
 SAD_EBUSY, SAD_ERANGE, SAD_ENOTFOUND, SAD_ECANCELED = -5, -6, -7, -8
 MEM_HOST, MEM_DEVICE = 0, 1
-PER_BUCKET, PERSISTENT = 0, 1
+PER_BUCKET, PERSISTENT, PERSISTENT_32 = 0, 1, 2
 
 _NAMES = {SAD_EINVAL: "EINVAL", SAD_ENOMEM: "ENOMEM", SAD_ECUDA: "ECUDA", SAD_ETIMEOUT: "ETIMEOUT",
           SAD_EBUSY: "EBUSY", SAD_ERANGE: "ERANGE", SAD_ENOTFOUND: "ENOTFOUND",
@@ -98,10 +98,13 @@ def load():
         "sad_trace_enable": (ctypes.c_int, [P, i32]),
         "sad_trace_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), i32]),
         "sad_kmer_gemm_work": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "sad_probe_alu": (ctypes.c_int, [i32, i32, i32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]),
         "sad_guide_trees": (ctypes.c_int, [P, P, i32, P, P, P, P, P, P, P, i32, P]),
         "sad_progressive_align": (ctypes.c_int, [P, P, P, P, i32, P, P, P, P, i32, i32, P, P, P, P, i32, P]),
         "sad_ancestor_glue": (ctypes.c_int, [P, P, P, P, i32, P, P, i32, P, i32, i32, P, P, P, P, i32, P]),
         "sad_progressive_columns": (ctypes.c_int, [P, i32]),
+        "sad_progressive_wait_limit": (ctypes.c_int, [P, i64]),
         "sad_trace_timeline": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(ctypes.c_int32)]),
         "sad_launch_count": (ctypes.c_uint64, []),
@@ -265,6 +268,18 @@ def kmer_gemm_work(ctx=None) -> tuple:
     a, b = ctypes.c_int64(0), ctypes.c_int64(0)
     _check(load().sad_kmer_gemm_work(_ctx(ctx), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+PROBE_MIXES = {"viaddmax_s32": 0, "vimax3_s32": 1, "viaddmax_s16x2": 2, "vimax3_s16x2": 3, "iadd": 4,
+               "row_dpx3_add2": 5, "row_dpx5": 6, "row_dpx3": 7}
+
+
+def probe_alu(mix: str, warps_per_sm: int = 16, iters: int = 4096) -> tuple:
+    """sad_probe_alu on the current device: (lanes per clock per SM, rows per
+    clock per SM) of one register-only instruction mix (PROBE_MIXES)."""
+    lanes, rows = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().sad_probe_alu(PROBE_MIXES[mix], warps_per_sm, iters, ctypes.byref(lanes), ctypes.byref(rows)))
+    return lanes.value, rows.value
 
 
 def set_score_variants(table, ctx=None):
@@ -457,6 +472,12 @@ def progressive_align(residues, offsets, alphabet: int, bucket_offsets, order, m
 def progressive_columns(columns: int, ctx=None):
     """sad_progressive_columns: force 1 or 2 columns per profile-DP lane step, 0 = per batch."""
     _check(load().sad_progressive_columns(_ctx(ctx), int(columns)))
+
+
+def progressive_wait_limit(polls: int, ctx=None):
+    """sad_progressive_wait_limit: bound of the profile DP's strip hand-off wait
+    (polls of 32 ns); 0 restores the default."""
+    _check(load().sad_progressive_wait_limit(_ctx(ctx), int(polls)))
 
 
 def ancestor_glue(residues, offsets, alphabet: int, bucket_offsets, order, widths, colmap, ga: int, subst,

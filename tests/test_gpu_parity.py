@@ -69,7 +69,7 @@ def run_gpu(sad, w, mode, device=False):
 
 
 @pytest.mark.parametrize("device", [False, True], ids=["host", "device"])
-@pytest.mark.parametrize("mode", [0, 1], ids=["per_bucket", "persistent"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["per_bucket", "persistent", "persistent_32"])
 def test_small_family_full_parity(sad, device, mode):
     w = synth.workload(1)
     want = oracle_all(w, "cfg1")
@@ -92,7 +92,7 @@ def test_small_family_seed_sweep(sad, seed):
     np.testing.assert_array_equal(sc, want[3])
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["per_bucket", "persistent"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["per_bucket", "persistent", "persistent_32"])
 def test_paper_scale_plain_full_parity(sad, mode):
     """N = 2000, L ~ N(316, 60), k = 3, p = 16: every output of every stage."""
     w = synth.workload(2)
@@ -202,7 +202,7 @@ def test_gotoh_random_buckets_and_gap_costs(sad, params):
     bo = np.array([0, 1, 1, 12, 30, n], np.int32)   # includes an empty and a singleton bucket
     S = synth.subst_matrix(5)
     want_so, want_sc = oracle.bucket_pair_scores(res, offs, bo, order, S, go, ge)
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         so, sc = sad.bucket_pair_scores(res, offs, 20, bo, order, S, go, ge, mode=mode)
         np.testing.assert_array_equal(so, want_so)
         np.testing.assert_array_equal(sc, want_sc)
@@ -295,6 +295,26 @@ def test_planes_skip_only_zero_kblocks(sad):
     assert_rank_equal(got, want)
     mma, dense = sad.kmer_gemm_work()
     assert 0 < mma < dense
+
+
+def test_planes_long_sequences_large_plane_sums(sad):
+    """Plane sums far above 2^14 in the fp32 tensor-memory accumulator: random
+    sequences of 40k-65k residues hold nearly every 3-mer of 20 letters 4 or
+    more times, so sum_tau min(c_i, c_j, 4) approaches 4 x 8000 = 32000 (the
+    accumulator stays exact below 2^24); short-period repeats and a homopolymer
+    tail add counts above the cap and above 255 (the residual and the excess
+    lists), and one short sequence gives small ratios beside them. k-mer stage
+    only (the rank outputs and every numerator), against the oracle."""
+    rng = np.random.default_rng(99)
+    seqs = [list(rng.integers(0, 20, L)) for L in (65537, 60000, 52000, 45000, 40000)]
+    seqs.append(list(np.tile(rng.integers(0, 20, 7), 8000)[:56000]))         # period 7: 7 k-mers, ~8000 each
+    seqs.append(list(rng.integers(0, 20, 30000)) + [0] * 20000)              # homopolymer tail
+    seqs.append(list(rng.integers(0, 20, 300)))
+    res, offs = synth.pack(seqs)
+    want = oracle.kmer_rank(res, offs, 20, 3, 3, want_A=True)
+    assert int(np.max(want["A"])) > 2 ** 14
+    got = sad.kmer_rank(res, offs, 20, 3, 3, cap=4, want_A=True)
+    assert_rank_equal(got, want)
 
 
 def test_planes_compressed_alphabet(sad):

@@ -115,6 +115,32 @@ def test_several_strips_and_ragged_tails(sad, mem, columns):
     assert_same(got, want)
 
 
+def test_strip_wait_that_runs_out_reports_a_timeout_and_the_context_recovers(sad):
+    """The strip hand-off wait of the profile DP is the kernel's one device-side
+    wait. With a bound of one poll, every strip that has to wait for the strip
+    above gives up: the call must return SAD_ETIMEOUT (not hang, not fault, not
+    report success), and the same context must then give the exact result once
+    the default bound is back."""
+    rng = random.Random(5)
+    S = random_symmetric(rng, 20, -4, 11)
+    buckets = [[[rng.randrange(20) for _ in range(600)] for _ in range(2)] for _ in range(3)]
+    args = layout(rng, buckets, lambda nb: random_tree(rng, nb))
+    sad.progressive_wait_limit(1)
+    try:
+        with pytest.raises(sad.SadError) as e:
+            sad.progressive_align(*args[:2], 20, *args[2:], S, -11, -1)
+        assert e.value.code == sad.SAD_ETIMEOUT, e.value
+    finally:
+        sad.progressive_wait_limit(0)
+    got, want = run_both(sad, 20, args, S, -11, -1)
+    assert_same(got, want)
+
+
+def test_wait_limit_setting_is_checked(sad):
+    with pytest.raises(sad.SadError):
+        sad.progressive_wait_limit(-1)
+
+
 def balanced_tree(nb):
     """Pairs neighbours level by level: the last merges join clusters of about nb/2 members."""
     live, left, right, k = list(range(nb)), [], [], 0
