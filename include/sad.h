@@ -192,7 +192,8 @@ const char* sad_version(void);
 #define SAD_STAGE_ALIGN 8      /* alignments with traceback (sad_align_pairs) */
 #define SAD_STAGE_TREE 9       /* guide trees (sad_guide_trees) */
 #define SAD_STAGE_PROG 10      /* progressive alignment (sad_progressive_align) */
-#define SAD_NUM_STAGES 11
+#define SAD_STAGE_PLANE_GEMM 11 /* the threshold-plane GEMM launch alone (inside SAD_STAGE_ALLPAIRS) */
+#define SAD_NUM_STAGES 12
 
 /* Turn event tracing of `ctx` on (1) or off (0); turning it on clears the
  * accumulated times. */

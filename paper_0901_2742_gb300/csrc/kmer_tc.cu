@@ -555,18 +555,29 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
         for (int32_t tj = 0; tj < ntj; tj++)
             for (int32_t ti = ib; ti < std::min(nti, ib + 8); ti++)
                 if ((int64_t)BN * tj + BN - 1 >= (int64_t)kTM * ti) tiles.push_back(make_int2(ti, tj));
-    // tile list, then (256-byte aligned) the work counter of this launch
+    // tile list, then (256-byte aligned) the work counter of this launch. The list
+    // depends on n and the tile shape only: it stays on the device between calls
+    // and is uploaded (with one synchronisation) only when it changes.
     const size_t work_off = (size_t)round_up((int64_t)(sizeof(int2) * tiles.size()), 256);
     void* dt = nullptr;
     SAD_RET(workspace(ctx, WS_GEMM_TILES, work_off + 16, stream, &dt));
     unsigned long long* work = (unsigned long long*)((char*)dt + work_off);
     SAD_CUDA(cudaMemsetAsync(work, 0, sizeof(unsigned long long), stream));
     ctx->gemm_work = work;
-    void* pin = nullptr;
-    SAD_RET(pinned(ctx, sizeof(int2) * tiles.size(), stream, &pin));
-    SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may feed an earlier copy
-    memcpy(pin, tiles.data(), sizeof(int2) * tiles.size());
-    SAD_CUDA(cudaMemcpyAsync(dt, pin, sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, stream));
+    const bool same = ctx->gemm_tiles_dev == dt && ctx->gemm_tiles_n == n && ctx->gemm_tiles_bn == BN &&
+                      ctx->gemm_tiles_count == (int64_t)tiles.size();
+    if (!same) {
+        void* pin = nullptr;
+        SAD_RET(pinned(ctx, sizeof(int2) * tiles.size(), stream, &pin));
+        SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area may feed an earlier copy
+        memcpy(pin, tiles.data(), sizeof(int2) * tiles.size());
+        SAD_CUDA(cudaMemcpyAsync(dt, pin, sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, stream));
+        SAD_CUDA(cudaStreamSynchronize(stream));  // the pinned area is free again for later copies
+        ctx->gemm_tiles_dev = dt;
+        ctx->gemm_tiles_n = n;
+        ctx->gemm_tiles_bn = BN;
+        ctx->gemm_tiles_count = (int64_t)tiles.size();
+    }
     CUtensorMap tmA, tmB;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n};
     const cuuint64_t strides[1] = {(cuuint64_t)K};
@@ -585,6 +596,7 @@ int allpairs_planes(sad_ctx* ctx, int32_t n, int32_t K, const uint8_t* planes, c
     const int32_t ntiles = (int32_t)tiles.size();
     ctx->gemm_dense_units = (int64_t)ntiles * kblocks * BN;  // k-blocks x BN of every tile
     const int grid = std::min<int32_t>(ntiles, ctx->num_sms);
+    TraceScope ts(ctx, SAD_STAGE_PLANE_GEMM, stream);
     if (BN == 256) {
         const size_t smem = (size_t)kStagesFor<256>() * (kTM + 256) * kKB + 1024;
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_plane_gemm2<256>));

@@ -148,6 +148,9 @@ struct sad_ctx {
     std::vector<cudaEvent_t> event_pool;
     unsigned long long* gemm_work = nullptr;  // device: k-blocks x BN the last plane GEMM ran
     int64_t gemm_dense_units = 0;             // k-blocks x BN of all its tiles
+    void* gemm_tiles_dev = nullptr;           // tile list on the device, for (n, BN, count) below
+    int32_t gemm_tiles_n = -1, gemm_tiles_bn = 0;
+    int64_t gemm_tiles_count = 0;
     std::vector<sad::Buffer> prog_chunks;     // progressive alignment: profile and column-map arena
     int32_t prog_columns = 0;                 // progressive DP columns per lane step: 0 chosen per batch, 1, 2
     int64_t prog_spin_limit = 0;              // progressive strip hand-off wait bound in polls: 0 = the default

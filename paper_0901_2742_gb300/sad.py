@@ -214,7 +214,8 @@ def _ctx(ctx):
 
 
 STAGES = ("prepare", "count", "allpairs", "rank", "partition", "scores", "scores_packed", "global", "align",
-          "tree", "prog")
+          "tree", "prog", "plane_gemm")
+NESTED_STAGES = ("plane_gemm",)  # intervals that lie inside another stage's interval
 
 
 def trace_enable(on: bool = True, ctx=None):
