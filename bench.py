@@ -327,6 +327,76 @@ def serving_report(jobs_n=200, slots=4, seed=5005):
                                    "gap -11/-1"}}
 
 
+def kmer_large_report(sad, peak_fp8, reps=5):
+    """The threshold-plane GEMM on the large uneven workload (N = 20000, k = 4
+    over the 6-letter classes, cap 4, K = 4 x 1344 bytes per sequence): the
+    k-mer stage alone (sad_kmer_rank, device arrays), the GEMM launch timed by
+    its own trace interval, against the same fp8 peak as the main line."""
+    import torch
+    from paper_0901_2742_gb300 import synth
+    w = synth.workload(4)
+    res = torch.from_numpy(w.residues).cuda()
+    offs = torch.from_numpy(w.offsets).cuda()
+    kw = dict(cap=4, kmer_alphabet=w.kmer_alphabet, class_map=w.class_map)
+    sad.kmer_rank(res, offs, w.alphabet, w.k, w.p, **kw)
+    torch.cuda.synchronize()
+    sad.trace_enable(True)
+    for _ in range(reps):
+        sad.kmer_rank(res, offs, w.alphabet, w.k, w.p, **kw)
+    torch.cuda.synchronize()
+    t = sad.trace_read()
+    sad.trace_enable(False)
+    flops, dense = sad.kmer_gemm_work()
+    ms = t["plane_gemm"][0] / max(t["plane_gemm"][1], 1)
+    ach = flops / (ms * 1e-3) / 1e12
+    stage = (t["count"][0] + t["allpairs"][0] + t["rank"][0]) / reps
+    return {"workload": w.name, "kernel_ms": ms, "flops_per_launch": flops, "achieved": ach, "peak": peak_fp8,
+            "frac": ach / peak_fp8, "unit": "TFLOP/s (fp8 e4m3)", "kmer_stage_ms": stage,
+            "pairs_per_s": w.n * (w.n + 1) / 2 / (stage * 1e-3)}
+
+
+def alignment_report(sad, w, res_d, offs_d, out_d, reps=2):
+    """Every pair u <= v of every bucket of the step aligned (columns, not only
+    scores) in linear space (sad_align_pairs_linear) and with every cell's
+    direction bits kept (sad_align_pairs), on the same pairs: time per call
+    (CUDA events on the stream around the call's kernel, from the tracer),
+    GCUPS over the pairs' cells, and the device memory each form needs."""
+    import torch
+    pairs = sad.bucket_pairs(out_d["bucket_offsets"], out_d["order"][:w.n])
+    L = np.diff(w.offsets).astype(np.int64)
+    cells = int((L[pairs[:, 0]] * L[pairs[:, 1]]).sum())
+    pairs_d = torch.from_numpy(pairs).to(res_d.device)
+    rep = {"pairs": int(len(pairs)), "cells": cells}
+    scores = {}
+    for name, linear in (("linear", True), ("quadratic", False)):
+        out = sad.align_pairs(res_d, offs_d, w.alphabet, pairs_d, w.subst, w.gap_open, w.gap_extend, linear=linear)
+        torch.cuda.synchronize()
+        sad.trace_enable(True)
+        for _ in range(reps):
+            out = sad.align_pairs(res_d, offs_d, w.alphabet, pairs_d, w.subst, w.gap_open, w.gap_extend,
+                                  linear=linear)
+        torch.cuda.synchronize()
+        t = sad.trace_read()["align"]
+        sad.trace_enable(False)
+        ms = t[0] / reps
+        scores[name] = out["scores"].cpu().numpy()
+        rep[name] = {"ms": ms, "gcups": cells / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                     "launches_per_call": t[1] / reps}
+    mx = int(L.max())
+    rep["linear"]["kernel"] = "k_align_linear (rows split at the middle down to 256-row blocks)"
+    rep["linear"]["device_bytes_per_warp"] = sad.align_linear_bytes_per_warp(mx)
+    rep["linear"]["bytes_per_residue"] = (sad.align_linear_bytes_per_warp(mx + 1000) -
+                                          sad.align_linear_bytes_per_warp(mx)) / 1000
+    # direction words of the quadratic form: 4 bits per cell of every 256-row strip
+    m, n = L[pairs[:, 0]], L[pairs[:, 1]]
+    words = ((m + 255) // 256) * (n + 31) * 32 * ((m > 0) & (n > 0))
+    rep["quadratic"]["kernel"] = "k_gotoh_trace (direction bits of every cell, batches within 1 GiB)"
+    rep["quadratic"]["direction_bytes_all_pairs"] = int(4 * words.sum())
+    rep["quadratic"]["direction_bytes_largest_pair"] = int(4 * words.max())
+    rep["scores_equal"] = bool(np.array_equal(scores["linear"], scores["quadratic"]))
+    return rep
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -593,6 +663,8 @@ def main():
                                         if peaks else "1.9 PFLOP/s, of fallback") +
                                         "; int8 MMA (kind::i8) does not assemble for sm_103a"),
                          "pairs_per_s": n * (n + 1) / 2 / (ap_ms * 1e-3)}
+        if not args.no_extras and args.workload == 2:
+            kmer_roofline["large_batch"] = kmer_large_report(sad, peak_fp8)
 
     # the three forms of the score stage on this step's layout (outside the timed region)
     forms = None if args.no_extras else score_forms(sad, w, res_d, offs_d, out_d, flush)
@@ -611,6 +683,7 @@ def main():
                    "largest_bucket": int(sizes.max()), "merges": int(tr["left"].shape[0])}
     # then the progressive alignment of every bucket along its tree (also outside the timed region)
     progressive = progressive_report(sad, w, res_d, offs_d, out_d, tr, bo, od)
+    alignments = None if args.no_extras else alignment_report(sad, w, res_d, offs_d, out_d)
     msa = msa_report(sad, w, res_d, offs_d, kw)
 
     # end to end through the C ABI with pinned host buffers
@@ -702,6 +775,7 @@ def main():
         "serving": serving,
         "guide_trees": guide_trees,
         "progressive": progressive,
+        "alignments": alignments,
         "msa": msa,
         "gpu_launches": int(launches),
         "wall_s": wall,

@@ -496,13 +496,39 @@ int sad_ancestor_glue(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucke
  * ops_offsets[npairs+1] (filled: pair k owns ops[ops_offsets[k] ..
  * ops_offsets[k] + |x| + |y|)), ops[ops_capacity] (pair k's columns, first
  * column first, SAD_COL_* bytes, at the start of its slot), ops_len[npairs]
- * (columns of pair k). Errors: SAD_EINVAL (a pair id outside 0..n-1, gap
- * costs > 0 or below -1000, a residue >= alphabet), SAD_ERANGE (ops_capacity
- * below sum |x| + |y|; ops_offsets is filled), SAD_ENOMEM, SAD_ECUDA. */
+ * (columns of pair k). The direction bits of every cell are kept: 4 bits per
+ * cell, |x| |y| / 2 bytes per pair, pairs in batches whose bits fit 1 GiB
+ * (sad_align_pairs_linear needs memory linear in the lengths). Errors:
+ * SAD_EINVAL (a pair id outside 0..n-1, gap costs > 0 or below -1000, a
+ * residue >= alphabet), SAD_ERANGE (ops_capacity below sum |x| + |y|;
+ * ops_offsets is filled), SAD_ENOMEM, SAD_ECUDA. */
 int sad_align_pairs(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* pairs, int32_t npairs,
                     const int8_t* subst, int32_t gap_open, int32_t gap_extend, int32_t* scores,
                     int64_t* ops_offsets, uint8_t* ops, int64_t ops_capacity, int32_t* ops_len,
                     int32_t mem, void* stream);
+/* The same alignments in linear space: memory per pair grows with the
+ * length of the sequences, not with their product. Rows are split at the
+ * middle (Hirschberg's divide and conquer with Myers and Miller's affine-gap
+ * bookkeeping: the best crossing of the middle row is taken from a forward
+ * pass over the top half and a pass over the reversed bottom half, with a
+ * vertical gap allowed to span the cut at one opening), down to blocks of at
+ * most 256 rows, which are solved with their direction bits. The shorter
+ * sequence of a pair is taken as the rows. Arguments, outputs and errors as
+ * sad_align_pairs; any optimal alignment may be returned (the two calls may
+ * return different ones of the same score). The device scratch is
+ * sad_align_linear_bytes_per_warp(L) bytes for each of up to 16 warps per SM,
+ * L the longest sequence of the pairs; a pass sums two 32-bit DP values, so
+ * (max|subst| + |gap_open| + |gap_extend|) x 2 x (L + 1) must stay below 2^28
+ * (SAD_EINVAL otherwise). */
+int sad_align_pairs_linear(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* pairs, int32_t npairs,
+                           const int8_t* subst, int32_t gap_open, int32_t gap_extend, int32_t* scores,
+                           int64_t* ops_offsets, uint8_t* ops, int64_t ops_capacity, int32_t* ops_len,
+                           int32_t mem, void* stream);
+/* Device bytes one warp of sad_align_pairs_linear uses for pairs whose longer
+ * sequence has max_len residues: 6 x (max_len + 2) int32 (the middle-row
+ * vectors and a strip boundary) and (max_len + 34) x 32 direction words; -1
+ * for max_len < 0. */
+int64_t sad_align_linear_bytes_per_warp(int32_t max_len);
 
 /* ---- both stages ------------------------------------------------------- */
 

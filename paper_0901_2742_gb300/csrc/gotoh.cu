@@ -1584,25 +1584,34 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
     table.filter = false;
     // Joint refinement: the bins' variants run side by side on forked streams, so
     // the fastest variant of a bin alone need not be the fastest with the others
-    // running. One pass of coordinate descent over the bins, every variant of a
-    // bin (its four fastest alone when the stage is long) timed as the whole stage
-    // over at least five runs; a change must gain 1 %, and 1.5 % again when measured
-    // beside the current table, and the result must beat the per-bin table.
-    const int32_t jreps = std::max(reps, 5);
+    // running (the per-bin table can be 20 % off the best table of the whole
+    // stage). Coordinate descent over the bins, largest share of the cells first,
+    // every variant that ran in a bin (the four fastest alone when the stage is
+    // long) timed as the whole stage: the median of at least seven runs, each
+    // after an L2 clear. A change is kept when it gains 0.5 % and again 0.5 %
+    // measured beside the current table; two passes, then the result must beat
+    // the per-bin table in an A, B, A, B comparison of medians.
+    const int32_t jreps = std::max(reps, 7);
     auto stage_ms = [&](const ScoreTuning& t, double* out) -> int {
         ctx->tuning = t;
-        trace_reset(ctx, true);
+        std::vector<double> runs;
         for (int32_t r = 0; r <= jreps; r++) {
-            if (r == 1) trace_reset(ctx, true);  // the first run warms up
+            trace_reset(ctx, true);
             int64_t tot = 0;
             SAD_CUDA(cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream));
             SAD_RET(bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend, SAD_SCORES_PERSISTENT,
                                          nullptr, (int32_t*)sw, total, &tot, stream));
+            double ms[SAD_NUM_STAGES];
+            int32_t cnt[SAD_NUM_STAGES];
+            SAD_RET(trace_collect(ctx, ms, cnt, SAD_NUM_STAGES));
+            if (r > 0 && cnt[SAD_STAGE_SCORES_PACKED] > 0) runs.push_back(ms[SAD_STAGE_SCORES_PACKED]);  // run 0 warms up
         }
-        double ms[SAD_NUM_STAGES];
-        int32_t cnt[SAD_NUM_STAGES];
-        SAD_RET(trace_collect(ctx, ms, cnt, SAD_NUM_STAGES));
-        *out = cnt[SAD_STAGE_SCORES_PACKED] > 0 ? ms[SAD_STAGE_SCORES_PACKED] / jreps : 1e300;
+        if (runs.empty()) {
+            *out = 1e300;
+            return SAD_OK;
+        }
+        std::sort(runs.begin(), runs.end());
+        *out = runs[runs.size() / 2];
         return SAD_OK;
     };
     if (rc == SAD_OK && table.nbins > 1) {
@@ -1612,13 +1621,26 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
             while (b < nm && merged[b] != table.upper[e]) b++;
             bin_of[e] = b < nm ? b : -1;
         }
+        // table entries by their bins' cells, largest first
+        std::vector<double> mcells((size_t)nm, 0.0);
+        for (int32_t b = 0, m = 0; b < nbins && m < nm; b++) {
+            mcells[m] += bin_cells[b];
+            if (bin_upper[b] == merged[m]) m++;
+        }
+        std::vector<int32_t> visit;
+        for (int32_t e = 0; e < table.nbins; e++)
+            if (bin_of[e] >= 0) visit.push_back(e);
+        std::stable_sort(visit.begin(), visit.end(),
+                         [&](int32_t x, int32_t y) { return mcells[bin_of[x]] > mcells[bin_of[y]]; });
         double best = 0;
         rc = stage_ms(table, &best);
-        const size_t max_cands = best > 20.0 ? 4 : 64;
-        for (int pass = 0; pass < 1 && rc == SAD_OK; pass++) {
+        const bool long_stage = best > 20.0;
+        const size_t max_cands = long_stage ? 4 : 64;
+        const int passes = long_stage ? 1 : 2;
+        for (int pass = 0; pass < passes && rc == SAD_OK; pass++) {
             bool improved = false;
-            for (int32_t e = 0; e < table.nbins && rc == SAD_OK; e++) {
-                if (bin_of[e] < 0) continue;
+            for (int32_t e : visit) {
+                if (rc != SAD_OK) break;
                 auto cands = ranked[bin_of[e]];
                 std::sort(cands.begin(), cands.end());
                 for (size_t c = 0; c < cands.size() && c < max_cands && rc == SAD_OK; c++) {
@@ -1629,12 +1651,12 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
                     cand.G[e] = G;
                     double t = 0;
                     rc = stage_ms(cand, &t);
-                    if (rc == SAD_OK && t < 0.99 * best) {
+                    if (rc == SAD_OK && t < 0.995 * best) {
                         // confirm against the current table, measured again beside it
                         double now = 0, again = 0;
                         rc = stage_ms(table, &now);
                         if (rc == SAD_OK) rc = stage_ms(cand, &again);
-                        if (rc == SAD_OK && again < 0.985 * now) {
+                        if (rc == SAD_OK && again < 0.995 * now) {
                             best = again;
                             table = cand;
                             improved = true;
@@ -1652,7 +1674,7 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
         if (rc == SAD_OK) rc = stage_ms(table, &b1);
         if (rc == SAD_OK) rc = stage_ms(per_bin, &a2);
         if (rc == SAD_OK) rc = stage_ms(table, &b2);
-        if (rc == SAD_OK && b1 + b2 > 0.99 * (a1 + a2)) table = per_bin;
+        if (rc == SAD_OK && b1 + b2 > a1 + a2) table = per_bin;
     }
     ctx->tuning = table;
     trace_reset(ctx, trace_was_on);

@@ -448,15 +448,17 @@ k_plane_gemm2(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             epi_barrier();
             const bool any_loc = tile_loc != 0;
+            // this thread's row tables, loaded while the tensor core still runs
+            const int32_t i = i0 + 32 * q + lane;
+            const bool row_ok = i < n;
+            const ColRec rowr = col_rec(tab, row_ok ? i : n, n);
+            const int32_t bli = row_ok ? tab.blk[i] : -2;
+            const int32_t hxi = row_ok ? tab.hidx[i] : -1;
             const bool ok_wait = mbar_wait(smem_u32(&tfull[a]), (lt >> 1) & 1, status);
             if (!ok_wait) give_up();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool valid = ok_wait && !aborted();
-            const int32_t i = i0 + 32 * q + lane;
-            const bool oki = valid && i < n;
-            const ColRec rowr = col_rec(tab, oki ? i : n, n);
-            const int32_t bli = oki ? tab.blk[i] : -2;
-            const int32_t hxi = oki ? tab.hidx[i] : -1;
+            const bool oki = valid && row_ok;
             // every pair valid and off the diagonal: the tile lies right of the
             // diagonal and inside n (uniform over the CTA)
             const bool full = i0 + kTM <= j0 && j0 + BN <= n;

@@ -88,6 +88,8 @@ def load():
         "sad_partition_keys64": (ctypes.c_int, [P, i32, P, i32, P, P, P, i32, P]),
         "sad_align_pairs": (ctypes.c_int, [P, P, P, i32, P, i32, i32, P, P, P, i64, P, i32, P]),
         "sad_partition_noalloc": (ctypes.c_int, [i32, P, P, i32, P, P, P, P]),
+        "sad_align_pairs_linear": (ctypes.c_int, [P, P, P, i32, P, i32, i32, P, P, P, i64, P, i32, P]),
+        "sad_align_linear_bytes_per_warp": (ctypes.c_int64, [i32]),
         "sad_scores_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(ctypes.c_int64)]),
         "sad_bucket_pair_scores": (ctypes.c_int, [P, ctypes.POINTER(SeqSet), P, P, i32, P, i32, i32,
                                                   i32, P, P, i64, i32, P]),
@@ -415,8 +417,10 @@ def bucket_pair_scores(residues, offsets, alphabet: int, bucket_offsets, order, 
 
 
 def align_pairs(residues, offsets, alphabet: int, pairs, subst, gap_open: int, gap_extend: int, ctx=None,
-                stream=None) -> dict:
-    """sad_align_pairs: dict(scores, ops_offsets, ops, ops_len); pairs is (npairs, 2) sequence ids.
+                stream=None, linear: bool = False) -> dict:
+    """sad_align_pairs (linear=False: direction bits of every cell) or
+    sad_align_pairs_linear (linear=True: memory linear in the lengths):
+    dict(scores, ops_offsets, ops, ops_len); pairs is (npairs, 2) sequence ids.
 
     ``columns(out, k)`` turns pair k's columns into a str over M, X, Y.
     """
@@ -436,10 +440,28 @@ def align_pairs(residues, offsets, alphabet: int, pairs, subst, gap_open: int, g
     ops = _empty(max(cap, 1), np.uint8, mem, offs)
     ol = _empty(max(npairs, 1), np.int32, mem, offs)
     ss = _seqset(res, offs, alphabet)
-    _check(load().sad_align_pairs(_ctx(ctx), ctypes.byref(ss), _ptr(pr), npairs, S.ctypes.data, gap_open,
-                                  gap_extend, _ptr(sc), _ptr(oo), _ptr(ops), cap, _ptr(ol), mem,
-                                  _stream(stream, mem)))
+    fn = load().sad_align_pairs_linear if linear else load().sad_align_pairs
+    _check(fn(_ctx(ctx), ctypes.byref(ss), _ptr(pr), npairs, S.ctypes.data, gap_open, gap_extend, _ptr(sc), _ptr(oo),
+              _ptr(ops), cap, _ptr(ol), mem, _stream(stream, mem)))
     return dict(scores=sc[:npairs], ops_offsets=oo, ops=ops, ops_len=ol[:npairs])
+
+
+def align_linear_bytes_per_warp(max_len: int) -> int:
+    """Device bytes of one warp of sad_align_pairs_linear for sequences of up to max_len residues."""
+    return int(load().sad_align_linear_bytes_per_warp(int(max_len)))
+
+
+def bucket_pairs(bucket_offsets, order):
+    """Every pair (u <= v) of every bucket as sequence ids, in the layout of the
+    score triangles: an int32 (npairs, 2) numpy array (host arrays or tensors in)."""
+    bo = bucket_offsets.cpu().numpy() if _is_torch(bucket_offsets) else np.asarray(bucket_offsets)
+    od = order.cpu().numpy() if _is_torch(order) else np.asarray(order)
+    out = []
+    for b in range(len(bo) - 1):
+        m = od[bo[b]:bo[b + 1]].astype(np.int32)
+        iu, iv = np.triu_indices(len(m))
+        out.append(np.stack([m[iu], m[iv]], axis=1))
+    return np.concatenate(out).astype(np.int32) if out else np.zeros((0, 2), np.int32)
 
 
 def progressive_align(residues, offsets, alphabet: int, bucket_offsets, order, merge_offsets, left, right, subst,

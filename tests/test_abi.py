@@ -77,3 +77,11 @@ def test_invalid_arguments_rejected_before_device_work(lib):
 def test_scores_size_host(lib):
     from paper_0901_2742_gb300 import sad
     assert sad.scores_size(np.array([0, 3, 3, 7], np.int32)) == 6 + 0 + 10
+
+
+def test_linear_alignment_scratch_grows_with_the_length(lib):
+    from paper_0901_2742_gb300 import sad
+    b = [sad.align_linear_bytes_per_warp(L) for L in (100, 1000, 10000)]
+    # 152 bytes per residue of the longer sequence: 6 int32 vectors and 32 direction words
+    assert b[1] - b[0] == 900 * 152 and b[2] - b[1] == 9000 * 152
+    assert sad.align_linear_bytes_per_warp(-1) == -1
