@@ -317,14 +317,43 @@ def serving_report(jobs_n=200, slots=4, seed=5005):
         span_stream = time.perf_counter() - t0
         st = srv.stats()
         same = all(np.array_equal(srv.result(j, w.n)["scores"], o["scores"]) for j, w, o in zip(ids, jobs, outs))
+        # jobs on the device at once: the sum of the jobs' device intervals over their union
+        spans = sorted(srv.span(j) for j in ids)
+        union, end = 0.0, -1.0
+        for a, b in spans:
+            if a > end:
+                union, end = union + b - a, b
+            elif b > end:
+                union, end = union + b - end, b
+        concurrency = sum(b - a for a, b in spans) / union if union > 0 else None
     return {"metric": "jobs/s with p50/p99 latency (Poisson arrivals)", "value": st["jobs_per_s"],
             "unit": "jobs/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
             "arrival_rate_jobs_per_s": rate, "offline_jobs_per_s": capacity,
             "offline_gcups": total_cells / span / 1e9, "stream_gcups": total_cells / span_stream / 1e9,
             "offline_p50_ms": st_off["p50_ms"], "offline_p99_ms": st_off["p99_ms"],
             "jobs": jobs_n, "slots": slots, "results_identical_to_offline": bool(same),
+            "device_concurrency": concurrency,
             "config": {"workload": "N ~ U{100..5000}, L ~ logN(300, 0.55) in [50, 1500], k=3, p=4, "
                                    "gap -11/-1"}}
+
+
+def _kmer_distinct_counts(w):
+    """Distinct k-mers of every sequence (host, numpy): the list lengths of the
+    sorted-list path, for its lookup count."""
+    L = np.diff(w.offsets)
+    cm = w.class_map if w.class_map is not None else np.arange(w.alphabet, dtype=np.uint8)
+    A2 = w.kmer_alphabet
+    out = np.zeros(w.n, np.int64)
+    for i in range(w.n):
+        x = cm[w.residues[w.offsets[i]:w.offsets[i + 1]]].astype(np.int64)
+        m = len(x) - w.k + 1
+        if m <= 0:
+            continue
+        code = np.zeros(m, np.int64)
+        for t in range(w.k):
+            code = code * A2 + x[t:t + m]
+        out[i] = len(np.unique(code))
+    return out
 
 
 def kmer_large_report(sad, peak_fp8, reps=5):
@@ -532,6 +561,8 @@ def main():
     ap.add_argument("--workload", type=int, default=2, help="2: N=2000 paper scale; 4: N=20000")
     ap.add_argument("--cap", type=int, default=4,
                     help="0: uint8 CUDA-core k-mer path; >0 tensor-core planes; -1 sorted k-mer lists")
+    ap.add_argument("--k", type=int, default=None, help="k-mer length instead of the workload's (20 letters: "
+                    "k >= 4 needs the sorted-list path, --cap=-1)")
     ap.add_argument("--mode", type=int, default=1, help="0: per-bucket launches, 1: persistent")
     ap.add_argument("--no-tune", action="store_true", help="skip the per-length-bin variant autotuner")
     ap.add_argument("--variants", default=None,
@@ -563,6 +594,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = synth.workload(args.workload)
     w.cap = args.cap
+    if args.k is not None and args.k != w.k:
+        w.name = w.name.replace(f"k={w.k}", f"k={args.k}")
+        w.k = args.k
     n, p = w.n, w.p
     dev = torch.device("cuda", local)
     # work on a created stream: the library replays its batched score graph there
@@ -668,6 +702,23 @@ def main():
 
     # the three forms of the score stage on this step's layout (outside the timed region)
     forms = None if args.no_extras else score_forms(sad, w, res_d, offs_d, out_d, flush)
+    # the sorted-list k-mer path: its all-pairs launch against the shared-memory port bound (one
+    # table lookup per column-list entry and row block of up to 8 rows; 32 lookups per clock per SM)
+    sparse_roofline = None
+    if w.cap < 0:
+        codes_k = _kmer_distinct_counts(w)
+        nd = np.asarray(codes_k, np.int64)
+        rb = (n + 7) // 8
+        suffix = np.concatenate([np.cumsum(nd[::-1])[::-1], [0]])
+        lookups = int(sum(suffix[min(8 * b, n)] for b in range(rb)))
+        ap_s = trace["allpairs"][0] / max(trace["allpairs"][1], 1) * 1e-3
+        peak_lk = SMS * 32 * SM_MAX_MHZ * 1e6
+        sparse_roofline = {"bound": "shared-memory port", "kernel": "k_sparse_pairs (sorted k-mer lists, 8 rows "
+                           "per hash table)", "kernel_ms": ap_s * 1e3, "lookups_per_launch": lookups,
+                           "achieved": lookups / ap_s / 1e12, "peak": peak_lk / 1e12, "unit": "T lookups/s",
+                           "frac": lookups / ap_s / peak_lk, "pairs_per_s": n * (n + 1) / 2 / ap_s,
+                           "distinct_kmers_per_sequence": float(nd.mean()), "kmer_space": int(w.kmer_alphabet ** w.k),
+                           "peak_basis": f"{SMS} SMs x 32 shared-memory lookups/clk x {SM_MAX_MHZ:.0f} MHz"}
     # the per-bucket guide trees (the progressive aligner's first step) on this step's own device
     # outputs, outside the timed region; the tracer times the tree kernel on its stream
     sad.trace_enable(True)
@@ -771,6 +822,7 @@ def main():
                      "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the score launches "
                                       "of one step, while the score kernels' device code is the one captured"},
         "kmer_roofline": kmer_roofline,
+        "sparse_kmer_roofline": sparse_roofline,
         "score_forms": forms,
         "serving": serving,
         "guide_trees": guide_trees,

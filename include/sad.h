@@ -615,6 +615,12 @@ int sad_server_release(sad_server* s, uint64_t job_id);
 /* Cancel: a queued job is dropped now; a running one stops between stages. */
 int sad_server_cancel(sad_server* s, uint64_t job_id);
 int sad_server_get_stats(sad_server* s, sad_server_stats* out);
+/* Device interval of a finished job: *t0_ms and *t1_ms are the times, in ms
+ * after the server was created, at which its first device operation started
+ * and its last one ended on its worker's stream (CUDA events around the job).
+ * Two jobs whose intervals intersect were on the device at the same time.
+ * SAD_EBUSY for a job that is not done. */
+int sad_server_job_span(sad_server* s, uint64_t job_id, double* t0_ms, double* t1_ms);
 /* Stop the workers (running jobs finish, queued jobs are cancelled) and free
  * everything. */
 int sad_server_destroy(sad_server* s);

@@ -1526,9 +1526,14 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
     const int32_t nm = (int32_t)merged.size();
     void* sw = nullptr;
     SAD_RET(workspace(ctx, WS_SCORE_OUT, 4ull * (total + 1), stream, &sw));
-    // every timed run starts with L2 cleared (a 256 MiB write), as a score stage
-    // does after the k-mer stage: the variants differ in how they take misses
+    // every timed run starts from the L2 state a score stage meets in a step: L2
+    // cleared (a 256 MiB write) and then the residues read once, as the k-mer
+    // stage reads them just before; the variants differ in how they take misses
+    // (with the residues cold as well, the tuned tables ran up to 20 % slower in
+    // a step than the best ones)
     const size_t flush_bytes = (size_t)256 << 20;
+    int64_t res_bytes = 0;
+    for (int32_t i = 0; i < n; i++) res_bytes += round_up(S.h_len[i], 16) + 16;
     void* flush = nullptr;
     SAD_CUDA(cudaMalloc(&flush, flush_bytes));
     struct FlushFree {
@@ -1558,6 +1563,9 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
                     if (r == 1) trace_reset(ctx, true);  // the first run warms up
                     int64_t tot = 0;
                     if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream) != cudaSuccess) rc = SAD_ECUDA;
+                    if (rc == SAD_OK && res_bytes > 0 &&
+                        cudaMemcpyAsync(flush, S.res, (size_t)res_bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
+                        rc = SAD_ECUDA;
                     if (rc == SAD_OK)
                         rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend,
                                                   SAD_SCORES_PERSISTENT, nullptr, (int32_t*)sw, total, &tot, stream);
@@ -1599,6 +1607,8 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
             trace_reset(ctx, true);
             int64_t tot = 0;
             SAD_CUDA(cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream));
+            if (res_bytes > 0)
+                SAD_CUDA(cudaMemcpyAsync(flush, S.res, (size_t)res_bytes, cudaMemcpyDeviceToDevice, stream));
             SAD_RET(bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend, SAD_SCORES_PERSISTENT,
                                          nullptr, (int32_t*)sw, total, &tot, stream));
             double ms[SAD_NUM_STAGES];

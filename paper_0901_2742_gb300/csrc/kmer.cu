@@ -691,7 +691,9 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     int64_t V = 1;
     for (int t = 0; t < k; t++) V = std::min<int64_t>(V * A2, (int64_t)1 << 40);
     const int32_t Vs = sparse ? 0 : (int32_t)round_up(V, 64);
-    const int32_t T = cap > 0 ? cap : 255;
+    // counts above T are exact through the residual: the cap of the planes; on the
+    // sorted-list path 1 with the byte table (it holds presence only), else 255
+    const int32_t T = cap > 0 ? cap : (sparse && sparse_byte_table(ctx, V) ? 1 : 255);
     SAD_CHECK(cap == 0 || S.max_len - k + 1 < 65536, SAD_EINVAL,
               "the threshold-plane path takes sequences of fewer than 65536 k-mers (longest: %d); use cap = 0",
               S.max_len - k + 1);

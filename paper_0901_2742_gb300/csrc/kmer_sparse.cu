@@ -9,14 +9,24 @@
 // Counting: one CTA per sequence computes every window's code into shared
 // memory, sorts them (bitonic) and run-length encodes the sorted codes.
 //
-// All pairs: a CTA takes TI <= 8 "row" sequences and a range of columns. It
-// inserts the rows' lists into a shared-memory hash table keyed by k-mer code
-// whose value holds one byte per row (the count clamped to 255). Each warp
-// then streams one column's list through the table: a hit adds
-// min(row byte, column count) for all rows at once (two vminu4 on the packed
-// bytes, accumulated as 16-bit halves). Counts above 255 are exact through the
-// residual matrix of the sequences whose lists hold such counts, as on the
-// uint8 dense path. The epilogue is the exact fixed-point D-sum epilogue.
+// All pairs: a CTA takes TI <= 8 "row" sequences and a range of columns, and
+// each warp streams one column's list against the rows at a time. Two forms:
+//  - k-mer spaces that fit shared memory as one byte per k-mer code (up to
+//    about 2^17.7 codes, e.g. k = 4 over 20 letters): bit r of byte c says that
+//    row r holds k-mer c. A lane reads the byte of each of its column entries
+//    and adds its two 4-row halves, spread to one byte per row by a multiply
+//    (((x & 15) * 0x00204081) & 0x01010101: the four 4-bit copies sit 7 bits
+//    apart, so none overlaps), to per-lane byte counters: no probing, no
+//    divergence. This counts sum_tau [c_i >= 1][c_j >= 1]; the rest of
+//    min(c_i, c_j) is the residual of the counts above 1 (threshold 1).
+//  - larger spaces: a shared-memory hash table keyed by k-mer code whose value
+//    holds one byte per row (the count clamped to 255); a hit adds
+//    min(row byte, column count) for all rows at once (two vminu4 on the packed
+//    bytes); counts above 255 go to the residual (threshold 255).
+// Both accumulate the rows' numerators as 16-bit halves, and counts above the
+// threshold are exact through the residual matrix of the sequences whose lists
+// hold such counts, as on the uint8 dense path. The epilogue is the exact
+// fixed-point D-sum epilogue.
 #include <algorithm>
 #include <cstring>
 
@@ -31,6 +41,8 @@ namespace {
 constexpr int kSortThreads = 1024;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr int kPairThreads = 256;
+constexpr int kPairThreadsBytes = 1024;  // a byte table of most of an SM's shared memory: one CTA, 32 warps
+constexpr int64_t kBigTable = 48 * 1024;  // byte tables above this size take the 1024-thread CTAs
 constexpr int kRowsMax = 8;       // rows per CTA: one byte each in an 8-byte table value
 constexpr int32_t kColChunkMin = kPairThreads / 32;  // one column per warp
 constexpr int32_t kColChunkMax = 2048;
@@ -153,29 +165,37 @@ struct PairOut {
     uint64_t* row_sums;
 };
 
-// Rows x columns through a per-CTA hash table of the rows' lists. Rows are the
-// row positions [blockIdx.x*TI, +TI) (sequence row_ids[pos], or pos itself when
-// row_ids is NULL; -1 is an empty row); columns are the positions
-// [blockIdx.y*cw, +cw) (sequence col_ids[pos] or pos; -1 skipped). Each lane
-// fetches four list entries before it probes, so four L2 loads are in flight.
-template <int kMode>
-__global__ void __launch_bounds__(kPairThreads)
+// Rows x columns through a per-CTA table of the rows' lists (kBytes: one byte
+// per k-mer code, log2S unused and V the table's codes; else a hash table of
+// 2^log2S slots). Rows are the row positions [blockIdx.x*TI, +TI) (sequence
+// row_ids[pos], or pos itself when row_ids is NULL; -1 is an empty row); columns
+// are the positions [blockIdx.y*cw, +cw) (sequence col_ids[pos] or pos; -1
+// skipped). Each lane fetches four list entries before it looks them up, so
+// four L2 loads are in flight.
+template <int kMode, bool kBytes, int kThreads>
+__global__ void __launch_bounds__(kThreads)
 k_sparse_pairs(int32_t n, int32_t nrows, const int32_t* __restrict__ row_ids, int32_t ncols,
-               const int32_t* __restrict__ col_ids, int32_t TI, int32_t cw, int32_t log2S, SparseLists L,
-               SeqTables tab, PairOut out) {
+               const int32_t* __restrict__ col_ids, int32_t TI, int32_t cw, int32_t log2S, int32_t V,
+               SparseLists L, SeqTables tab, PairOut out) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ unsigned long long rowc[kRowsMax], rowl[kRowsMax];
     const int32_t S = 1 << log2S;
     uint32_t* keys = sm;
     uint32_t* vals = sm + S;  // two words per slot: bytes of rows 0-3 and 4-7
+    const uint8_t* pres = (const uint8_t*)sm;  // kBytes: bit r of byte c = row r holds k-mer c
     const int32_t r0 = blockIdx.x * TI;
     const int32_t jbeg = max(kMode == kDSums ? r0 : 0, (int32_t)blockIdx.y * cw);
     const int32_t jend = min(ncols, (int32_t)(blockIdx.y + 1) * cw);
     if (jbeg >= jend) return;  // whole CTA (uniform)
-    for (int32_t t = threadIdx.x; t < S; t += blockDim.x) {
-        keys[t] = kEmpty;
-        vals[2 * t] = 0;
-        vals[2 * t + 1] = 0;
+    if constexpr (kBytes) {
+        const int32_t nw16 = (V + 15) / 16;
+        for (int32_t t = threadIdx.x; t < nw16; t += blockDim.x) ((uint4*)sm)[t] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        for (int32_t t = threadIdx.x; t < S; t += blockDim.x) {
+            keys[t] = kEmpty;
+            vals[2 * t] = 0;
+            vals[2 * t + 1] = 0;
+        }
     }
     if (threadIdx.x < kRowsMax) {
         rowc[threadIdx.x] = 0;
@@ -190,13 +210,17 @@ k_sparse_pairs(int32_t n, int32_t nrows, const int32_t* __restrict__ row_ids, in
         const int32_t nq = L.nd[q];
         for (int32_t t = threadIdx.x; t < nq; t += blockDim.x) {
             const uint2 e = lq[t];
-            uint32_t slot = hash_slot(e.x, log2S);
-            for (int32_t probe = 0; probe < S; probe++) {
-                const uint32_t prev = atomicCAS(&keys[slot], kEmpty, e.x);
-                if (prev == kEmpty || prev == e.x) break;
-                slot = (slot + 1) & (uint32_t)(S - 1);
+            if constexpr (kBytes) {
+                atomicOr(&sm[e.x >> 2], 1u << (8 * (e.x & 3) + r));
+            } else {
+                uint32_t slot = hash_slot(e.x, log2S);
+                for (int32_t probe = 0; probe < S; probe++) {
+                    const uint32_t prev = atomicCAS(&keys[slot], kEmpty, e.x);
+                    if (prev == kEmpty || prev == e.x) break;
+                    slot = (slot + 1) & (uint32_t)(S - 1);
+                }
+                atomicOr(&vals[2 * slot + (r >> 2)], min(e.y, 255u) << (8 * (r & 3)));
             }
-            atomicOr(&vals[2 * slot + (r >> 2)], min(e.y, 255u) << (8 * (r & 3)));
         }
     }
     __syncthreads();
@@ -217,7 +241,39 @@ k_sparse_pairs(int32_t n, int32_t nrows, const int32_t* __restrict__ row_ids, in
         const uint2* lj = L.lists + L.loff[j];
         const int32_t nj = L.nd[j];
         uint32_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-        for (int32_t t0 = 0; t0 < nj; t0 += 4 * 32) {
+        if constexpr (kBytes) {
+            // per-lane byte counters of rows 0-3 (lo) and 4-7 (hi); a lane adds at
+            // most 4 per round and at most 63 rounds before folding: <= 252 per byte
+            uint32_t lo = 0, hi = 0;
+            int32_t rounds = 0;
+            for (int32_t t0 = 0; t0 < nj; t0 += 4 * 32) {
+                uint32_t code[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int32_t t = t0 + u * 32 + lane;
+                    code[u] = t < nj ? lj[t].x : kEmpty;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t b = code[u] != kEmpty ? (uint32_t)pres[code[u]] : 0u;
+                    lo += ((b & 15u) * 0x00204081u) & 0x01010101u;
+                    hi += ((b >> 4) * 0x00204081u) & 0x01010101u;
+                }
+                if (++rounds == 63) {
+                    acc0 += lo & 0x00ff00ffu;
+                    acc1 += (lo >> 8) & 0x00ff00ffu;
+                    acc2 += hi & 0x00ff00ffu;
+                    acc3 += (hi >> 8) & 0x00ff00ffu;
+                    lo = hi = 0;
+                    rounds = 0;
+                }
+            }
+            acc0 += lo & 0x00ff00ffu;         // rows 0 and 2
+            acc1 += (lo >> 8) & 0x00ff00ffu;  // rows 1 and 3
+            acc2 += hi & 0x00ff00ffu;         // rows 4 and 6
+            acc3 += (hi >> 8) & 0x00ff00ffu;  // rows 5 and 7
+        }
+        for (int32_t t0 = 0; !kBytes && t0 < nj; t0 += 4 * 32) {
             uint2 e[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
@@ -323,21 +379,31 @@ int log2_ceil(int64_t v) {
     return l;
 }
 
-// Launch shape of the rows x columns kernel: the largest TI in {8, 4, 2, 1}
-// whose hash table (a power of two with the rows' distinct k-mers, bounded by
-// the k-mer space, filling at most 0.6 of it; at least 16 slots) fits in shared
-// memory, and a column chunk that leaves a few waves of CTAs (a wider chunk
+// Launch shape of the rows x columns kernel: the byte table (8 rows) when the
+// k-mer space fits shared memory at one byte per code; else the largest TI in
+// {8, 4, 2, 1} whose hash table (a power of two with the rows' distinct k-mers,
+// bounded by the k-mer space, filling at most 0.6 of it; at least 16 slots)
+// fits; and a column chunk that leaves a few waves of CTAs (a wider chunk
 // amortises the table's clear and build).
 struct PairShape {
     int32_t TI, log2S, cw;
     size_t smem;
+    bool bytes;
+    int32_t V;
 };
 
 int pair_shape(sad_ctx* ctx, int64_t keys8, int64_t per_row, int64_t V, int64_t nrows, int64_t ncols,
                bool triangle, PairShape* sh) {
     const int64_t limit = (int64_t)ctx->smem_optin - 1024;
     sh->TI = 0;
-    for (int t = kRowsMax; t >= 1; t >>= 1) {
+    sh->bytes = sparse_byte_table(ctx, V);
+    sh->V = sh->bytes ? (int32_t)V : 0;
+    if (sh->bytes) {
+        sh->TI = kRowsMax;
+        sh->log2S = 0;
+        sh->smem = (size_t)round_up(V, 16);
+    }
+    for (int t = kRowsMax; t >= 1 && !sh->bytes; t >>= 1) {
         int64_t keys = t == kRowsMax ? keys8 : std::min(keys8, per_row * t);
         keys = std::min(keys, V);
         const int l = std::max(4, log2_ceil(std::max<int64_t>((5 * keys + 2) / 3, 16)));
@@ -348,15 +414,30 @@ int pair_shape(sad_ctx* ctx, int64_t keys8, int64_t per_row, int64_t V, int64_t 
         }
     }
     SAD_CHECK(sh->TI > 0, SAD_EINVAL, "a sequence has too many distinct k-mers for the sorted-list hash table");
-    sh->smem = (size_t)12 << sh->log2S;
-    // the widest chunk (up to 2048 columns) that still gives 8 CTAs per SM, else
-    // the narrowest (one column per warp)
+    if (!sh->bytes) sh->smem = (size_t)12 << sh->log2S;
+    // the widest chunk (up to 2048 columns) that still gives 8 CTAs per SM (4 of
+    // the 1024-thread CTAs of a big byte table), else the narrowest (one column
+    // per warp)
     const int64_t rb = (nrows + sh->TI - 1) / sh->TI;
-    const int64_t want = 8ll * ctx->num_sms;
+    const bool big = sh->bytes && (int64_t)sh->smem > kBigTable;
+    const int64_t want = (big ? 4ll : 8ll) * ctx->num_sms;
     sh->cw = kColChunkMax;
-    while (sh->cw > kColChunkMin &&
+    while (sh->cw > (big ? kPairThreadsBytes / 32 : kColChunkMin) &&
            rb * ((ncols + sh->cw - 1) / sh->cw) / (triangle ? 2 : 1) < want)
         sh->cw /= 2;
+    return SAD_OK;
+}
+
+template <int kMode, bool kBytes, int kThreads>
+int launch_pairs_t(sad_ctx* ctx, int32_t n, int32_t nrows, const int32_t* row_ids, int32_t ncols,
+                   const int32_t* col_ids, const PairShape& sh, const SparseLists& L, const SeqTables& tab,
+                   const PairOut& out, cudaStream_t stream) {
+    if (sh.smem > 40 * 1024)
+        SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_sparse_pairs<kMode, kBytes, kThreads>));
+    const dim3 grid((unsigned)((nrows + sh.TI - 1) / sh.TI), (unsigned)((ncols + sh.cw - 1) / sh.cw));
+    k_sparse_pairs<kMode, kBytes, kThreads><<<grid, kThreads, sh.smem, stream>>>(
+        n, nrows, row_ids, ncols, col_ids, sh.TI, sh.cw, sh.log2S, sh.V, L, tab, out);
+    SAD_LAUNCHED();
     return SAD_OK;
 }
 
@@ -364,15 +445,21 @@ template <int kMode>
 int launch_pairs(sad_ctx* ctx, int32_t n, int32_t nrows, const int32_t* row_ids, int32_t ncols,
                  const int32_t* col_ids, const PairShape& sh, const SparseLists& L, const SeqTables& tab,
                  const PairOut& out, cudaStream_t stream) {
-    if (sh.smem > 40 * 1024) SAD_RET(allow_max_dynamic_smem(ctx, (const void*)k_sparse_pairs<kMode>));
-    const dim3 grid((unsigned)((nrows + sh.TI - 1) / sh.TI), (unsigned)((ncols + sh.cw - 1) / sh.cw));
-    k_sparse_pairs<kMode><<<grid, kPairThreads, sh.smem, stream>>>(n, nrows, row_ids, ncols, col_ids, sh.TI, sh.cw,
-                                                                   sh.log2S, L, tab, out);
-    SAD_LAUNCHED();
-    return SAD_OK;
+    if (!sh.bytes)
+        return launch_pairs_t<kMode, false, kPairThreads>(ctx, n, nrows, row_ids, ncols, col_ids, sh, L, tab, out,
+                                                          stream);
+    if ((int64_t)sh.smem > kBigTable)
+        return launch_pairs_t<kMode, true, kPairThreadsBytes>(ctx, n, nrows, row_ids, ncols, col_ids, sh, L, tab,
+                                                              out, stream);
+    return launch_pairs_t<kMode, true, kPairThreads>(ctx, n, nrows, row_ids, ncols, col_ids, sh, L, tab, out,
+                                                     stream);
 }
 
 }  // namespace
+
+bool sparse_byte_table(const sad_ctx* ctx, int64_t V) {
+    return V >= 1 && round_up(V, 16) <= (int64_t)ctx->smem_optin - 2048;
+}
 
 int sparse_count(sad_ctx* ctx, const DevSeqs& S, int32_t k, int32_t A2, const ClassMap& cm, int32_t T,
                  const int64_t* loff, uint2* lists, int32_t* nd, const int64_t* ex_off, int32_t* ex_tau,

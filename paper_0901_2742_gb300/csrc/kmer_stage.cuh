@@ -65,6 +65,11 @@ struct SparseLists {
     const int32_t* nd;
 };
 
+// Whether the sorted-list path of this k-mer space uses the byte table (one
+// byte per k-mer code in shared memory; counts above 1 then go to the residual)
+// instead of the hash table (counts above 255 to the residual).
+bool sparse_byte_table(const sad_ctx* ctx, int64_t V);
+
 // Sort every sequence's k-mer codes and run-length encode them; counts above T
 // also go to the excess lists (ascending code) used by the residual matrix.
 int sparse_count(sad_ctx* ctx, const DevSeqs& S, int32_t k, int32_t A2, const ClassMap& cm, int32_t T,

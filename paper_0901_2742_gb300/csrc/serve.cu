@@ -50,6 +50,14 @@ struct Job {
     std::vector<int32_t> bucket_offsets, order, scores;
     std::vector<int64_t> score_offsets;
     Clock::time_point t_submit, t_start, t_done;
+    // device interval: events on the worker's stream before the job's first and
+    // after its last device operation
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    ~Job() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
 };
 
 }  // namespace
@@ -73,6 +81,7 @@ struct sad_server {
     std::vector<double> latencies_ms;
     sad::Clock::time_point t_first_submit, t_last_done;
     bool any_submit = false;
+    cudaEvent_t origin = nullptr;  // recorded at creation: zero of the jobs' device intervals
 };
 
 namespace sad {
@@ -117,6 +126,12 @@ void run_job(sad_server* s, int slot, Job* job) {
         return fail(SAD_ECUDA);
     }
     clear_error();
+    if (cudaEventCreate(&job->ev0) != cudaSuccess || cudaEventCreate(&job->ev1) != cudaSuccess ||
+        cudaEventRecord(job->ev0, stream) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaEventCreate/Record failed");
+        return fail(SAD_ECUDA);
+    }
     int rc = status_clear(ctx, stream);
     if (rc != SAD_OK) return fail(rc);
     sad_seqset ss{job->res.data(), job->offs.data(), job->n, job->alphabet};
@@ -192,6 +207,8 @@ void run_job(sad_server* s, int slot, Job* job) {
     }
     job->scores.resize((size_t)total);
     job->order.resize((size_t)n);
+    job->timed = cudaEventRecord(job->ev1, stream) == cudaSuccess;
+    cudaGetLastError();
     rc = status_check(ctx, stream);
     if (rc != SAD_OK) return fail(rc);
     job->rc = SAD_OK;
@@ -304,6 +321,18 @@ int sad_server_create(const sad_server_config* cfg, sad_server** out) {
         }
         s->slot_ctx.push_back(c);
         s->slot_stream.push_back(st);
+    }
+    if (cudaEventCreate(&s->origin) != cudaSuccess || cudaEventRecord(s->origin, s->slot_stream[0]) != cudaSuccess ||
+        cudaEventSynchronize(s->origin) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->origin) cudaEventDestroy(s->origin);
+        for (size_t q = 0; q < s->slot_ctx.size(); q++) {
+            cudaStreamDestroy(s->slot_stream[q]);
+            sad_ctx_destroy(s->slot_ctx[q]);
+        }
+        delete s;
+        set_error("cudaEventCreate/Record of the server origin failed");
+        return SAD_ECUDA;
     }
     for (int i = 0; i < cfg->slots; i++) s->workers.emplace_back(worker_main, s, i);
     *out = s;
@@ -465,6 +494,24 @@ int sad_server_cancel(sad_server* s, uint64_t job_id) {
     return SAD_OK;
 }
 
+int sad_server_job_span(sad_server* s, uint64_t job_id, double* t0_ms, double* t1_ms) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(s && t0_ms && t1_ms, SAD_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(job_id);
+    SAD_CHECK(it != s->jobs.end(), SAD_ENOTFOUND, "unknown job %llu", (unsigned long long)job_id);
+    Job* j = it->second.get();
+    SAD_CHECK(j->state == SAD_JOB_DONE && j->timed, SAD_EBUSY, "job %llu has no device interval (state %d)",
+              (unsigned long long)job_id, j->state);
+    float a = 0, b = 0;
+    SAD_CUDA(cudaEventElapsedTime(&a, s->origin, j->ev0));
+    SAD_CUDA(cudaEventElapsedTime(&b, s->origin, j->ev1));
+    *t0_ms = a;
+    *t1_ms = b;
+    return SAD_OK;
+}
+
 int sad_server_get_stats(sad_server* s, sad_server_stats* out) {
     using namespace sad;
     clear_error();
@@ -504,10 +551,13 @@ int sad_server_destroy(sad_server* s) {
     }
     s->cv_work.notify_all();
     for (auto& t : s->workers) t.join();
+    s->queue.clear();
+    s->jobs.clear();  // the jobs' events go before their streams
     for (size_t q = 0; q < s->slot_ctx.size(); q++) {
         cudaStreamDestroy(s->slot_stream[q]);
         sad_ctx_destroy(s->slot_ctx[q]);
     }
+    if (s->origin) cudaEventDestroy(s->origin);
     delete s;
     return SAD_OK;
 }

@@ -640,6 +640,7 @@ def _bind_server(lib):
         "sad_server_release": [P, u64],
         "sad_server_cancel": [P, u64],
         "sad_server_get_stats": [P, ctypes.POINTER(ServerStats)],
+        "sad_server_job_span": [P, u64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "sad_server_destroy": [P],
     }
     for name, args in sig.items():
@@ -706,6 +707,12 @@ class Server:
                                           sc.ctypes.data, len(sc), ctypes.byref(cnt), ctypes.byref(lat)))
         return dict(bucket_offsets=bo, order=order[:n], score_offsets=so, scores=sc[:cnt.value],
                     latency_ms=lat.value)
+
+    def span(self, job_id) -> tuple:
+        """(start, end) in ms after the server's creation of the job's device work."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.sad_server_job_span(self.handle, job_id, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def release(self, job_id):
         _check(self.lib.sad_server_release(self.handle, job_id))

@@ -99,3 +99,32 @@ def test_cancel_a_queued_job(sad):
         assert srv.wait(queued[0], 120000) == sad.SAD_OK
         assert srv.wait(queued[2], 120000) == sad.SAD_OK
         assert srv.stats()["cancelled"] == 1
+
+
+def test_jobs_in_the_mix_overlap_on_the_device(sad):
+    """Continuous batching: jobs submitted together run on the device at the same
+    time (their device intervals, from CUDA events on the workers' streams,
+    intersect), and every result is the job's result alone."""
+    ws = job_workloads(8, seed0=600)
+    ref = [alone(sad, w) for w in ws]
+    with sad.Server(slots=4) as srv:
+        ids = [submit(srv, w) for w in ws]
+        for jid in ids:
+            assert srv.wait(jid, 120000) == sad.SAD_OK, srv.error()
+        spans = [srv.span(j) for j in ids]
+        for jid, w, r in zip(ids, ws, ref):
+            np.testing.assert_array_equal(srv.result(jid, w.n)["scores"], r[3])
+    assert all(0 <= a < b for a, b in spans)
+    overlapping = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
+                      if max(spans[i][0], spans[j][0]) < min(spans[i][1], spans[j][1]))
+    assert overlapping >= 3, spans
+    # busy time of the union is below the sum of the intervals: work ran side by side
+    union, end = 0.0, -1.0
+    for a, b in sorted(spans):
+        if a > end:
+            union += b - a
+            end = b
+        elif b > end:
+            union += b - end
+            end = b
+    assert union < 0.9 * sum(b - a for a, b in spans)
