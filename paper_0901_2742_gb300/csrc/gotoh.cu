@@ -1452,6 +1452,13 @@ extern "C" int sad_scores_set_variants(sad_ctx* ctx_in, const int32_t* upper, co
     return SAD_OK;
 }
 
+namespace sad {
+int bucket_pair_scores_locked(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                              const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
+                              int32_t gap_extend, int32_t mode, int64_t* score_offsets, int32_t* scores,
+                              int64_t scores_capacity, int32_t mem, cudaStream_t stream);
+}  // namespace sad
+
 extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, const int32_t* bucket_offsets,
                                    const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
                                    int32_t gap_extend, const int32_t* bin_upper, int32_t nbins, int32_t reps,
@@ -1524,16 +1531,29 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
         }
     }
     const int32_t nm = (int32_t)merged.size();
-    void* sw = nullptr;
-    SAD_RET(workspace(ctx, WS_SCORE_OUT, 4ull * (total + 1), stream, &sw));
-    // every timed run starts from the L2 state a score stage meets in a step: L2
-    // cleared (a 256 MiB write) and then the residues read once, as the k-mer
-    // stage reads them just before; the variants differ in how they take misses
-    // (with the residues cold as well, the tuned tables ran up to 20 % slower in
-    // a step than the best ones)
+    // every timed run is a whole sad_bucket_pair_scores call on the caller's own
+    // arguments (sequence staging included), its score launches timed by the
+    // tracer; outputs go to buffers of the tuner in the caller's memory space
+    std::vector<int64_t> h_so((size_t)p + 1);
+    std::vector<int32_t> h_sc((size_t)total + 1);
+    void* d_out = nullptr;
+    if (mem == SAD_MEM_DEVICE) SAD_CUDA(cudaMalloc(&d_out, 8ull * (p + 1) + 4ull * (total + 1) + 256));
+    struct OutFree {
+        void* p;
+        ~OutFree() {
+            if (p) cudaFree(p);
+        }
+    } out_free{d_out};
+    int64_t* so_out = mem == SAD_MEM_DEVICE ? (int64_t*)d_out : h_so.data();
+    int32_t* sc_out = mem == SAD_MEM_DEVICE ? (int32_t*)((char*)d_out + round_up(8ll * (p + 1), 256)) : h_sc.data();
+    auto score_call = [&]() {
+        return bucket_pair_scores_locked(ctx, seqs, bucket_offsets, order, p, subst, gap_open, gap_extend,
+                                         SAD_SCORES_PERSISTENT, so_out, sc_out, total, mem, stream);
+    };
+    // every timed run starts with L2 cleared (a 256 MiB write), as a step's
+    // score stage meets it after the k-mer stage (which, like the call's own
+    // staging, reads the residues again)
     const size_t flush_bytes = (size_t)256 << 20;
-    int64_t res_bytes = 0;
-    for (int32_t i = 0; i < n; i++) res_bytes += round_up(S.h_len[i], 16) + 16;
     void* flush = nullptr;
     SAD_CUDA(cudaMalloc(&flush, flush_bytes));
     struct FlushFree {
@@ -1561,14 +1581,8 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
                 trace_reset(ctx, true);
                 for (int32_t r = 0; r <= reps && rc == SAD_OK; r++) {
                     if (r == 1) trace_reset(ctx, true);  // the first run warms up
-                    int64_t tot = 0;
                     if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream) != cudaSuccess) rc = SAD_ECUDA;
-                    if (rc == SAD_OK && res_bytes > 0 &&
-                        cudaMemcpyAsync(flush, S.res, (size_t)res_bytes, cudaMemcpyDeviceToDevice, stream) != cudaSuccess)
-                        rc = SAD_ECUDA;
-                    if (rc == SAD_OK)
-                        rc = bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend,
-                                                  SAD_SCORES_PERSISTENT, nullptr, (int32_t*)sw, total, &tot, stream);
+                    if (rc == SAD_OK) rc = score_call();
                 }
                 double ms[SAD_NUM_STAGES];
                 int32_t cnt[SAD_NUM_STAGES];
@@ -1605,12 +1619,8 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
         std::vector<double> runs;
         for (int32_t r = 0; r <= jreps; r++) {
             trace_reset(ctx, true);
-            int64_t tot = 0;
             SAD_CUDA(cudaMemsetAsync(flush, r & 0xff, flush_bytes, stream));
-            if (res_bytes > 0)
-                SAD_CUDA(cudaMemcpyAsync(flush, S.res, (size_t)res_bytes, cudaMemcpyDeviceToDevice, stream));
-            SAD_RET(bucket_scores_device(ctx, S, dbo, dord, p, subst, gap_open, gap_extend, SAD_SCORES_PERSISTENT,
-                                         nullptr, (int32_t*)sw, total, &tot, stream));
+            SAD_RET(score_call());
             double ms[SAD_NUM_STAGES];
             int32_t cnt[SAD_NUM_STAGES];
             SAD_RET(trace_collect(ctx, ms, cnt, SAD_NUM_STAGES));
@@ -1724,29 +1734,17 @@ extern "C" int sad_scores_size(const int32_t* bucket_offsets, int32_t p, int32_t
     return SAD_OK;
 }
 
-extern "C" int sad_bucket_pair_scores(sad_ctx* ctx_in, const sad_seqset* seqs,
-                                      const int32_t* bucket_offsets, const int32_t* order, int32_t p,
-                                      const int8_t* subst, int32_t gap_open, int32_t gap_extend,
-                                      int32_t mode, int64_t* score_offsets, int32_t* scores,
-                                      int64_t scores_capacity, int32_t mem, void* stream_ptr) {
-    using namespace sad;
-    clear_error();
-    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
-    SAD_CHECK(seqs && bucket_offsets && score_offsets && subst, SAD_EINVAL, "a required pointer is NULL");
-    SAD_CHECK(p >= 1, SAD_EINVAL, "p = %d < 1", p);
-    SAD_CHECK(gap_open <= 0 && gap_extend <= 0, SAD_EINVAL,
-              "gap costs must be <= 0 (got open %d, extend %d)", gap_open, gap_extend);
-    SAD_CHECK(gap_open >= -(1 << 20) && gap_extend >= -(1 << 20), SAD_EINVAL, "gap costs too large");
+namespace sad {
+
+// The work of sad_bucket_pair_scores once its arguments are checked and ctx is
+// locked: staging of the sequences, the score stage, the copies back (host
+// mode) and the status check. The autotuner times candidate tables through it,
+// so that it measures exactly what a caller's call runs.
+int bucket_pair_scores_locked(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* bucket_offsets,
+                              const int32_t* order, int32_t p, const int8_t* subst, int32_t gap_open,
+                              int32_t gap_extend, int32_t mode, int64_t* score_offsets, int32_t* scores,
+                              int64_t scores_capacity, int32_t mem, cudaStream_t stream) {
     const int32_t A = seqs->alphabet;
-    SAD_CHECK(A >= 1 && A <= SAD_MAX_ALPHABET, SAD_EINVAL, "alphabet %d", A);
-    for (int32_t x = 0; x < A; x++)
-        for (int32_t y = 0; y < A; y++)
-            SAD_CHECK(subst[x * A + y] == subst[y * A + x], SAD_EINVAL,
-                      "substitution matrix is not symmetric at (%d, %d)", x, y);
-    sad_ctx* ctx = nullptr;
-    SAD_RET(resolve_ctx(ctx_in, &ctx));
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    cudaStream_t stream = (cudaStream_t)stream_ptr;
     SAD_RET(status_clear(ctx, stream));
     DevSeqs S;
     SAD_RET(prepare_seqs(ctx, seqs, mem, stream, &S));
@@ -1792,4 +1790,32 @@ extern "C" int sad_bucket_pair_scores(sad_ctx* ctx_in, const sad_seqset* seqs,
     }
     SAD_RET(status_check(ctx, stream));
     return SAD_OK;
+}
+
+}  // namespace sad
+
+extern "C" int sad_bucket_pair_scores(sad_ctx* ctx_in, const sad_seqset* seqs,
+                                      const int32_t* bucket_offsets, const int32_t* order, int32_t p,
+                                      const int8_t* subst, int32_t gap_open, int32_t gap_extend,
+                                      int32_t mode, int64_t* score_offsets, int32_t* scores,
+                                      int64_t scores_capacity, int32_t mem, void* stream_ptr) {
+    using namespace sad;
+    clear_error();
+    SAD_CHECK(mem == SAD_MEM_HOST || mem == SAD_MEM_DEVICE, SAD_EINVAL, "mem = %d", mem);
+    SAD_CHECK(seqs && bucket_offsets && score_offsets && subst, SAD_EINVAL, "a required pointer is NULL");
+    SAD_CHECK(p >= 1, SAD_EINVAL, "p = %d < 1", p);
+    SAD_CHECK(gap_open <= 0 && gap_extend <= 0, SAD_EINVAL,
+              "gap costs must be <= 0 (got open %d, extend %d)", gap_open, gap_extend);
+    SAD_CHECK(gap_open >= -(1 << 20) && gap_extend >= -(1 << 20), SAD_EINVAL, "gap costs too large");
+    const int32_t A = seqs->alphabet;
+    SAD_CHECK(A >= 1 && A <= SAD_MAX_ALPHABET, SAD_EINVAL, "alphabet %d", A);
+    for (int32_t x = 0; x < A; x++)
+        for (int32_t y = 0; y < A; y++)
+            SAD_CHECK(subst[x * A + y] == subst[y * A + x], SAD_EINVAL,
+                      "substitution matrix is not symmetric at (%d, %d)", x, y);
+    sad_ctx* ctx = nullptr;
+    SAD_RET(resolve_ctx(ctx_in, &ctx));
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    return bucket_pair_scores_locked(ctx, seqs, bucket_offsets, order, p, subst, gap_open, gap_extend, mode,
+                                     score_offsets, scores, scores_capacity, mem, (cudaStream_t)stream_ptr);
 }

@@ -28,3 +28,22 @@ def test_traffic_only_for_the_profiled_kernel(monkeypatch):
     stale = dict(bench.SCORE_TRAFFIC, gotoh_device_sha256="0" * 64)
     monkeypatch.setattr(bench, "SCORE_TRAFFIC", stale)
     assert bench.score_traffic() is None
+
+
+def test_sparse_lookup_count_brute_force():
+    """The sorted-list path's lookup count: per row block of 8 rows, one lookup
+    per k-mer entry of every column j >= the block's first row; distinct k-mers
+    counted here with Python sets."""
+    import numpy as np
+    from paper_0901_2742_gb300 import synth
+    w = synth.workload(1)
+    w.k = 4
+    L = np.diff(w.offsets)
+    distinct = [len({tuple(w.residues[w.offsets[i] + t:w.offsets[i] + t + w.k]) for t in range(L[i] - w.k + 1)})
+                for i in range(w.n)]
+    assert list(bench._kmer_distinct_counts(w)) == distinct
+    want = sum(distinct[j] for b0 in range(0, w.n, 8) for j in range(b0, w.n))
+    r = bench.sparse_kmer_roofline(w, 1.0)
+    assert r["lookups_per_launch"] == want
+    assert r["kmer_space"] == w.kmer_alphabet ** 4
+    assert abs(r["frac"] - want / 1e-3 / (bench.SMS * 32 * bench.SM_MAX_MHZ * 1e6)) < 1e-12
