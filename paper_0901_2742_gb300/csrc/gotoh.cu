@@ -503,6 +503,14 @@ __device__ void align_pair16c(const uint32_t* __restrict__ prof, int32_t m1, int
 // The group's non-empty subjects go to shared memory first (slots g, g + NG,
 // ... of subj_pos / subj_off), so that moving to the next subject inside the
 // wavefront loop is an index step and one shared load.
+// With C = 2 columns per step a subject of odd length starts one column early,
+// at a virtual column 0 that the recurrence itself fills with the boundary
+// values: the lane enters it with H = E = the stored sentinel 0 and
+// Hg = go + ge (so the diagonal and horizontal candidates stay below every
+// boundary value, which the bias guarantees to exceed the largest substitution
+// score), and the vertical candidate down the column, started from H(0, 0),
+// is go + i ge, the boundary H(i, 0). Every chunk then holds two columns, and
+// no lane runs a one-column step while the others of its warp run two.
 template <int R, int C>
 __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int32_t m2, int32_t u1, int32_t u2,
                               int32_t b, int32_t boff, int32_t nb, int32_t vfirst, int32_t vend, int32_t vstep,
@@ -546,6 +554,8 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
     const int32_t steps = __reduce_max_sync(0xffffffffu, nchunks > 0 ? nchunks + G - 1 : 0);
     if (steps == 0) return;
     // this lane's cursor: subject ordinal k, its length, CSR position, residues, next column
+    // (0: the virtual column of an odd-length subject)
+    constexpr bool kVirt = C == 2;
     int32_t ck = -1, cn = 0, cuv = 0, cj = 1;
     const uint8_t* cy = nullptr;
     auto advance = [&]() {
@@ -556,7 +566,7 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
             cn = e.y;
             cy = a.res + subj_off[ck * vstep];
         }
-        cj = 1;
+        cj = kVirt ? 1 - (cn & 1) : 1;
     };
     advance();
     const int32_t row0 = lane * R;
@@ -574,13 +584,24 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
     for (int32_t tau = 0; tau < steps; tau++) {
         const bool live = tau >= lane && ck < nsubj;
         if (lane == 0 && live) {
-            yin = 0;
+            if constexpr (kVirt) {
+                // columns cj, cj + 1 (letters y[cj - 1], y[cj]; the virtual column
+                // takes any letter, here y[0]); the top row H(0, j) = go + j ge
+                // (H(0, 0) = 0), stored values below 2^16 so that pk2(x, x) = x 0x10001
+                yin = (uint32_t)cy[max(cj - 1, 0)] | ((uint32_t)cy[cj] << 8);
+                hin[1] = (uint32_t)(go + (cj + 1) * ge + B) * 0x10001u;
+                hin[0] = cj == 0 ? (uint32_t)B * 0x10001u : hin[1] - (uint32_t)ge * 0x10001u;
+                fin[0] = 0u;
+                fin[1] = 0u;
+            } else {
+                yin = 0;
 #pragma unroll
-            for (int c = 0; c < C; c++) {
-                yin |= (uint32_t)cy[cj - 1 + c] << (8 * c);  // bytes past the subject are zero padding
-                const int32_t bnd0 = go + (cj + c) * ge + B;
-                hin[c] = pk2(bnd0, bnd0);
-                fin[c] = 0u;
+                for (int c = 0; c < C; c++) {
+                    yin |= (uint32_t)cy[cj - 1 + c] << (8 * c);  // bytes past the subject are zero padding
+                    const int32_t bnd0 = go + (cj + c) * ge + B;
+                    hin[c] = pk2(bnd0, bnd0);
+                    fin[c] = 0u;
+                }
             }
         }
         uint32_t hout[C], fout[C];
@@ -590,7 +611,16 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
             fout[c] = fin[c];
         }
         if (live) {
-            if (cj == 1) {  // entering a subject: column 0 of my rows
+            if (kVirt && cj == 0) {  // entering an odd-length subject: the sentinel column -1
+                const uint32_t hg0 = pk2(go + ge, go + ge);
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    H[r] = 0u;
+                    Hg[r] = hg0;
+                    E[r] = 0u;
+                }
+                hdiag = 0u;
+            } else if (cj == 1) {  // entering a subject: column 0 of my rows
                 // recomputed here on purpose: hoisting these 2R loop-invariant values
                 // out of the loop would hold them in registers for the whole stream
                 int32_t base;
@@ -606,9 +636,13 @@ __device__ void stream_pair16(const uint32_t* __restrict__ prof, int32_t m1, int
                 }
                 hdiag = row0 == 0 ? pk2(B, B) : pk2(base, base);
             }
-            const int32_t cnt = min(C, cn - cj + 1);
-            pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe_w, hout,
-                               fout);
+            const int32_t cnt = kVirt ? C : min(C, cn - cj + 1);
+            if constexpr (kVirt)
+                pair16_columns<R, C>(prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe_w, hout,
+                                     fout);
+            else
+                pair16_chunk<R, C>(cnt, prof, a.prof_stride, chunk, yin, H, Hg, E, hin, fin, hdiag, ge2, goe_w,
+                                   hout, fout);
 #pragma unroll
             for (int c = 0; c < C; c++)
                 if (c == cnt - 1) hdiag = hin[c];
@@ -893,7 +927,11 @@ bool packed16_bias(const DevSeqs& S, const int8_t* subst, int32_t go, int32_t ge
     const int64_t rows = L + 1024;  // padding of the widest strip
     const int64_t vmax = (int64_t)smax * L;
     const int64_t vmin = 2ll * go + (int64_t)ge * (rows + L);
-    const int64_t lo = -vmin - std::min<int64_t>(std::min<int64_t>(smin, go + ge), 0);
+    // every stored value, and each sum with a negative addend, >= 0; every
+    // boundary value go + i ge + B (i <= rows) above the largest substitution
+    // score (the virtual column of the streaming form relies on it)
+    const int64_t lo = std::max<int64_t>(-vmin - std::min<int64_t>(std::min<int64_t>(smin, go + ge), 0),
+                                         (int64_t)smax + 1 - go - (int64_t)ge * rows);
     const int64_t hi = 32767 - vmax - smax;
     if (lo > hi) return false;
     *bias = (int32_t)lo;

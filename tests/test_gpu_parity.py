@@ -347,6 +347,33 @@ def test_every_packed_variant_exact(sad, R, G):
     np.testing.assert_array_equal(sc, want_sc)
 
 
+@pytest.mark.parametrize("R", [8, 12, 16, 20, 24, 32])
+@pytest.mark.parametrize("G", [8, 16, 32])
+@pytest.mark.parametrize("gaps", [(-11, -1), (0, 0)])
+def test_every_packed_variant_streaming_exact(sad, R, G, gaps):
+    """One packed variant forced for query pairs that all fit one strip of
+    G x R rows, so the launch streams every group's subjects through one
+    wavefront: subjects of odd and even length (1, 2 and 3 residues among them)
+    follow each other, each odd one entered through its virtual column 0."""
+    go, ge = gaps
+    rng = np.random.default_rng(R * 1000 + G * 10 + abs(go))
+    lens = list(rng.integers(1, G * R + 1, 40)) + [1, 2, 3, 4, 5, G * R, G * R - 1, 0]
+    seqs = [list(rng.integers(0, 20, L)) for L in lens]
+    res, offs = synth.pack(seqs)
+    n = len(seqs)
+    order = rng.permutation(n).astype(np.int32)
+    bo = np.array([0, 3, 17, n], np.int32)
+    S = synth.subst_matrix(7)
+    want_so, want_sc = oracle.bucket_pair_scores(res, offs, bo, order, S, go, ge)
+    sad.set_score_variants([(2 ** 31 - 1, R, G)])
+    try:
+        so, sc = sad.bucket_pair_scores(res, offs, 20, bo, order, S, go, ge, mode=1)
+    finally:
+        sad.set_score_variants([])
+    np.testing.assert_array_equal(so, want_so)
+    np.testing.assert_array_equal(sc, want_sc)
+
+
 def test_autotuned_variants_stay_exact(sad):
     """The autotuner only picks speeds: after tuning on the paper-scale layout
     the scores are still those of the oracle."""
