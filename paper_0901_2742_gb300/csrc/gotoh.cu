@@ -994,6 +994,20 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
     }
     const ScoreTuning& tu = ctx->tuning;
     const int fv = tu.filter ? variant_index(tu.force_R, tu.force_G) : -1;
+    // subjects per work item: up to kChunkSubjects, fewer when the call holds
+    // few (query pair, subject) visits, so that there are about five items per
+    // resident CTA and the persistent launches end on small items (N = 2000:
+    // 24 subjects, scores 2.22 -> 2.11 ms; N = 20000 keeps 64, where 24 cost 2 %
+    // in profile builds)
+    int64_t visits = 0;
+    for (int32_t b = 0; b < p; b++) {
+        const int64_t nb = h_bo[b + 1] - h_bo[b];
+        const int64_t nq = (nb + 1) / 2;  // query pairs; pair q visits subjects 2q .. nb - 1
+        visits += nq * nb - nq * (nq - 1);
+    }
+    const int64_t slots = 4ll * std::max(ctx->num_sms, 1);
+    const int32_t chunk = (int32_t)std::min<int64_t>(
+        kChunkSubjects, std::max<int64_t>(24, round_up((visits + 5 * slots - 1) / (5 * slots), 8)));
     // per-thread scratch kept across calls (no allocation once warm)
     thread_local std::vector<GotohItem> by_var[kNumVariants];
     thread_local std::vector<double> cost_var[kNumVariants];
@@ -1055,8 +1069,8 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
             double ca[kNumVariants], cb[kNumVariants];
             if (fixed_v < 0)
                 for (int v = 0; v < kNumVariants; v++) fit[v] = variant_cost(v, rows1, &ca[v], &cb[v]);
-            for (int32_t v0 = 2 * qp; v0 < nb; v0 += kChunkSubjects) {
-                const int32_t v1 = std::min(nb, v0 + kChunkSubjects);
+            for (int32_t v0 = 2 * qp; v0 < nb; v0 += chunk) {
+                const int32_t v1 = std::min(nb, v0 + chunk);
                 const double navg = (double)(pre[v1] - pre[v0]) / (v1 - v0);
                 int best = fixed_v;
                 double bc = best >= 0 ? fa * navg + fb : 1e300;
@@ -1177,12 +1191,13 @@ int launch_packed(sad_ctx* ctx, const DevSeqs& S, const PackedPlan& plan, const 
         shp[v].smem = (size_t)S.alphabet * shp[v].prof_stride * 4;
         SAD_CHECK(shp[v].smem <= ctx->smem_optin, SAD_EINVAL,
                   "packed query profile of %zu bytes exceeds shared memory", shp[v].smem);
-        // every query pair within one strip and 32 lanes per subject: the streaming
-        // kernel (its single fill and drain saves most where one wavefront per
-        // subject costs 31 idle steps; with 8 or 16 lanes per subject the per-step
-        // bookkeeping of the stream measured as large as the fill it saves)
+        // every query pair within one strip: the streaming kernel, one fill and
+        // drain per group and item instead of one per subject (N = 2000 scores
+        // 2.37 -> 2.21 ms once the virtual column had removed its one-column steps;
+        // before that, with 8 or 16 lanes per subject its per-step bookkeeping cost
+        // as much as the fill it saved)
         shp[v].strips = rows_var[v] > strip_h;
-        shp[v].stream = !shp[v].strips && G == 32;
+        shp[v].stream = !shp[v].strips;
         KernelFn fn = pair16_kernel_for(R, shp[v].stream);
         SAD_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
         int occ = 0;
@@ -1647,10 +1662,12 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
     // running (the per-bin table can be 20 % off the best table of the whole
     // stage). Coordinate descent over the bins, largest share of the cells first,
     // every variant that ran in a bin (the four fastest alone when the stage is
-    // long) timed as the whole stage: the median of at least seven runs, each
-    // after an L2 clear. A change is kept when it gains 0.5 % and again 0.5 %
-    // measured beside the current table; two passes, then the result must beat
-    // the per-bin table in an A, B, A, B comparison of medians.
+    // long) timed as the whole stage: the mean of at least seven runs, each after
+    // an L2 clear (some tables run fast in a few runs and slow in most: the mean
+    // counts both). It starts from the better of the per-bin table and the
+    // least-padding table (A, B, A, B); a change is kept when it gains 0.5 % and
+    // again 0.5 % measured beside the current table; two passes, then the result
+    // must beat its start in an A, B, A, B comparison.
     const int32_t jreps = std::max(reps, 7);
     auto stage_ms = [&](const ScoreTuning& t, double* out) -> int {
         ctx->tuning = t;
@@ -1668,17 +1685,47 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
             *out = 1e300;
             return SAD_OK;
         }
-        std::sort(runs.begin(), runs.end());
-        *out = runs[runs.size() / 2];
+        double sum = 0;
+        for (double x : runs) sum += x;
+        *out = sum / (double)runs.size();
         return SAD_OK;
     };
     if (rc == SAD_OK && table.nbins > 1) {
-        const ScoreTuning per_bin = table;
         std::vector<int32_t> bin_of((size_t)table.nbins, -1);  // merged bin of each table entry
         for (int32_t e = 0, b = 0; e < table.nbins; e++) {
             while (b < nm && merged[b] != table.upper[e]) b++;
             bin_of[e] = b < nm ? b : -1;
         }
+        // the second start: per bin the variant of least padding among those that
+        // ran in it (the smallest strip G R that holds the bin's longest rows; then
+        // R <= 24; then G nearest 16), the open-ended last bin as timed alone
+        ScoreTuning least = table;
+        for (int32_t e = 0; e < table.nbins; e++) {
+            if (bin_of[e] < 0 || table.upper[e] == INT32_MAX) continue;
+            int64_t best_strip = INT64_MAX;
+            int best_tie = INT32_MAX;
+            for (const auto& c : ranked[bin_of[e]]) {
+                const int R = c.second.first, G = c.second.second;
+                const int64_t strip = (int64_t)R * G;
+                if (strip < table.upper[e]) continue;
+                const int tie = (R <= 24 ? 0 : 100) + std::abs(G - 16);
+                if (strip < best_strip || (strip == best_strip && tie < best_tie)) {
+                    best_strip = strip;
+                    best_tie = tie;
+                    least.R[e] = R;
+                    least.G[e] = G;
+                }
+            }
+        }
+        {
+            double a1 = 0, b1 = 0, a2 = 0, b2 = 0;
+            if (rc == SAD_OK) rc = stage_ms(table, &a1);
+            if (rc == SAD_OK) rc = stage_ms(least, &b1);
+            if (rc == SAD_OK) rc = stage_ms(table, &a2);
+            if (rc == SAD_OK) rc = stage_ms(least, &b2);
+            if (rc == SAD_OK && b1 + b2 < a1 + a2) table = least;
+        }
+        const ScoreTuning start = table;
         // table entries by their bins' cells, largest first
         std::vector<double> mcells((size_t)nm, 0.0);
         for (int32_t b = 0, m = 0; b < nbins && m < nm; b++) {
@@ -1726,13 +1773,13 @@ extern "C" int sad_scores_autotune(sad_ctx* ctx_in, const sad_seqset* seqs, cons
             }
             if (!improved) break;
         }
-        // keep the refined table only if it still beats the per-bin table, measured A, B, A, B
+        // keep the refined table only if it still beats its start, measured A, B, A, B
         double a1 = 0, b1 = 0, a2 = 0, b2 = 0;
-        if (rc == SAD_OK) rc = stage_ms(per_bin, &a1);
+        if (rc == SAD_OK) rc = stage_ms(start, &a1);
         if (rc == SAD_OK) rc = stage_ms(table, &b1);
-        if (rc == SAD_OK) rc = stage_ms(per_bin, &a2);
+        if (rc == SAD_OK) rc = stage_ms(start, &a2);
         if (rc == SAD_OK) rc = stage_ms(table, &b2);
-        if (rc == SAD_OK && b1 + b2 > a1 + a2) table = per_bin;
+        if (rc == SAD_OK && b1 + b2 > a1 + a2) table = start;
     }
     ctx->tuning = table;
     trace_reset(ctx, trace_was_on);
