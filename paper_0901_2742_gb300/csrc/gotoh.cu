@@ -1063,6 +1063,22 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
                 int tv = -1;
                 for (int t = 0; t < tu.nbins && tv < 0; t++)
                     if (rows <= tu.upper[t]) tv = bin_v[t];
+                if (tu.nbins == 0) {
+                    // no table: the variant of least padding whose one strip holds the
+                    // pair (smallest G R >= rows; then R <= 24; then G nearest 16), the
+                    // table the autotuner ends on for the N = 2000 workload (untuned, the
+                    // cost model below gave 3.2 ms there against 2.1 ms)
+                    int best_key = INT32_MAX;
+                    for (int v = 0; v < kNumVariants; v++) {
+                        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+                        if (vsh[v] < rows1 || vmax_strips[v] < 1) continue;
+                        const int key = vsh[v] * 1024 + (R <= 24 ? 0 : 512) + std::abs(G - 16);
+                        if (key < best_key) {
+                            best_key = key;
+                            tv = v;
+                        }
+                    }
+                }
                 if (tv >= 0 && variant_cost(tv, rows1, &fa, &fb)) fixed_v = tv;
             }
             bool fit[kNumVariants];
