@@ -1009,8 +1009,12 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
     const int32_t chunk = (int32_t)std::min<int64_t>(
         kChunkSubjects, std::max<int64_t>(24, round_up((visits + 5 * slots - 1) / (5 * slots), 8)));
     // per-thread scratch kept across calls (no allocation once warm)
-    thread_local std::vector<GotohItem> by_var[kNumVariants];
-    thread_local std::vector<double> cost_var[kNumVariants];
+    // (the arrays are reached through local pointers: in a shared library each
+    // thread_local access may otherwise go through the TLS lookup call)
+    thread_local std::vector<GotohItem> by_var_tls[kNumVariants];
+    thread_local std::vector<double> cost_var_tls[kNumVariants];
+    std::vector<GotohItem>* const by_var = by_var_tls;
+    std::vector<double>* const cost_var = cost_var_tls;
     for (int v = 0; v < kNumVariants; v++) {
         by_var[v].clear();
         cost_var[v].clear();
@@ -1021,6 +1025,19 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
     // the table's variant per bin (or -1)
     int bin_v[ScoreTuning::kMaxBins];
     for (int t = 0; t < tu.nbins; t++) bin_v[t] = variant_index(tu.R[t], tu.G[t]);
+    // without a table: the variants whose profile fits one strip, in the order of
+    // least padding (smallest strip G R; then R <= 24; then G nearest 16); a pair
+    // takes the first whose strip holds its rows
+    int lp_v[kNumVariants], n_lp = 0;
+    if (tu.nbins == 0 && !tu.filter) {
+        for (int v = 0; v < kNumVariants; v++)
+            if (vmax_strips[v] >= 1) lp_v[n_lp++] = v;
+        auto lp_key = [&](int v) {
+            const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
+            return vsh[v] * 1024 + (R <= 24 ? 0 : 512) + std::abs(G - 16);
+        };
+        std::sort(lp_v, lp_v + n_lp, [&](int x, int y) { return lp_key(x) < lp_key(y); });
+    }
     // per variant for a pair of `rows` rows: whether its profile fits, and the
     // estimated instruction slots of one subject of length n, ca n + cb =
     // strips G ((n + G + 1)(5 R + 16) + 40): every strip runs n + G + 1 steps on
@@ -1033,8 +1050,10 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
         *cb = k * ((G + 1) * (5.0 * R + 16.0) + 40.0);
         return strips <= vmax_strips[v];
     };
-    thread_local std::vector<int32_t> lens;  // the bucket's lengths in length order
-    thread_local std::vector<int64_t> pre;   // and their prefix sums
+    thread_local std::vector<int32_t> lens_tls;  // the bucket's lengths in length order
+    thread_local std::vector<int64_t> pre_tls;   // and their prefix sums
+    std::vector<int32_t>& lens = lens_tls;
+    std::vector<int64_t>& pre = pre_tls;
     for (int32_t b = 0; b < p; b++) {
         const int32_t nb = h_bo[b + 1] - h_bo[b];
         lens.resize((size_t)nb);
@@ -1065,19 +1084,10 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
                     if (rows <= tu.upper[t]) tv = bin_v[t];
                 if (tu.nbins == 0) {
                     // no table: the variant of least padding whose one strip holds the
-                    // pair (smallest G R >= rows; then R <= 24; then G nearest 16), the
-                    // table the autotuner ends on for the N = 2000 workload (untuned, the
-                    // cost model below gave 3.2 ms there against 2.1 ms)
-                    int best_key = INT32_MAX;
-                    for (int v = 0; v < kNumVariants; v++) {
-                        const int R = kPackedR[v / kNumG], G = kPackedG[v % kNumG];
-                        if (vsh[v] < rows1 || vmax_strips[v] < 1) continue;
-                        const int key = vsh[v] * 1024 + (R <= 24 ? 0 : 512) + std::abs(G - 16);
-                        if (key < best_key) {
-                            best_key = key;
-                            tv = v;
-                        }
-                    }
+                    // pair, the table the autotuner ends on for the N = 2000 workload
+                    // (untuned, the cost model below gave 3.2 ms there against 2.1 ms)
+                    for (int t = 0; t < n_lp && tv < 0; t++)
+                        if (vsh[lp_v[t]] >= rows1) tv = lp_v[t];
                 }
                 if (tv >= 0 && variant_cost(tv, rows1, &fa, &fb)) fixed_v = tv;
             }
@@ -1119,10 +1129,16 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
     // plan order inside a class (about 3 % resolution is enough to leave the
     // shortest items for the end of the queue)
     std::vector<GotohItem> all;
-    all.reserve(plan->all.capacity());
+    {
+        size_t total = singles.size();
+        for (int v = 0; v < kNumVariants; v++) total += by_var[v].size();
+        all.reserve(total);
+    }
     int32_t first[kNumVariants + 1];
-    thread_local std::vector<int32_t> ccnt;
-    thread_local std::vector<int32_t> cls;
+    thread_local std::vector<int32_t> ccnt_tls;
+    thread_local std::vector<int32_t> cls_tls;
+    std::vector<int32_t>& ccnt = ccnt_tls;
+    std::vector<int32_t>& cls = cls_tls;
     for (int v = 0; v < kNumVariants; v++) {
         first[v] = (int32_t)all.size();
         const size_t nv = by_var[v].size();
@@ -1359,10 +1375,18 @@ int bucket_scores_device(sad_ctx* ctx, const DevSeqs& S, const int32_t* d_bo, co
                          int64_t* total_out, cudaStream_t stream) {
     const int32_t n = S.n;
     std::vector<int32_t> h_bo((size_t)p + 1), h_order((size_t)n);
-    SAD_CUDA(cudaMemcpyAsync(h_bo.data(), d_bo, 4ull * (p + 1), cudaMemcpyDeviceToHost, stream));
-    if (n > 0)
-        SAD_CUDA(cudaMemcpyAsync(h_order.data(), d_order, 4ull * n, cudaMemcpyDeviceToHost, stream));
-    SAD_CUDA(cudaStreamSynchronize(stream));
+    {
+        // through the context's pinned area (stream-ordered after any earlier
+        // copy from it): two asynchronous copies and one wait
+        void* pin = nullptr;
+        SAD_RET(pinned(ctx, 4ull * (p + 1 + n) + 64, stream, &pin));
+        int32_t* pb = (int32_t*)pin;
+        SAD_CUDA(cudaMemcpyAsync(pb, d_bo, 4ull * (p + 1), cudaMemcpyDeviceToHost, stream));
+        if (n > 0) SAD_CUDA(cudaMemcpyAsync(pb + p + 1, d_order, 4ull * n, cudaMemcpyDeviceToHost, stream));
+        SAD_CUDA(cudaStreamSynchronize(stream));
+        memcpy(h_bo.data(), pb, 4ull * (p + 1));
+        if (n > 0) memcpy(h_order.data(), pb + p + 1, 4ull * n);
+    }
     SAD_CHECK(h_bo[0] == 0 && h_bo[p] == n, SAD_EINVAL,
               "bucket_offsets must start at 0 and end at n = %d", n);
     std::vector<char> seen((size_t)n, 0);
