@@ -1099,13 +1099,14 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
                 for (int v = 0; v < kNumVariants; v++) fit[v] = variant_cost(v, rows1, &ca[v], &cb[v]);
             for (int32_t v0 = 2 * qp; v0 < nb; v0 += chunk) {
                 const int32_t v1 = std::min(nb, v0 + chunk);
-                const double navg = (double)(pre[v1] - pre[v0]) / (v1 - v0);
+                // the chunk's cost: per subject ca n + cb, summed (no mean, no division)
+                const double nsum = (double)(pre[v1] - pre[v0]), ncnt = (double)(v1 - v0);
                 int best = fixed_v;
-                double bc = best >= 0 ? fa * navg + fb : 1e300;
+                double bc = best >= 0 ? fa * nsum + fb * ncnt : 1e300;
                 if (best < 0) {
                     for (int v = 0; v < kNumVariants; v++) {
                         if (!fit[v]) continue;
-                        const double c = ca[v] * navg + cb[v];
+                        const double c = ca[v] * nsum + cb[v] * ncnt;
                         if (c < bc) {
                             bc = c;
                             best = v;
@@ -1121,7 +1122,7 @@ void plan_packed(sad_ctx* ctx, const DevSeqs& S, const std::vector<int32_t>& h_b
                     continue;
                 }
                 by_var[best].push_back(GotohItem{b, qp, v0, v1});
-                cost_var[best].push_back(bc * (v1 - v0));
+                cost_var[best].push_back(bc);
                 rows_var[best] = std::max(rows_var[best], rows);
             }
         }
