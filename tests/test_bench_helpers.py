@@ -47,3 +47,15 @@ def test_sparse_lookup_count_brute_force():
     assert r["lookups_per_launch"] == want
     assert r["kmer_space"] == w.kmer_alphabet ** 4
     assert abs(r["frac"] - want / 1e-3 / (bench.SMS * 32 * bench.SM_MAX_MHZ * 1e6)) < 1e-12
+
+
+def test_least_padding_seed_table():
+    """The refinement's second start: per bin the smallest strip G R that holds
+    the bin's rows, then R <= 24, then G nearest 16; the open-ended bin keeps
+    its variant."""
+    t = bench.least_padding_table([(256, 32, 8), (320, 24, 16), (384, 24, 16), (512, 32, 16), (2 ** 31 - 1, 20, 32)])
+    assert t == [(256, 16, 16), (320, 20, 16), (384, 24, 16), (512, 16, 32), (2 ** 31 - 1, 20, 32)]
+    for u, R, G in t[:-1]:
+        assert R * G >= u
+        assert R in bench.VARIANT_R and G in bench.VARIANT_G
+    assert bench.least_padding_table([(100, 8, 8)]) == [(100, 8, 16)]
