@@ -147,11 +147,14 @@ __global__ void k_heavy_index(int32_t n, const int32_t* __restrict__ nex, int32_
 // Residual numerators R[h1][h2] = sum_tau min(excess_i(tau), excess_j(tau))
 // = sum_tau max(0, min(c_i, c_j) - T) for every pair of sequences with
 // excess lists (merge of two tau-sorted lists).
-__global__ void k_residual(int32_t H, const int32_t* __restrict__ hlist,
-                           const int64_t* __restrict__ ex_off, const int32_t* __restrict__ ex_tau,
-                           const int32_t* __restrict__ ex_val, const int32_t* __restrict__ nex,
-                           int32_t* __restrict__ R) {
-    const int64_t npairs = (int64_t)H * (H + 1) / 2;
+// H heavy sequences: *Hp when Hp is given (read on the device, so that the host
+// need not wait for it), else Hhost; R is row-major with row length `stride`.
+__global__ void k_residual(const int32_t* __restrict__ Hp, int32_t Hhost, int32_t stride,
+                           const int32_t* __restrict__ hlist, const int64_t* __restrict__ ex_off,
+                           const int32_t* __restrict__ ex_tau, const int32_t* __restrict__ ex_val,
+                           const int32_t* __restrict__ nex, int32_t* __restrict__ R) {
+    const int64_t H = Hp ? *Hp : Hhost;
+    const int64_t npairs = H * (H + 1) / 2;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs;
          q += (int64_t)gridDim.x * blockDim.x) {
         // row h1 of the upper triangle starts at h1*H - h1*(h1-1)/2
@@ -181,8 +184,8 @@ __global__ void k_residual(int32_t H, const int32_t* __restrict__ hlist,
                 y++;
             }
         }
-        R[h1 * H + h2] = s;
-        R[h2 * H + h1] = s;
+        R[h1 * stride + h2] = s;
+        R[h2 * stride + h1] = s;
     }
 }
 
@@ -816,17 +819,36 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
     k_heavy_index<<<1, 1024, 0, stream>>>(n, d_nex, d_hidx, d_hlist, d_H);
     SAD_LAUNCHED();
     }
-    SAD_CUDA(cudaMemcpyAsync(&H, d_H, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-    // the sorted-list path sizes its hash tables from the distinct k-mer counts
+    // Up to 4096 sequences on the dense paths the residual matrix is reserved for
+    // every sequence (at most 64 MiB) and k_residual reads H on the device: no wait
+    // here (N = 2000: the device idled 23 us for it). Otherwise, and on the
+    // sorted-list path, which sizes its hash tables from the distinct k-mer counts,
+    // the host reads H (and the counts) back.
+    const bool device_H = !sparse && (int64_t)n * n <= (1ll << 24);
     std::vector<int32_t> nd_host;
     int32_t max_nd = 0;
-    if (sparse) {
-        nd_host.resize(n);
-        SAD_CUDA(cudaMemcpyAsync(nd_host.data(), dm + o_nd, 4ull * n, cudaMemcpyDeviceToHost, stream));
+    if (device_H && n > 0) {
+        TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
+        void* rb = nullptr;
+        SAD_RET(workspace(ctx, WS_HEAVY, sizeof(int32_t) * (size_t)n * n, stream, &rb));
+        tab.R = (const int32_t*)rb;
+        tab.H = n;  // the row length; rows and columns beyond the device's H are never read
+        // a small grid: H is usually far below n, and the loop strides over any H
+        const int64_t npairs = (int64_t)n * (n + 1) / 2;
+        const int grid = (int)std::min<int64_t>((npairs + 255) / 256, (int64_t)ctx->num_sms * 2);
+        k_residual<<<grid, 256, 0, stream>>>(d_H, 0, n, d_hlist, (const int64_t*)(dm + o_exoff), ex_tau, ex_val,
+                                             d_nex, (int32_t*)rb);
+        SAD_LAUNCHED();
+    } else {
+        SAD_CUDA(cudaMemcpyAsync(&H, d_H, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        if (sparse) {
+            nd_host.resize(n);
+            SAD_CUDA(cudaMemcpyAsync(nd_host.data(), dm + o_nd, 4ull * n, cudaMemcpyDeviceToHost, stream));
+        }
+        SAD_CUDA(cudaStreamSynchronize(stream));
+        for (int32_t v : nd_host) max_nd = std::max(max_nd, v);
     }
-    SAD_CUDA(cudaStreamSynchronize(stream));
-    for (int32_t v : nd_host) max_nd = std::max(max_nd, v);
-    if (H > 0) {
+    if (!device_H && H > 0) {
         TraceScope ts(ctx, SAD_STAGE_COUNT, stream);
         SAD_CHECK((int64_t)H * H <= (1ll << 29), SAD_ENOMEM,
                   "%d sequences have k-mer counts above %d; the residual matrix would need %lld "
@@ -838,7 +860,7 @@ int kmer_rank_device(sad_ctx* ctx, const DevSeqs& S, const sad_kmer_params* kp,
         tab.H = H;
         const int64_t npairs = (int64_t)H * (H + 1) / 2;
         const int grid = (int)std::min<int64_t>((npairs + 255) / 256, (int64_t)ctx->num_sms * 16);
-        k_residual<<<grid, 256, 0, stream>>>(H, d_hlist, (const int64_t*)(dm + o_exoff), ex_tau,
+        k_residual<<<grid, 256, 0, stream>>>(nullptr, H, H, d_hlist, (const int64_t*)(dm + o_exoff), ex_tau,
                                              ex_val, d_nex, (int32_t*)rb);
         SAD_LAUNCHED();
     }
