@@ -358,9 +358,12 @@ int sad_bucket_pair_scores(sad_ctx* ctx, const sad_seqset* seqs, const int32_t* 
  * when every score provably fits 16 bits). The pair of queries at length-order
  * positions 2q, 2q+1 of a bucket with `rows` = the longer length uses the first
  * bin b with rows <= upper[b]: R[b] query rows per lane (8, 12, 16, 20, 24 or
- * 32) and G[b] lanes per subject (8, 16 or 32); rows beyond every bin, or an
- * empty table (nbins = 0, the default), use the built-in cost model. Bounds
- * must increase; at most 16 bins. The table only changes speed, never a score.
+ * 32) and G[b] lanes per subject (8, 16 or 32); rows beyond every bin use the
+ * built-in cost model. With an empty table (nbins = 0, the default) each pair
+ * takes the variant of least padding whose one strip of G x R rows holds it
+ * (the smallest G R >= rows; then R <= 24; then G nearest 16), and only pairs
+ * longer than every strip use the cost model. Bounds must increase; at most 16
+ * bins. The table only changes speed, never a score.
  * get: copies up to max_bins entries and the bin count. */
 int sad_scores_set_variants(sad_ctx* ctx, const int32_t* upper, const int32_t* R, const int32_t* G,
                             int32_t nbins);
@@ -371,7 +374,13 @@ int sad_scores_get_variants(sad_ctx* ctx, int32_t* upper, int32_t* R, int32_t* G
  * sad_bucket_pair_scores), time every packed-kernel variant on the query
  * pairs of each length bin (rows in (bin_upper[b-1], bin_upper[b]]), `reps`
  * times after one warm-up run, with CUDA events on `stream`, and store the
- * fastest variant of every non-empty bin in ctx's variant table (read it with
+ * fastest variant of every non-empty bin. The variants of different bins run
+ * side by side, so it then times whole score stages (each a full
+ * sad_bucket_pair_scores call on these arguments, into buffers of its own; the
+ * mean of at least seven runs): it starts from the better of that per-bin table
+ * and the least-padding table (see sad_scores_set_variants), changes one bin at
+ * a time while that gains 0.5 % twice, and keeps the result only if it still
+ * beats its start. The table ends in ctx's variant table (read it with
  * sad_scores_get_variants; save and restore it with set). A variant that
  * cannot hold some pair of a bin in shared memory is not eligible for that
  * bin. Synchronises `stream`. SAD_EINVAL when the inputs need the 32-bit

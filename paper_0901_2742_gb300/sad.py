@@ -286,7 +286,8 @@ def probe_alu(mix: str, warps_per_sm: int = 16, iters: int = 4096) -> tuple:
 
 
 def set_score_variants(table, ctx=None):
-    """table: list of (upper_rows, R, G); [] restores the built-in cost model."""
+    """table: list of (upper_rows, R, G); [] restores the default (per pair the
+    least-padding variant, the cost model for pairs longer than every strip)."""
     n = len(table)
     up = np.array([t[0] for t in table] or [0], np.int32)
     R = np.array([t[1] for t in table] or [0], np.int32)
