@@ -51,6 +51,11 @@ DPX_OPS_PER_CLK_SM = 64
 SCORE_TRAFFIC = {"bytes_per_step": 2182912,
                  "gotoh_device_sha256": "6dd60525784cc9be35dca38569972b6aef1059923cb06113568575d78e4605db"}
 DEVICE_CODE_END = "// Host-side plan: per bucket, members sorted by length"
+# DRAM bytes (read + write) of one plane-GEMM launch of this benchmark's N = 2000
+# step, from one ncu capture (the launch list of the timed steps); reported while
+# csrc/kmer_tc.cu is the source that was measured (sha256 of the file), else null.
+GEMM_TRAFFIC = {"bytes_per_launch": 35881344,
+                "kmer_tc_sha256": "af73c47a07d298c124e865cb084937f233099f78adef37bf3de8bbdd28acec9f"}
 
 
 def score_traffic():
@@ -64,6 +69,15 @@ def score_traffic():
     if hashlib.sha256(src[:end].encode()).hexdigest() != SCORE_TRAFFIC["gotoh_device_sha256"]:
         return None
     return SCORE_TRAFFIC["bytes_per_step"]
+
+
+def gemm_traffic():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_0901_2742_gb300", "csrc", "kmer_tc.cu")) as f:
+        src = f.read()
+    if hashlib.sha256(src.encode()).hexdigest() != GEMM_TRAFFIC["kmer_tc_sha256"]:
+        return None
+    return GEMM_TRAFFIC["bytes_per_launch"]
 
 
 def measured_peaks():
@@ -837,7 +851,10 @@ def main():
         peak_fp8 = 2.0 * bf16
         ach = flops / (ap_ms * 1e-3) / 1e12
         kmer_roofline = {"bound": "tensor", "achieved": ach, "peak": peak_fp8, "unit": "TFLOP/s (fp8 e4m3)",
-                         "frac": ach / peak_fp8, "traffic": None,
+                         "frac": ach / peak_fp8,
+                         "traffic": gemm_traffic() if args.workload == 2 and w.k == 3 else None,
+                         "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
+                                          "N=2000 step, while csrc/kmer_tc.cu is the source captured",
                          "kernel": "k_plane_gemm2 (threshold-plane GEMM, tcgen05 kind::f8f6f4, fused D sums)",
                          "kernel_ms": ap_ms, "flops_per_launch": flops, "dense_flops_per_launch": dense_flops,
                          "kblocks_run_frac": flops / dense_flops if dense_flops else None,

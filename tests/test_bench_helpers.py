@@ -1,6 +1,9 @@
 """Host-side helpers of bench.py (no GPU): the device-idle summary of the
 tracer's timeline, and the rule that the recorded DRAM traffic of the score
-kernels is reported only for the kernel source that was profiled."""
+kernels and of the plane GEMM is reported only for the source that was
+profiled, the refinement's least-padding start and the sparse lookup count."""
+import os
+
 import bench
 
 
@@ -59,3 +62,13 @@ def test_least_padding_seed_table():
         assert R * G >= u
         assert R in bench.VARIANT_R and G in bench.VARIANT_G
     assert bench.least_padding_table([(100, 8, 8)]) == [(100, 8, 16)]
+
+
+def test_gemm_traffic_only_for_the_profiled_source(monkeypatch):
+    import hashlib
+    with open(os.path.join(bench.ROOT, "paper_0901_2742_gb300", "csrc", "kmer_tc.cu")) as f:
+        h = hashlib.sha256(f.read().encode()).hexdigest()
+    want = bench.GEMM_TRAFFIC["bytes_per_launch"] if h == bench.GEMM_TRAFFIC["kmer_tc_sha256"] else None
+    assert bench.gemm_traffic() == want
+    monkeypatch.setattr(bench, "GEMM_TRAFFIC", dict(bench.GEMM_TRAFFIC, kmer_tc_sha256="0" * 64))
+    assert bench.gemm_traffic() is None
